@@ -1,0 +1,388 @@
+/*
+ * FP64 CPU oracle for the MLFMA near-field (P2P) operator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+ * CUDA path is checked against.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load it.  It shares no code, header,
+ * table or helper with the CUDA library, and the library never calls it.
+ *
+ * What it computes (readings of the paper are marked "reading"):
+ *
+ *  - Leaf boxes of a uniform octree of `level` levels over the cube
+ *    [lo, lo+edge)^3, with boxes numbered by Morton (Z-order) key: the
+ *    space-filling-curve ordering of Section 1 / Section 2.3.  Box of a point,
+ *    per axis, with float32 operations exactly as written (reading):
+ *        t = x - lo,  u = t * s,  s = (float)2^level / edge,
+ *        cell = min(floor(u), 2^level - 1);  invalid unless 0 <= u <= 2^level.
+ *    Morton key: bit b of the x, y, z cell goes to key bit 3b, 3b+1, 3b+2.
+ *  - Stable sort of (key, original index) -> perm (sorted -> original).
+ *  - Box CSR over the sorted particles (non-empty boxes only, ascending key).
+ *  - Neighbour lists: the E2 neighbourhood of Section 5.1 / Table 5, i.e. the
+ *    same-level boxes at Chebyshev cell distance <= 1 (self included), no
+ *    periodic wrap, non-empty only, ascending key (reading).
+ *  - The redundant layout of Section 5.2.1 (data duplicated per interaction
+ *    so that a thread reads one contiguous block), restated per target box:
+ *    red_start = exclusive scan of S_b = sum of the occupancies of b's
+ *    neighbours, gather_idx = the sorted source indices in neighbour order.
+ *  - The P2P sums (the near-field operator of Section 2.1; the paper names
+ *    the physics only, the kernels are readings):
+ *      gravity   (Section 5.2, stellar dynamics; G = 1, Plummer softening)
+ *          phi_i = - sum_{j in near(i), j != i} m_j (r^2 + eps^2)^(-1/2)
+ *          a_i   =   sum_{j in near(i), j != i} m_j (x_j - x_i) (r^2 + eps^2)^(-3/2)
+ *      Helmholtz (Section 5.1, Green's function of the Helmholtz equation, 3-D)
+ *          u_i   =   sum_{j in near(i), j != i} q_j exp(i k r) / (4 pi r)
+ *    where near(i) = particles of the neighbour boxes of i's box.  The
+ *    excluded term is the self pair (j = i), i.e. the r = 0 term (reading).
+ *
+ * Every sum is a plain double-precision loop over the definition; the inputs
+ * are the float32 values widened exactly.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_DOMAIN 6
+#define ORC_ERR_NOMEM 3
+
+static const double ORC_PI = 3.14159265358979323846264338327950288;
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* boxing                                                                     */
+/* ------------------------------------------------------------------------- */
+
+/* One axis of the box rule (float32 ops, no contraction: built -ffp-contract=off). */
+static int orc_axis_cell(float x, float lo, float s, int level, int32_t* cell) {
+    float t = x - lo;
+    float u = t * s;
+    float side = (float)(1 << level);
+    if (!(u >= 0.0f && u <= side)) return -1; /* also rejects NaN */
+    int32_t c = (int32_t)floorf(u);
+    if (c > (1 << level) - 1) c = (1 << level) - 1;
+    *cell = c;
+    return 0;
+}
+
+uint32_t orc_morton(int32_t cx, int32_t cy, int32_t cz, int level) {
+    uint32_t key = 0;
+    for (int b = 0; b < level; ++b) {
+        key |= (uint32_t)((cx >> b) & 1) << (3 * b);
+        key |= (uint32_t)((cy >> b) & 1) << (3 * b + 1);
+        key |= (uint32_t)((cz >> b) & 1) << (3 * b + 2);
+    }
+    return key;
+}
+
+void orc_unmorton(uint32_t key, int level, int32_t* cx, int32_t* cy, int32_t* cz) {
+    int32_t x = 0, y = 0, z = 0;
+    for (int b = 0; b < level; ++b) {
+        x |= (int32_t)((key >> (3 * b)) & 1) << b;
+        y |= (int32_t)((key >> (3 * b + 1)) & 1) << b;
+        z |= (int32_t)((key >> (3 * b + 2)) & 1) << b;
+    }
+    *cx = x; *cy = y; *cz = z;
+}
+
+/* Cells [n,3] and Morton keys [n] of every point (original order).  Returns
+ * ORC_ERR_DOMAIN if any point lies outside the boxing domain. */
+int orc_cells(const float* pos, int64_t n, int level, const float* lo, float edge,
+              int32_t* cell, uint32_t* key) {
+    if (n < 0 || level < 1 || level > 10 || !(edge > 0.0f)) return ORC_ERR_ARG;
+    float s = (float)(1 << level) / edge;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t c[3];
+        for (int a = 0; a < 3; ++a)
+            if (orc_axis_cell(pos[3 * i + a], lo[a], s, level, &c[a]) != 0) return ORC_ERR_DOMAIN;
+        if (cell) { cell[3 * i] = c[0]; cell[3 * i + 1] = c[1]; cell[3 * i + 2] = c[2]; }
+        if (key) key[i] = orc_morton(c[0], c[1], c[2], level);
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* tree: sort, box CSR, neighbour CSR                                         */
+/* ------------------------------------------------------------------------- */
+
+typedef struct { uint32_t key; int32_t idx; } orc_kv;
+
+static int orc_kv_cmp(const void* a, const void* b) {
+    const orc_kv* x = (const orc_kv*)a;
+    const orc_kv* y = (const orc_kv*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+static int orc_u32_cmp(const void* a, const void* b) {
+    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+    return (x > y) - (x < y);
+}
+
+static int orc_i32_cmp(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* index of `key` in the ascending array box_key[0..nb), or -1 */
+static int32_t orc_find_box(const uint32_t* box_key, int32_t nb, uint32_t key) {
+    const uint32_t* p = (const uint32_t*)bsearch(&key, box_key, (size_t)nb, sizeof(uint32_t), orc_u32_cmp);
+    return p ? (int32_t)(p - box_key) : -1;
+}
+
+/*
+ * Build the leaf-box structure.  Outputs (caller-allocated):
+ *   perm[n]            sorted position -> original index
+ *   box_key[n] (cap)   Morton key of each non-empty box, ascending
+ *   box_start[n+1]     CSR bounds of each box in sorted order
+ *   *n_boxes
+ *   nbr_start[n+1]     CSR bounds of each box's neighbour list
+ *   nbr_idx[27 n]      neighbour box indices, ascending
+ *   *n_nbr             total neighbour entries E
+ */
+int orc_tree(const float* pos, int64_t n, int level, const float* lo, float edge,
+             int32_t* perm, uint32_t* box_key, int32_t* box_start, int32_t* n_boxes,
+             int32_t* nbr_start, int32_t* nbr_idx, int64_t* n_nbr) {
+    if (n <= 0) return ORC_ERR_ARG;
+    uint32_t* key = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
+    orc_kv* kv = (orc_kv*)malloc((size_t)n * sizeof(orc_kv));
+    if (!key || !kv) { free(key); free(kv); return ORC_ERR_NOMEM; }
+    int st = orc_cells(pos, n, level, lo, edge, NULL, key);
+    if (st != ORC_OK) { free(key); free(kv); return st; }
+    for (int64_t i = 0; i < n; ++i) { kv[i].key = key[i]; kv[i].idx = (int32_t)i; }
+    qsort(kv, (size_t)n, sizeof(orc_kv), orc_kv_cmp);
+
+    int32_t nb = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        perm[s] = kv[s].idx;
+        if (s == 0 || kv[s].key != kv[s - 1].key) {
+            box_key[nb] = kv[s].key;
+            box_start[nb] = (int32_t)s;
+            ++nb;
+        }
+    }
+    box_start[nb] = (int32_t)n;
+    *n_boxes = nb;
+
+    int64_t e = 0;
+    int32_t side = 1 << level;
+    for (int32_t b = 0; b < nb; ++b) {
+        int32_t cx, cy, cz;
+        orc_unmorton(box_key[b], level, &cx, &cy, &cz);
+        int32_t found[27];
+        int nf = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int32_t x = cx + dx, y = cy + dy, z = cz + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) continue;
+                    int32_t c = orc_find_box(box_key, nb, orc_morton(x, y, z, level));
+                    if (c >= 0) found[nf++] = c;
+                }
+        qsort(found, (size_t)nf, sizeof(int32_t), orc_i32_cmp);
+        nbr_start[b] = (int32_t)e;
+        for (int j = 0; j < nf; ++j) nbr_idx[e++] = found[j];
+    }
+    nbr_start[nb] = (int32_t)e;
+    *n_nbr = e;
+    free(key);
+    free(kv);
+    return ORC_OK;
+}
+
+/*
+ * Redundant layout (Section 5.2.1, restated per target box): for each box b,
+ * its sources are the particles of its neighbour boxes, in neighbour order,
+ * each box's particles in sorted order.
+ *   red_start[nb+1]  exclusive scan of S_b
+ *   red_self[nb]     offset of b's own particles inside its stream
+ *   gather_idx[sum S_b] (optional) sorted source index of each record
+ * Returns the total number of records in *total.
+ */
+int orc_redundant(const int32_t* box_start, int32_t nb, const int32_t* nbr_start,
+                  const int32_t* nbr_idx, int32_t* red_start, int32_t* red_self,
+                  uint32_t* gather_idx, int64_t* total) {
+    int64_t off = 0;
+    for (int32_t b = 0; b < nb; ++b) {
+        red_start[b] = (int32_t)off;
+        int64_t own = 0;
+        for (int32_t e = nbr_start[b]; e < nbr_start[b + 1]; ++e) {
+            int32_t c = nbr_idx[e];
+            if (c == b && red_self) red_self[b] = (int32_t)own;
+            for (int32_t s = box_start[c]; s < box_start[c + 1]; ++s) {
+                if (gather_idx) gather_idx[off] = (uint32_t)s;
+                ++off;
+                ++own;
+            }
+        }
+    }
+    red_start[nb] = (int32_t)off;
+    *total = off;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* P2P sums                                                                   */
+/* ------------------------------------------------------------------------- */
+
+/* Shared tree context used by the sums: built once per call by orc_tree. */
+typedef struct {
+    int64_t n;
+    int32_t nb;
+    int32_t* perm;
+    uint32_t* box_key;
+    int32_t* box_start;
+    int32_t* nbr_start;
+    int32_t* nbr_idx;
+    int32_t* box_of;   /* original index -> box */
+} orc_ctx;
+
+static void orc_ctx_free(orc_ctx* c) {
+    free(c->perm); free(c->box_key); free(c->box_start);
+    free(c->nbr_start); free(c->nbr_idx); free(c->box_of);
+}
+
+static int orc_ctx_build(orc_ctx* c, const float* pos, int64_t n, int level, const float* lo, float edge) {
+    memset(c, 0, sizeof(*c));
+    c->n = n;
+    c->perm = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    c->box_key = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
+    c->box_start = (int32_t*)malloc((size_t)(n + 1) * sizeof(int32_t));
+    c->nbr_start = (int32_t*)malloc((size_t)(n + 1) * sizeof(int32_t));
+    c->nbr_idx = (int32_t*)malloc((size_t)n * 27 * sizeof(int32_t));
+    c->box_of = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    if (!c->perm || !c->box_key || !c->box_start || !c->nbr_start || !c->nbr_idx || !c->box_of) {
+        orc_ctx_free(c);
+        return ORC_ERR_NOMEM;
+    }
+    int64_t e;
+    int st = orc_tree(pos, n, level, lo, edge, c->perm, c->box_key, c->box_start, &c->nb,
+                      c->nbr_start, c->nbr_idx, &e);
+    if (st != ORC_OK) { orc_ctx_free(c); return st; }
+    for (int32_t b = 0; b < c->nb; ++b)
+        for (int32_t s = c->box_start[b]; s < c->box_start[b + 1]; ++s) c->box_of[c->perm[s]] = b;
+    return ORC_OK;
+}
+
+/*
+ * Softened gravity at the listed targets (original indices; NULL = all n).
+ * phi[nt], acc[nt*3] in double.  eps is the float32 softening widened.
+ * Optionally counts the ordered pairs visited into *pairs.
+ */
+int orc_gravity(const float* pos, const float* mass, int64_t n, int level, const float* lo,
+                float edge, float eps, const int64_t* targets, int64_t nt,
+                double* phi, double* acc, int64_t* pairs) {
+    orc_ctx c;
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    if (st != ORC_OK) return st;
+    if (!targets) nt = n;
+    const double e2 = (double)eps * (double)eps;
+    int64_t count = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : count)
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = targets ? targets[t] : t;
+        int32_t b = c.box_of[i];
+        double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+        double p = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
+        for (int32_t e = c.nbr_start[b]; e < c.nbr_start[b + 1]; ++e) {
+            int32_t nbox = c.nbr_idx[e];
+            for (int32_t s = c.box_start[nbox]; s < c.box_start[nbox + 1]; ++s) {
+                int64_t j = c.perm[s];
+                if (j == i) continue;
+                double dx = (double)pos[3 * j] - xi;
+                double dy = (double)pos[3 * j + 1] - yi;
+                double dz = (double)pos[3 * j + 2] - zi;
+                double r2 = dx * dx + dy * dy + dz * dz + e2;
+                double inv = 1.0 / sqrt(r2);
+                double m = (double)mass[j];
+                p -= m * inv;
+                double w = m * inv * inv * inv;
+                ax += w * dx; ay += w * dy; az += w * dz;
+                ++count;
+            }
+        }
+        phi[t] = p;
+        acc[3 * t] = ax; acc[3 * t + 1] = ay; acc[3 * t + 2] = az;
+    }
+    if (pairs) *pairs = count;
+    orc_ctx_free(&c);
+    return ORC_OK;
+}
+
+/*
+ * Helmholtz near field at the listed targets (original indices; NULL = all).
+ * q: complex64 sources laid out [nrhs][n][re,im] (float32); u: [nrhs][nt][re,im]
+ * in double.  k is the float32 wavenumber widened.
+ */
+int orc_helmholtz(const float* pos, const float* q, int nrhs, int64_t n, int level,
+                  const float* lo, float edge, float k, const int64_t* targets, int64_t nt,
+                  double* u, int64_t* pairs) {
+    if (nrhs < 1) return ORC_ERR_ARG;
+    orc_ctx c;
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    if (st != ORC_OK) return st;
+    if (!targets) nt = n;
+    const double kk = (double)k;
+    const double inv4pi = 1.0 / (4.0 * ORC_PI);
+    int64_t count = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : count)
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = targets ? targets[t] : t;
+        int32_t b = c.box_of[i];
+        double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+        for (int r = 0; r < nrhs; ++r) { u[2 * (r * nt + t)] = 0.0; u[2 * (r * nt + t) + 1] = 0.0; }
+        for (int32_t e = c.nbr_start[b]; e < c.nbr_start[b + 1]; ++e) {
+            int32_t nbox = c.nbr_idx[e];
+            for (int32_t s = c.box_start[nbox]; s < c.box_start[nbox + 1]; ++s) {
+                int64_t j = c.perm[s];
+                if (j == i) continue;
+                double dx = (double)pos[3 * j] - xi;
+                double dy = (double)pos[3 * j + 1] - yi;
+                double dz = (double)pos[3 * j + 2] - zi;
+                double r = sqrt(dx * dx + dy * dy + dz * dz);
+                double gre = cos(kk * r) * inv4pi / r;
+                double gim = sin(kk * r) * inv4pi / r;
+                for (int rr = 0; rr < nrhs; ++rr) {
+                    double qre = q[2 * (rr * n + j)], qim = q[2 * (rr * n + j) + 1];
+                    u[2 * (rr * nt + t)] += gre * qre - gim * qim;
+                    u[2 * (rr * nt + t) + 1] += gre * qim + gim * qre;
+                }
+                ++count;
+            }
+        }
+    }
+    if (pairs) *pairs = count;
+    orc_ctx_free(&c);
+    return ORC_OK;
+}
+
+/* Number of ordered pairs P = sum_b n_b S_b - n (self pairs excluded). */
+int orc_pair_count(const float* pos, int64_t n, int level, const float* lo, float edge,
+                   int64_t* pairs) {
+    orc_ctx c;
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    if (st != ORC_OK) return st;
+    int64_t p = 0;
+    for (int32_t b = 0; b < c.nb; ++b) {
+        int64_t sb = 0;
+        for (int32_t e = c.nbr_start[b]; e < c.nbr_start[b + 1]; ++e) {
+            int32_t nbox = c.nbr_idx[e];
+            sb += c.box_start[nbox + 1] - c.box_start[nbox];
+        }
+        p += (int64_t)(c.box_start[b + 1] - c.box_start[b]) * sb;
+    }
+    *pairs = p - n;
+    orc_ctx_free(&c);
+    return ORC_OK;
+}

@@ -1,0 +1,288 @@
+"""Pins for the FP64 oracle: checks against facts that do not come from the
+oracle itself (hand-derived closed forms, brute-force O(N^2) sums written
+independently here, counting identities, invariants of the operator).
+
+CPU only.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_21535_gb300 import workloads as wl
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
+# ---------------------------------------------------------------------------
+# helpers written independently of the oracle (brute force)
+# ---------------------------------------------------------------------------
+
+def brute_cells_unit(pos, level):
+    """Cells in the unit cube: floor(x * 2^L) is exact for a power of two."""
+    c = np.floor(pos.astype(np.float64) * (1 << level)).astype(np.int64)
+    return np.minimum(c, (1 << level) - 1)
+
+
+def brute_mask(cells):
+    """near[i, j] = boxes of i and j at Chebyshev distance <= 1."""
+    d = np.abs(cells[:, None, :] - cells[None, :, :]).max(axis=2)
+    return d <= 1
+
+
+def brute_gravity(pos, mass, cells, eps):
+    x = pos.astype(np.float64)
+    d = x[None, :, :] - x[:, None, :]                    # d[i, j] = x_j - x_i
+    r2 = (d ** 2).sum(axis=2) + float(eps) ** 2
+    w = brute_mask(cells)
+    np.fill_diagonal(w, False)
+    m = np.where(w, mass.astype(np.float64)[None, :], 0.0)
+    inv = 1.0 / np.sqrt(np.where(w, r2, 1.0))
+    phi = -(m * inv).sum(axis=1)
+    acc = ((m * inv ** 3)[:, :, None] * d).sum(axis=1)
+    return phi, acc
+
+
+def brute_helmholtz(pos, q, cells, k):
+    x = pos.astype(np.float64)
+    d = x[None, :, :] - x[:, None, :]
+    r = np.sqrt((d ** 2).sum(axis=2))
+    w = brute_mask(cells)
+    np.fill_diagonal(w, False)
+    rs = np.where(w, r, 1.0)
+    g = np.where(w, np.exp(1j * float(k) * rs) / (4.0 * math.pi * rs), 0.0)
+    return (g @ q.astype(np.complex128).T).T
+
+
+def rel_l2(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------------------
+# Morton keys and boxing
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", GOLDEN["morton"]["cases"])
+def test_morton_hand_values(case):
+    cx, cy, cz = case["cell"]
+    assert oracle.morton(cx, cy, cz, case["level"]) == case["key"]
+    assert oracle.unmorton(case["key"], case["level"]) == (cx, cy, cz)
+
+
+def test_cells_unit_cube_exact():
+    rng = np.random.default_rng(5)
+    pos = rng.random((20000, 3), dtype=np.float32)
+    for level in (1, 3, 7, 10):
+        cell, key = oracle.cells(pos, level, (0, 0, 0), 1.0)
+        np.testing.assert_array_equal(cell, brute_cells_unit(pos, level))
+
+
+def test_cells_domain_edges():
+    # the upper face belongs to the last cell; outside points are rejected
+    cell, _ = oracle.cells(np.array([[1.0, 0.0, 0.999999]], np.float32), 2, (0, 0, 0), 1.0)
+    assert cell.tolist() == [[3, 0, 3]]
+    for bad in ([-1e-7, 0.5, 0.5], [0.5, 1.0000001, 0.5], [np.nan, 0.5, 0.5], [0.5, 0.5, np.inf]):
+        with pytest.raises(RuntimeError):
+            oracle.cells(np.array([bad], np.float32), 2, (0, 0, 0), 1.0)
+
+
+def test_cells_grid_domain_centres():
+    # grid points sit half a spacing inside their leaf box: box = index // 4
+    for e in (16, 24, 64):
+        level, lo, edge = wl.grid_domain(e)
+        pos = wl.grid_points(e)
+        cell, _ = oracle.cells(pos, level, lo, edge)
+        idx = np.arange(e ** 3)
+        ix, iy, iz = idx % e, (idx // e) % e, idx // (e * e)
+        np.testing.assert_array_equal(cell, np.stack([ix // 4, iy // 4, iz // 4], axis=1))
+
+
+# ---------------------------------------------------------------------------
+# tree structure
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,level", [(1, 2), (7, 1), (500, 2), (3000, 3), (2000, 5)])
+def test_tree_bruteforce(n, level):
+    rng = np.random.default_rng(n + level)
+    pos = rng.random((n, 3), dtype=np.float32)
+    t = oracle.tree(pos, level, (0, 0, 0), 1.0)
+    cells = brute_cells_unit(pos, level)
+    keys = np.array([oracle.morton(*c, level) for c in cells], np.int64)
+    perm = t["perm"]
+    assert sorted(perm.tolist()) == list(range(n))
+    sk = keys[perm]
+    assert np.all(np.diff(sk) >= 0)
+    ties = np.diff(sk) == 0
+    assert np.all(np.diff(perm)[ties] > 0)                  # stable: ties by original index
+    ub = np.unique(keys)
+    np.testing.assert_array_equal(t["box_key"], ub)
+    np.testing.assert_array_equal(np.diff(t["box_start"]), np.array([np.sum(keys == k) for k in ub]))
+    bc = np.array([oracle.unmorton(int(k), level) for k in ub])
+    near = np.abs(bc[:, None, :] - bc[None, :, :]).max(axis=2) <= 1
+    for b in range(len(ub)):
+        lst = t["nbr_idx"][t["nbr_start"][b]:t["nbr_start"][b + 1]]
+        assert lst.tolist() == np.nonzero(near[b])[0].tolist()   # exactly the E2 set, ascending
+
+
+def test_regular_grid_neighbour_counts():
+    for case in GOLDEN["grid_counts"]["cases"][:2]:
+        e, B = case["edge_points"], case["boxes_per_edge"]
+        level, lo, edge = wl.grid_domain(e)
+        t = oracle.tree(wl.grid_points(e), level, lo, edge)
+        cnt = np.diff(t["nbr_start"])
+        assert t["n_boxes"] == B ** 3
+        assert t["n_nbr"] == case["n_nbr"] == (3 * B - 2) ** 3
+        vals, mult = np.unique(cnt, return_counts=True)
+        expect = {8: 8, 12: 12 * (B - 2), 18: 6 * (B - 2) ** 2, 27: (B - 2) ** 3}
+        assert dict(zip(vals.tolist(), mult.tolist())) == {k: v for k, v in expect.items() if v}
+        assert np.all(np.diff(t["box_start"]) == 64)
+
+
+def test_pair_count_closed_forms():
+    for case in GOLDEN["grid_counts"]["cases"]:
+        e = case["edge_points"]
+        level, lo, edge = wl.grid_domain(e)
+        assert oracle.pair_count(wl.grid_points(e), level, lo, edge) == case["pairs"]
+
+
+def test_redundant_identities():
+    p = wl.uniform_gravity(n=3000, level=3)
+    t = oracle.tree(p.pos, p.level, p.lo, p.edge)
+    r = oracle.redundant(t)
+    bs, ns, ni = t["box_start"], t["nbr_start"], t["nbr_idx"]
+    occ = np.diff(bs)
+    deg = np.diff(ns)
+    S = np.array([occ[ni[ns[b]:ns[b + 1]]].sum() for b in range(t["n_boxes"])])
+    assert r["total"] == S.sum() == (occ * deg).sum()             # sum S_b = sum_c n_c |N(c)|
+    np.testing.assert_array_equal(np.diff(r["red_start"]), S)
+    # each sorted source appears |N(box)| times
+    box_of_sorted = np.repeat(np.arange(t["n_boxes"]), occ)
+    np.testing.assert_array_equal(np.bincount(r["gather_idx"], minlength=3000), deg[box_of_sorted])
+    # the self segment holds the box's own particles in order
+    for b in range(t["n_boxes"]):
+        s0 = r["red_start"][b] + r["red_self"][b]
+        np.testing.assert_array_equal(r["gather_idx"][s0:s0 + occ[b]], np.arange(bs[b], bs[b + 1]))
+    # pairs = sum n_b S_b - n
+    assert oracle.pair_count(p.pos, p.level, p.lo, p.edge) == int((occ * S).sum()) - 3000
+
+
+# ---------------------------------------------------------------------------
+# sums
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,level,eps", [(400, 1, 1e-3), (1500, 2, 1e-3), (2000, 3, 0.0)])
+def test_gravity_vs_bruteforce(n, level, eps):
+    rng = np.random.default_rng(11 + n)
+    pos = rng.random((n, 3), dtype=np.float32)
+    mass = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    phi, acc, pairs = oracle.gravity(pos, mass, level, (0, 0, 0), 1.0, eps)
+    bphi, bacc = brute_gravity(pos, mass, brute_cells_unit(pos, level), np.float32(eps))
+    assert rel_l2(phi, bphi) < 1e-13
+    assert rel_l2(acc, bacc) < 1e-13
+    w = brute_mask(brute_cells_unit(pos, level))
+    assert pairs == int(w.sum()) - n
+
+
+@pytest.mark.parametrize("n,level,nrhs", [(500, 1, 1), (1800, 2, 3), (2000, 3, 2)])
+def test_helmholtz_vs_bruteforce(n, level, nrhs):
+    rng = np.random.default_rng(3 + n)
+    pos = rng.random((n, 3), dtype=np.float32)
+    q = wl.complex_normal((nrhs, n), rng)
+    k = np.float32(2 * math.pi * 3.0)
+    u, _ = oracle.helmholtz(pos, q, level, (0, 0, 0), 1.0, k)
+    bu = brute_helmholtz(pos, q, brute_cells_unit(pos, level), k)
+    assert rel_l2(u, bu) < 1e-13
+
+
+def test_targets_subset_matches_full():
+    p = wl.uniform_gravity(n=4000, level=3)
+    phi, acc, _ = oracle.gravity(p.pos, p.strength, p.level, p.lo, p.edge, p.eps)
+    tg = np.array([0, 17, 3999, 1234, 17])
+    phi2, acc2, _ = oracle.gravity(p.pos, p.strength, p.level, p.lo, p.edge, p.eps, targets=tg)
+    np.testing.assert_array_equal(phi2, phi[tg])
+    np.testing.assert_array_equal(acc2, acc[tg])
+
+
+def test_gravity_single_pair_closed_form():
+    g = GOLDEN["gravity_pair"]
+    pos = np.array(g["pos"], np.float32)
+    phi, acc, pairs = oracle.gravity(pos, np.array(g["mass"], np.float32), g["level"],
+                                     (0, 0, 0), 1.0, np.float32(g["eps"]))
+    np.testing.assert_allclose(phi, g["phi"], rtol=1e-15)
+    np.testing.assert_allclose(acc, g["acc"], rtol=1e-15, atol=0)
+    assert pairs == 2
+
+
+def test_helmholtz_single_pair_closed_form():
+    g = GOLDEN["helmholtz_pair"]
+    pos = np.array(g["pos"], np.float32)
+    q = np.array([[complex(*g["q"][0]), complex(*g["q"][1])]], np.complex64)
+    k = np.float32(g["k_over_pi"] * math.pi)
+    u, _ = oracle.helmholtz(pos, q, g["level"], (0, 0, 0), 1.0, k)
+    # k is float32, so the phase is pi/5 to ~1e-7
+    np.testing.assert_allclose(u[0, 0], complex(*g["u1"]), rtol=0, atol=2e-7)
+    np.testing.assert_allclose(u[0, 1], complex(*g["u2"]), rtol=0, atol=2e-7)
+
+
+def test_far_pair_contributes_nothing():
+    # boxes 0 and 2 along x at level 2 are not neighbours
+    pos = np.array([[0.1, 0.1, 0.1], [0.6, 0.1, 0.1]], np.float32)
+    phi, acc, pairs = oracle.gravity(pos, np.ones(2, np.float32), 2, (0, 0, 0), 1.0, 1e-3)
+    assert pairs == 0 and np.all(phi == 0) and np.all(acc == 0)
+    u, pairs = oracle.helmholtz(pos, np.ones((1, 2), np.complex64), 2, (0, 0, 0), 1.0, 1.0)
+    assert pairs == 0 and np.all(u == 0)
+
+
+def test_helmholtz_k0_is_laplace():
+    # k = 0: u = sum q/(4 pi r) = -phi/(4 pi) for gravity with eps = 0 and m = q
+    p = wl.uniform_gravity(n=3000, level=3)
+    u, _ = oracle.helmholtz(p.pos, p.strength.astype(np.complex64)[None, :], p.level, p.lo, p.edge, 0.0)
+    phi, _, _ = oracle.gravity(p.pos, p.strength, p.level, p.lo, p.edge, 0.0)
+    assert rel_l2(u[0].real, -phi / (4 * math.pi)) < 1e-14
+    assert np.all(u[0].imag == 0)
+
+
+def test_momentum_invariant():
+    # neighbour relation symmetric + odd force: sum_i m_i a_i = 0
+    for p in (wl.uniform_gravity(n=6000, level=3), wl.plummer_gravity(n=20000, level=4, eps=1e-3)):
+        _, acc, _ = oracle.gravity(p.pos, p.strength, p.level, p.lo, p.edge, p.eps)
+        f = p.strength.astype(np.float64)[:, None] * acc
+        assert np.abs(f.sum(axis=0)).max() < 1e-12 * np.abs(f).sum()
+
+
+def test_reciprocity_and_linearity():
+    # G(r) = G(-r) and a symmetric neighbour relation: P^T = P (bilinear)
+    p = wl.grid_helmholtz(edge_points=16, nrhs=2, seed=4)
+    a, b = p.strength[0], p.strength[1]
+    ua, _ = oracle.helmholtz(p.pos, a[None], p.level, p.lo, p.edge, p.k)
+    ub, _ = oracle.helmholtz(p.pos, b[None], p.level, p.lo, p.edge, p.k)
+    lhs = np.sum(b.astype(np.complex128) * ua[0])
+    rhs = np.sum(a.astype(np.complex128) * ub[0])
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # multi-RHS equals stacked single-RHS results
+    uab, _ = oracle.helmholtz(p.pos, p.strength, p.level, p.lo, p.edge, p.k)
+    np.testing.assert_array_equal(uab[0], ua[0])
+    np.testing.assert_array_equal(uab[1], ub[0])
+    # linearity (sources exactly representable so the combination is exact in complex64)
+    c = (a.astype(np.complex128) * 2.0 - b.astype(np.complex128)).astype(np.complex64)
+    uc, _ = oracle.helmholtz(p.pos, c[None], p.level, p.lo, p.edge, p.k)
+    lin = 2.0 * ua[0] - ub[0]
+    assert rel_l2(uc[0], lin) < 1e-6   # c is rounded to complex64
+
+
+def test_grid_translation_invariance():
+    # equal unit sources on a regular grid: all interior boxes see the same pattern
+    e = 24
+    level, lo, edge = wl.grid_domain(e)
+    pos = wl.grid_points(e)
+    q = np.ones((1, e ** 3), np.complex64)
+    u, _ = oracle.helmholtz(pos, q, level, lo, edge, np.float32(2 * math.pi))
+    u = u[0].reshape(e, e, e)                     # [iz, iy, ix]
+    a = u[4:8, 4:8, 4:8]
+    for (z, y, x) in ((8, 8, 8), (4, 12, 8), (12, 4, 16)):
+        np.testing.assert_allclose(u[z:z + 4, y:y + 4, x:x + 4], a, rtol=1e-6, atol=0)
