@@ -1,0 +1,385 @@
+"""Benchmark: near-field (P2P) pair interactions per second on one GB300.
+
+One step = the whole hot path on one batch of synthetic input already in HBM:
+tree build (Morton keys, radix sort, box CSR, E2 neighbour lists) ->
+restructuring (box-ordered records, redundant per-box streams) -> P2P kernel
+(outputs written in original order).  Default workload: the Helmholtz near
+field on a 64^3 grid at lambda/10 spacing, 4^3-point leaf boxes, one complex
+right-hand side, redundant layout.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(the only other code path this script may run), on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2511_21535_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "P2P pair-interactions/s"
+L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
+MUFU_PER_SM_CLK = 16           # nominal XU (MUFU) throughput per SM per clock
+FP32_PER_SM_CLK = 128
+
+
+def make_problem(name: str):
+    if name == "grid_helmholtz":
+        return wl.grid_helmholtz()
+    if name == "uniform_gravity":
+        return wl.uniform_gravity()
+    if name == "plummer_gravity":
+        return wl.plummer_gravity()
+    if name == "grid_helmholtz_128":
+        return wl.grid_helmholtz(edge_points=128)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(prob, layout):
+    cfg = {"workload": prob.name, "n": prob.n, "level": prob.level, "kernel": prob.kind, "layout": layout,
+           "nrhs": prob.nrhs, "l2": "flushed between steps (512 MiB write)", "inputs": "seeded synthetic"}
+    if prob.kind == "gravity":
+        cfg["eps"] = prob.eps
+    else:
+        cfg["k"] = prob.k
+        cfg["spacing"] = wl.SPACING
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2511_21535_gb300 import p2p
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    prob = make_problem(args.workload)
+    layout = args.layout
+    plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
+                    timing=True, device=dev)
+    if args.tpl:
+        plan.set_tuning(args.tpl, args.tile)
+    pos = torch.from_numpy(prob.pos).to(dev)
+    strength = torch.from_numpy(prob.strength).to(dev)
+    out_a = torch.empty(prob.n, dtype=torch.float32, device=dev)
+    out_b = torch.empty(prob.n, 3, dtype=torch.float32, device=dev)
+    out_u = torch.empty(prob.nrhs, prob.n, dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.tree_build(pos)
+        plan.restructure(pos, strength)
+        if prob.kind == "gravity":
+            plan.gravity(prob.eps, out_a, out_b)
+        else:
+            plan.helmholtz(prob.k, out_u)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    cnt = plan.counters(check=True)
+    pairs = cnt["pairs"] * (prob.nrhs if prob.kind == "helmholtz" else 1)
+    geo_pairs = cnt["pairs"]
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.barrier()
+    torch.cuda.synchronize()
+    launches0 = p2p.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phases = {k: [] for k in p2p.PHASES}
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_id = vis.split(",")[local_rank].strip() if vis else str(local_rank)
+    with ClockSampler(smi_id) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            t = plan.timing()      # waits for this step's events
+            for k, v in t.items():
+                phases[k].append(v)
+        torch.cuda.synchronize()
+    launches = p2p.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        import torch.distributed as td
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        td.all_reduce(tt, op=td.ReduceOp.MAX)
+        ms = float(tt.item())
+        td.barrier()
+
+    # end to end through the API from pinned host buffers: H2D, full step, D2H
+    hpos = torch.from_numpy(prob.pos).pin_memory()
+    hstr = torch.from_numpy(prob.strength).pin_memory()
+    if prob.kind == "gravity":
+        hout = (torch.empty(prob.n, dtype=torch.float32).pin_memory(),
+                torch.empty(prob.n, 3, dtype=torch.float32).pin_memory())
+    else:
+        hout = (torch.empty(prob.nrhs, prob.n, dtype=torch.complex64).pin_memory(),)
+    dpos = torch.empty_like(pos)
+    dstr = torch.empty_like(strength)
+
+    def e2e_step():
+        dpos.copy_(hpos, non_blocking=True)
+        dstr.copy_(hstr, non_blocking=True)
+        plan.tree_build(dpos)
+        plan.restructure(dpos, dstr)
+        if prob.kind == "gravity":
+            plan.gravity(prob.eps, out_a, out_b)
+            hout[0].copy_(out_a, non_blocking=True)
+            hout[1].copy_(out_b, non_blocking=True)
+        else:
+            plan.helmholtz(prob.k, out_u)
+            hout[0].copy_(out_u, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        flush.zero_()
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    h2d = prob.pos.nbytes + prob.strength.nbytes
+    d2h = sum(t.numel() * t.element_size() for t in hout)
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+
+    kern_ms = sum(phases["kernel"]) / len(phases["kernel"])
+    csum = clk.summary()
+    f_mhz = csum["sm_mhz"] or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if prob.kind == "helmholtz" and prob.nrhs <= 2:
+        pipe, per_pair = "mufu", 3.0        # rsqrt, sin, cos per geometric pair
+        peak = MUFU_PER_SM_CLK * sms * f_mhz * 1e6 / per_pair
+    elif prob.kind == "helmholtz":
+        pipe, per_pair = "fp32", 12.0 + 4.0 * prob.nrhs
+        peak = FP32_PER_SM_CLK * sms * f_mhz * 1e6 / per_pair
+    else:
+        pipe, per_pair = "fp32", 13.0
+        peak = FP32_PER_SM_CLK * sms * f_mhz * 1e6 / per_pair
+    achieved = geo_pairs / (kern_ms * 1e-3)
+    result = {
+        "metric": METRIC,
+        "value": world * pairs / (ms * 1e-3),
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(prob, layout),
+        "e2e": {"value": world * pairs / (e2e_mean * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
+        "roofline": {"bound": "alu", "pipe": pipe, "kernel": f"k_{prob.kind}", "achieved": achieved / 1e9,
+                     "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+                     "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms, "peak_source": "nominal unit counts"},
+        "phases_ms": {k: (sum(v) / len(v) if v else None) for k, v in phases.items()},
+        "pairs_per_step": pairs,
+        "gpu_launches": launches,
+        "clocks": csum,
+    }
+    return result, prob
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(prob, target_seconds: float, seed: int = 0):
+    """Time the FP64 oracle on a random sample of targets sized for ~target_seconds."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    nt = 256
+    while True:
+        tg = rng.choice(prob.n, min(nt, prob.n), replace=False)
+        t0 = time.perf_counter()
+        _, pairs = _oracle_eval(oracle, prob, tg)
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 * target_seconds or nt >= prob.n:
+            return pairs, dt, len(tg)
+        nt = min(prob.n, int(nt * max(2.0, 0.5 * target_seconds / max(dt, 1e-3))))
+
+
+def _oracle_eval(oracle, prob, tg):
+    if prob.kind == "gravity":
+        _, _, pairs = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps, targets=tg)
+        return None, pairs
+    u, pairs = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k, targets=tg)
+    return u, pairs * prob.nrhs
+
+
+def cpu_baseline(prob, seconds):
+    import oracle
+    pairs, dt, nt = oracle_sample(prob, seconds)
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle on {nt} random targets of the same workload ({pairs} pairs, {dt:.2f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    prob = make_problem(args.workload)
+    oracle.build()
+    rng = np.random.default_rng(1)
+    # size one step to ~2 s of oracle work
+    pairs1, dt1, nt1 = oracle_sample(prob, 2.0)
+    per_target = dt1 / nt1
+    nt = max(64, min(prob.n, int(2.0 / max(per_target, 1e-9))))
+    samples = [rng.choice(prob.n, nt, replace=False) for _ in range(args.warmup + args.steps)]
+    for tg in samples[:args.warmup]:
+        _oracle_eval(oracle, prob, tg)
+    tot_pairs, tot_t = 0, 0.0
+    for tg in samples[args.warmup:]:
+        t0 = time.perf_counter()
+        _, p = _oracle_eval(oracle, prob, tg)
+        tot_t += time.perf_counter() - t0
+        tot_pairs += p
+    value = tot_pairs / tot_t
+    ms = 1e3 * tot_t / max(1, args.steps)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(prob, args.layout),
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"each step: FP64 oracle on {nt} random targets of the workload"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="grid_helmholtz")
+    ap.add_argument("--layout", default="redundant", choices=["redundant", "indirect"])
+    ap.add_argument("--tpl", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=64)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+
+    # the oracle's process pool is created before any GPU work
+    import torch
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2511_21535_gb300 import build as cuda_build
+    cuda_build.build()
+    res, prob = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

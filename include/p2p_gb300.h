@@ -1,0 +1,259 @@
+/*
+ * p2p_gb300.h -- C ABI of the GB300 (sm_103a) near-field (P2P) library.
+ *
+ * The library computes the near-field operator of the Multilevel Fast
+ * Multipole Algorithm (MLFMA): for every leaf box of a uniform octree, the
+ * direct pairwise kernel is summed over the particles of the box's E2
+ * neighbourhood (the <= 27 same-level boxes at Chebyshev distance <= 1,
+ * itself included).  It follows the paper's P2P pipeline (Section 3.2,
+ * Proposition 2, Eq. 2: collect -> transfer -> compute -> update), with the
+ * collect step done on the device, and offers both data layouts the paper
+ * compares (Section 5.2.1):
+ *
+ *   P2P_LAYOUT_INDIRECT   sources read through the box bounds and neighbour
+ *                         lists from the box-ordered particle array
+ *                         (the "Indexing" implementation);
+ *   P2P_LAYOUT_REDUNDANT  a restructuring pass first copies every box's
+ *                         neighbour sources into one contiguous per-box
+ *                         stream (the "Redundant" implementation, data
+ *                         duplicated so that each worker reads one
+ *                         contiguous block).
+ *
+ * Kernels (the paper names the physics, Sections 5.1 and 5.2, not formulas;
+ * these are the library's definitions):
+ *   gravity    phi_i = - sum_{j in near(i), j != i} m_j (r_ij^2 + eps^2)^(-1/2)
+ *              a_i   =   sum_{j in near(i), j != i} m_j (x_j - x_i)(r_ij^2 + eps^2)^(-3/2)
+ *   Helmholtz  u_i   =   sum_{j in near(i), j != i} q_j exp(i k r_ij) / (4 pi r_ij)
+ *              for each of nrhs right-hand sides.
+ * The excluded term is the self pair; for Helmholtz on distinct points this
+ * is exactly the r = 0 term.  Two distinct particles at the same position
+ * are outside the Helmholtz operator's domain (and outside gravity's when
+ * eps = 0).
+ *
+ * Conventions
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless
+ *    the comment says "host".  The library allocates no device memory: it
+ *    works inside one caller-provided workspace whose size
+ *    p2p_plan_workspace_bytes() returns.  Workspace base must be 256-byte
+ *    aligned; array arguments must be aligned to their element type (float2
+ *    arrays to 8 bytes).
+ *  - Inputs and outputs are in ORIGINAL particle order.  Positions are
+ *    float32 [n][3] row-major; masses float32 [n]; complex data is complex64
+ *    (interleaved re, im float32) laid out [nrhs][n].
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All work is enqueued asynchronously on it; no call
+ *    synchronises with the host except p2p_read_counters() and
+ *    p2p_plan_timing().  No call performs a host<->device copy on the hot
+ *    path, so a sequence of calls can be captured into a CUDA graph.
+ *  - Errors: argument checks are synchronous and return a status.  Errors the
+ *    device detects (a position outside the boxing domain, an expired
+ *    bounded wait) set bits in a flag word in the workspace header, read with
+ *    p2p_read_counters().  No call aborts, traps or throws.
+ *  - Thread-compatible: distinct plans may be used concurrently; one plan
+ *    must not be used by two host threads at once.
+ */
+#ifndef P2P_GB300_H
+#define P2P_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define P2P_ABI_VERSION 1
+
+typedef enum {
+    P2P_OK = 0,
+    P2P_ERR_INVALID_ARG = 1,   /* bad size, pointer, alignment or option        */
+    P2P_ERR_CUDA = 2,          /* a CUDA runtime call failed                     */
+    P2P_ERR_OOM = 3,           /* host allocation failed                         */
+    P2P_ERR_TIMEOUT = 4,       /* a bounded device wait expired                  */
+    P2P_ERR_UNSUPPORTED = 5,   /* valid request this build does not handle       */
+    P2P_ERR_DOMAIN = 6,        /* a position lies outside the boxing domain      */
+    P2P_ERR_WORKSPACE = 7,     /* workspace missing, misaligned or too small     */
+    P2P_ERR_STATE = 8          /* call out of order (e.g. operator before tree)  */
+} p2p_status;
+
+typedef enum { P2P_GRAVITY = 0, P2P_HELMHOLTZ = 1 } p2p_kernel_kind;
+typedef enum { P2P_LAYOUT_INDIRECT = 0, P2P_LAYOUT_REDUNDANT = 1 } p2p_layout;
+
+/* plan flags */
+#define P2P_PLAN_GATHER_MAP  0x1u  /* restructuring also writes the gather map      */
+#define P2P_PLAN_PLAIN_FP32  0x2u  /* plain FP32 accumulation (default: compensated) */
+#define P2P_PLAN_TIMING      0x4u  /* record CUDA events around each phase           */
+
+/* device flag bits (p2p_read_counters: counters[P2P_CTR_FLAGS]) */
+#define P2P_FLAG_DOMAIN   0x1u     /* a position was outside the domain             */
+#define P2P_FLAG_TIMEOUT  0x2u     /* a bounded wait expired in a kernel             */
+#define P2P_FLAG_CAPACITY 0x4u     /* an imported structure overflowed a workspace   */
+                                   /* array; the affected step was skipped          */
+
+/* limits of this build */
+#define P2P_MAX_N      (1LL << 26) /* particles per plan (27 n must fit in int32)   */
+#define P2P_MAX_LEVEL  10          /* octree levels (30-bit Morton keys)            */
+#define P2P_MAX_NRHS   16
+
+typedef struct p2p_plan p2p_plan;
+
+/* Human-readable name of a status code (static storage). */
+const char* p2p_status_string(int status);
+
+/* ABI version (P2P_ABI_VERSION). */
+int p2p_abi_version(void);
+
+/*
+ * Create a plan (host memory only).  The plan fixes the problem shape:
+ *   kind    P2P_GRAVITY or P2P_HELMHOLTZ
+ *   n       particles, 1 <= n <= P2P_MAX_N
+ *   level   octree level, 1..P2P_MAX_LEVEL; 8^level leaf boxes
+ *   lo      host float[3], lower corner of the boxing cube
+ *   edge    edge length of the boxing cube (> 0); a point's box per axis is
+ *           min(floor((x - lo) * s), 2^level - 1) with s = (float)2^level / edge,
+ *           evaluated in float32 as written (one subtraction, one product);
+ *           points with (x - lo) * s outside [0, 2^level] are out of domain
+ *   nrhs    right-hand sides (Helmholtz, 1..P2P_MAX_NRHS; must be 1 for gravity)
+ *   layout  P2P_LAYOUT_INDIRECT or P2P_LAYOUT_REDUNDANT
+ *   flags   P2P_PLAN_* bits
+ * Returns P2P_ERR_INVALID_ARG on a bad shape, P2P_ERR_OOM if the host
+ * allocation fails.  *out is NULL on failure.
+ */
+int p2p_plan_create(p2p_plan** out, int kind, int64_t n, int level, const float* lo,
+                    float edge, int nrhs, int layout, unsigned flags);
+
+/* Release a plan (NULL is a no-op).  Does not touch device memory. */
+int p2p_plan_destroy(p2p_plan* plan);
+
+/* Bytes of device workspace the plan needs (host out-pointer). */
+int p2p_plan_workspace_bytes(const p2p_plan* plan, size_t* bytes);
+
+/*
+ * Tuning knobs (the autotuner's search space, Section 3.5: threads per box
+ * and redundancy grain).  targets_per_lane: 1, 2 or 4 targets held in
+ * registers by each lane; a warp owns 32*targets_per_lane targets of one box.
+ * tile: source records per shared-memory stage (32 or 64).  ctas_per_sm: 0 =
+ * as many as fit.  Returns P2P_ERR_INVALID_ARG on values outside these sets.
+ */
+int p2p_plan_set_tuning(p2p_plan* plan, int targets_per_lane, int tile, int ctas_per_sm);
+
+/*
+ * Collect, part 1 -- build the leaf-box structure from positions:
+ * Morton keys, stable radix sort of (key, original index), box bounds (CSR
+ * over the sorted particles, non-empty boxes in ascending key), and each
+ * box's E2 neighbour list (ascending key).  pos: float32 [n][3] (device).
+ * Clears the device flag word first.  Out-of-domain points set
+ * P2P_FLAG_DOMAIN.  Results stay in the workspace; p2p_plan_array() locates
+ * them.
+ */
+int p2p_tree_build(p2p_plan* plan, const float* pos, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Collect, alternative -- import a caller-built leaf-box structure (the
+ * paper's statement of the problem: leaf-box bounds and neighbour lists in).
+ * All arrays device, int32:
+ *   perm[n]                   sorted position -> original particle index
+ *   box_start[n_boxes+1]      CSR bounds of each box in sorted order
+ *   nbr_start[n_boxes+1]      CSR bounds of each box's neighbour list
+ *   nbr_idx[nbr_start[n_boxes]] neighbour box indices
+ * box_key may be NULL (it is only used by p2p_tree_build itself).  The
+ * neighbour relation must be symmetric and each list must contain the box
+ * itself and be ascending; the library does not verify this.
+ */
+int p2p_tree_import(p2p_plan* plan, const int32_t* perm, const int32_t* box_start,
+                    int32_t n_boxes, const int32_t* nbr_start, const int32_t* nbr_idx,
+                    int32_t n_nbr, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Collect, part 2 -- restructuring.  Gathers positions and source strengths
+ * into box order (both layouts), and for P2P_LAYOUT_REDUNDANT copies each
+ * box's neighbour sources into one contiguous stream (Section 5.2.1), plus
+ * the gather map if P2P_PLAN_GATHER_MAP.
+ *   pos        float32 [n][3]
+ *   strength   gravity: float32 mass [n]; Helmholtz: complex64 q [nrhs][n]
+ */
+int p2p_restructure(p2p_plan* plan, const float* pos, const void* strength, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/*
+ * Compute + update -- softened gravity.  Needs p2p_tree_build (or import) and
+ * p2p_restructure on this workspace first.  Writes phi float32 [n] and acc
+ * float32 [n][3] in original particle order.  eps >= 0 (float32).
+ */
+int p2p_gravity(p2p_plan* plan, float eps, float* phi, float* acc, void* ws, size_t ws_bytes,
+                void* stream);
+
+/*
+ * Compute + update -- Helmholtz.  Writes u complex64 [nrhs][n] in original
+ * order.  k is the float32 wavenumber.  When k times the largest in-box
+ * distance stays below 100 pi the sine and cosine use the hardware
+ * approximation (absolute error below 1e-6 there); otherwise the accurate
+ * library routines.
+ */
+int p2p_helmholtz(p2p_plan* plan, float k, void* u, void* ws, size_t ws_bytes, void* stream);
+
+/* identifiers of workspace arrays for p2p_plan_array */
+typedef enum {
+    P2P_ARR_PERM = 0,        /* int32 [n]               sorted -> original index    */
+    P2P_ARR_BOX_KEY = 1,     /* uint32 [n_boxes]        Morton key of each box       */
+    P2P_ARR_BOX_START = 2,   /* int32 [n_boxes+1]       box bounds                   */
+    P2P_ARR_NBR_START = 3,   /* int32 [n_boxes+1]       neighbour-list bounds        */
+    P2P_ARR_NBR_IDX = 4,     /* int32 [n_nbr]           neighbour box indices        */
+    P2P_ARR_RED_START = 5,   /* int32 [n_boxes+1]       redundant stream bounds      */
+    P2P_ARR_RED_SELF = 6,    /* int32 [n_boxes]         own particles' stream offset */
+    P2P_ARR_GATHER_IDX = 7,  /* uint32 [red_start[n_boxes]] sorted source per record */
+    P2P_ARR_SORTED_KEY = 8,  /* uint32 [n]              Morton key, sorted order     */
+    P2P_ARR_COUNT = 9
+} p2p_array_id;
+
+/*
+ * Where a workspace array lives: *offset_bytes from the workspace base and
+ * *capacity elements reserved (the used length is given by the counters).
+ * Returns P2P_ERR_UNSUPPORTED for an array the plan does not keep (the
+ * gather map without P2P_PLAN_GATHER_MAP; redundant arrays for the indirect
+ * layout).
+ */
+int p2p_plan_array(const p2p_plan* plan, int which, int64_t* offset_bytes, int64_t* capacity);
+
+/* counters of the workspace header (p2p_read_counters) */
+typedef enum {
+    P2P_CTR_N_BOXES = 0,     /* non-empty leaf boxes                        */
+    P2P_CTR_N_NBR = 1,       /* neighbour-list entries E                    */
+    P2P_CTR_FLAGS = 2,       /* P2P_FLAG_* bits                             */
+    P2P_CTR_TOTAL_SRC = 3,   /* redundant records, sum_b S_b                */
+    P2P_CTR_PAIRS = 4,       /* ordered pairs sum_b n_b S_b - n (last op)   */
+    P2P_CTR_N_ITEMS = 5,     /* work items of the last operator call        */
+    P2P_CTR_COUNT = 6
+} p2p_counter_id;
+
+/*
+ * Copy the header counters to host int64 out[P2P_CTR_COUNT] and synchronise
+ * the stream.  Returns P2P_ERR_DOMAIN / P2P_ERR_TIMEOUT if the flag word has
+ * the matching bit set (the counters are still written).
+ */
+int p2p_read_counters(const p2p_plan* plan, const void* ws, int64_t* out, void* stream);
+
+/* phases timed when the plan has P2P_PLAN_TIMING */
+typedef enum {
+    P2P_PHASE_TREE = 0,        /* p2p_tree_build                                 */
+    P2P_PHASE_RESTRUCTURE = 1, /* p2p_restructure                                */
+    P2P_PHASE_KERNEL = 2,      /* the P2P compute kernel alone                   */
+    P2P_PHASE_OPERATOR = 3,    /* p2p_gravity / p2p_helmholtz as a whole         */
+    P2P_PHASE_COUNT = 4
+} p2p_phase_id;
+
+/*
+ * Milliseconds of each phase's last run (host float out[P2P_PHASE_COUNT]),
+ * measured with CUDA events on the launching stream; waits for the events.
+ * A phase not run since the plan was created reports -1.
+ */
+int p2p_plan_timing(p2p_plan* plan, float* ms_out);
+
+/* Number of kernels this library has launched in this process (all plans). */
+int64_t p2p_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P2P_GB300_H */

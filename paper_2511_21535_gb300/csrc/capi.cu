@@ -1,0 +1,341 @@
+// C ABI: plans, workspace layout, argument checks, phase timing.
+#include <atomic>
+#include <new>
+
+#include "common.cuh"
+#include "p2p_loop.cuh"
+
+struct p2p_plan {
+    p2p::Plan p;
+};
+
+namespace p2p {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static void compute_layout(Plan* p) {
+    Layout& L = p->L;
+    const int64_t n = p->n;
+    const int64_t bc = p->box_cap;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + (bytes ? bytes : 16), 256);
+        return o;
+    };
+    L.header = take(kHeaderBytes);
+    L.keys_a = take(n * 4);
+    L.keys_b = take(n * 4);
+    L.vals_a = take(n * 4);
+    L.perm = take(n * 4);
+    L.sorted_key = take(n * 4);
+    L.hist = take(((size_t)256 * p->sort_tiles + 1) * 4);
+    int64_t scan_max = (int64_t)256 * p->sort_tiles;
+    if (n > scan_max) scan_max = n;
+    L.scan_tmp = take(scan_scratch_bytes(scan_max));
+    L.flags = take((n + 1) * 4);
+    L.box_key = take(bc * 4);
+    L.box_start = take((bc + 1) * 4);
+    L.table = p->use_table ? take(((size_t)1 << (3 * p->level)) * 4) : 0;
+    L.nbr_cnt = take(bc * 4);
+    L.nbr_start = take((bc + 1) * 4);
+    L.nbr_idx = take((size_t)27 * bc * 4);
+    L.src = take((size_t)n * p->rec_words * 16);
+    L.box_S = take((bc + 1) * 4);
+    L.items = take((size_t)p->items_cap * 8);
+    if (p->layout == P2P_LAYOUT_REDUNDANT) {
+        L.red_start = take((bc + 1) * 4);
+        L.red_self = take(bc * 4);
+        L.red_src = take((size_t)p->red_cap * p->rec_words * 16);
+        L.gather = (p->flags & P2P_PLAN_GATHER_MAP) ? take((size_t)p->red_cap * 4) : 0;
+    } else {
+        L.red_start = L.red_self = L.red_src = L.gather = 0;
+    }
+    L.total = off;
+}
+
+static int check_ws(const Plan* p, const void* ws, size_t ws_bytes) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < p->L.total) return P2P_ERR_WORKSPACE;
+    return P2P_OK;
+}
+
+static void ev_begin(Plan* p, int ph, cudaStream_t s) {
+    if (p->timing) cudaEventRecord(p->ev[ph][0], s);
+}
+static void ev_end(Plan* p, int ph, cudaStream_t s) {
+    if (p->timing) {
+        cudaEventRecord(p->ev[ph][1], s);
+        p->ev_valid[ph] = 1;
+    }
+}
+
+static LoopArgs loop_args(const Plan* p, void* ws) {
+    const Layout& L = p->L;
+    LoopArgs a;
+    a.rec = at<float4>(ws, L.src);
+    a.red = (p->layout == P2P_LAYOUT_REDUNDANT) ? at<float4>(ws, L.red_src) : nullptr;
+    a.words = p->rec_words;
+    a.tile = p->tile;
+    a.box_start = at<int32_t>(ws, L.box_start);
+    a.nbr_start = at<int32_t>(ws, L.nbr_start);
+    a.nbr_idx = at<int32_t>(ws, L.nbr_idx);
+    a.red_start = (p->layout == P2P_LAYOUT_REDUNDANT) ? at<int32_t>(ws, L.red_start) : nullptr;
+    a.red_self = (p->layout == P2P_LAYOUT_REDUNDANT) ? at<int32_t>(ws, L.red_self) : nullptr;
+    a.items = at<int2>(ws, L.items);
+    a.hdr = at<Header>(ws, L.header);
+    return a;
+}
+
+}  // namespace p2p
+
+using namespace p2p;
+
+extern "C" {
+
+const char* p2p_status_string(int status) {
+    switch (status) {
+        case P2P_OK: return "ok";
+        case P2P_ERR_INVALID_ARG: return "invalid argument";
+        case P2P_ERR_CUDA: return "CUDA runtime error";
+        case P2P_ERR_OOM: return "out of host memory";
+        case P2P_ERR_TIMEOUT: return "bounded device wait expired";
+        case P2P_ERR_UNSUPPORTED: return "unsupported request";
+        case P2P_ERR_DOMAIN: return "position outside the boxing domain";
+        case P2P_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case P2P_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+int p2p_abi_version(void) { return P2P_ABI_VERSION; }
+
+int64_t p2p_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int p2p_plan_create(p2p_plan** out, int kind, int64_t n, int level, const float* lo, float edge, int nrhs,
+                    int layout, unsigned flags) {
+    if (!out) return P2P_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (kind != P2P_GRAVITY && kind != P2P_HELMHOLTZ) return P2P_ERR_INVALID_ARG;
+    if (n < 1 || n > P2P_MAX_N) return P2P_ERR_INVALID_ARG;
+    if (level < 1 || level > P2P_MAX_LEVEL) return P2P_ERR_INVALID_ARG;
+    if (!lo || !(edge > 0.0f) || !(edge < 3.0e38f)) return P2P_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!(lo[a] == lo[a]) || lo[a] > 3.0e38f || lo[a] < -3.0e38f) return P2P_ERR_INVALID_ARG;
+    if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT) return P2P_ERR_INVALID_ARG;
+    if (kind == P2P_GRAVITY && nrhs != 1) return P2P_ERR_INVALID_ARG;
+    if (nrhs < 1 || nrhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
+    if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING)) return P2P_ERR_INVALID_ARG;
+    p2p_plan* h = new (std::nothrow) p2p_plan;
+    if (!h) return P2P_ERR_OOM;
+    Plan* p = &h->p;
+    *p = Plan{};
+    p->kind = kind;
+    p->n = n;
+    p->level = level;
+    for (int a = 0; a < 3; ++a) p->lo[a] = lo[a];
+    p->edge = edge;
+    p->scale = (float)(1 << level) / edge;
+    p->nrhs = nrhs;
+    p->layout = layout;
+    p->flags = flags;
+    const int64_t boxes = (int64_t)1 << (3 * level);
+    p->box_cap = n < boxes ? n : boxes;
+    p->red_cap = 27 * n;
+    p->rec_words = (kind == P2P_GRAVITY) ? 1 : helmholtz_rec_words(nrhs);
+    p->sort_tiles = (int)((n + 2047) / 2048);
+    p->use_table = level <= 8;
+    // defaults; p2p_plan_set_tuning / the autotuner may change them
+    if (kind == P2P_GRAVITY) {
+        p->tpl = 2;
+        p->tile = 64;
+    } else {
+        p->tpl = nrhs >= 4 ? 1 : 2;
+        p->tile = nrhs >= 4 ? 32 : 64;
+    }
+    p->ctas_per_sm = 0;
+    p->items_cap = p->box_cap + (n + 31) / 32 + 1;
+    compute_layout(p);
+    p->timing = (flags & P2P_PLAN_TIMING) ? 1 : 0;
+    if (p->timing) {
+        for (int ph = 0; ph < P2P_PHASE_COUNT; ++ph)
+            for (int e = 0; e < 2; ++e)
+                if (cudaEventCreate(&p->ev[ph][e]) != cudaSuccess) {
+                    for (int q = 0; q <= ph; ++q)
+                        for (int f = 0; f < 2; ++f)
+                            if (p->ev[q][f]) cudaEventDestroy(p->ev[q][f]);
+                    delete h;
+                    return P2P_ERR_CUDA;
+                }
+    }
+    *out = h;
+    return P2P_OK;
+}
+
+int p2p_plan_destroy(p2p_plan* h) {
+    if (!h) return P2P_OK;
+    Plan* p = &h->p;
+    if (p->timing)
+        for (int ph = 0; ph < P2P_PHASE_COUNT; ++ph)
+            for (int e = 0; e < 2; ++e) cudaEventDestroy(p->ev[ph][e]);
+    delete h;
+    return P2P_OK;
+}
+
+int p2p_plan_workspace_bytes(const p2p_plan* h, size_t* bytes) {
+    if (!h || !bytes) return P2P_ERR_INVALID_ARG;
+    *bytes = h->p.L.total;
+    return P2P_OK;
+}
+
+int p2p_plan_set_tuning(p2p_plan* h, int targets_per_lane, int tile, int ctas_per_sm) {
+    if (!h) return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    const bool tpl_ok = targets_per_lane == 1 || targets_per_lane == 2 ||
+                        (targets_per_lane == 4 && p->kind == P2P_GRAVITY);
+    if (!tpl_ok || (tile != 32 && tile != 64) || ctas_per_sm < 0 || ctas_per_sm > 32) return P2P_ERR_INVALID_ARG;
+    p->tpl = targets_per_lane;
+    p->tile = tile;
+    p->ctas_per_sm = ctas_per_sm;
+    return P2P_OK;
+}
+
+int p2p_tree_build(p2p_plan* h, const float* pos, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || !pos || (reinterpret_cast<uintptr_t>(pos) & 3u)) return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    int st = check_ws(p, ws, ws_bytes);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ev_begin(p, P2P_PHASE_TREE, s);
+    st = tree_build(p, pos, ws, s);
+    ev_end(p, P2P_PHASE_TREE, s);
+    return st;
+}
+
+int p2p_tree_import(p2p_plan* h, const int32_t* perm, const int32_t* box_start, int32_t n_boxes,
+                    const int32_t* nbr_start, const int32_t* nbr_idx, int32_t n_nbr, void* ws, size_t ws_bytes,
+                    void* stream) {
+    if (!h || !perm || !box_start || !nbr_start || !nbr_idx) return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    int st = check_ws(p, ws, ws_bytes);
+    if (st) return st;
+    if ((int64_t)n_boxes > p->box_cap) return P2P_ERR_INVALID_ARG;
+    return tree_import(p, perm, box_start, n_boxes, nbr_start, nbr_idx, n_nbr, ws, static_cast<cudaStream_t>(stream));
+}
+
+int p2p_restructure(p2p_plan* h, const float* pos, const void* strength, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || !pos || !strength || (reinterpret_cast<uintptr_t>(pos) & 3u)) return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    if ((reinterpret_cast<uintptr_t>(strength) & (p->kind == P2P_GRAVITY ? 3u : 7u)) != 0) return P2P_ERR_INVALID_ARG;
+    int st = check_ws(p, ws, ws_bytes);
+    if (st) return st;
+    if (!p->tree_ready) return P2P_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ev_begin(p, P2P_PHASE_RESTRUCTURE, s);
+    st = restructure(p, pos, strength, ws, s);
+    ev_end(p, P2P_PHASE_RESTRUCTURE, s);
+    return st;
+}
+
+int p2p_gravity(p2p_plan* h, float eps, float* phi, float* acc, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || !phi || !acc) return P2P_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(phi) & 3u) || (reinterpret_cast<uintptr_t>(acc) & 3u)) return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    if (p->kind != P2P_GRAVITY || !(eps >= 0.0f) || !(eps < 1.0e19f)) return P2P_ERR_INVALID_ARG;
+    int st = check_ws(p, ws, ws_bytes);
+    if (st) return st;
+    if (!p->tree_ready || !p->src_ready) return P2P_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ev_begin(p, P2P_PHASE_OPERATOR, s);
+    st = build_items(p, ws, s);
+    if (st) return st;
+    ev_begin(p, P2P_PHASE_KERNEL, s);
+    st = launch_gravity_kernel(p, loop_args(p, ws), at<int32_t>(ws, p->L.perm), eps, phi, acc, s);
+    if (st) return st;
+    ev_end(p, P2P_PHASE_KERNEL, s);
+    ev_end(p, P2P_PHASE_OPERATOR, s);
+    return P2P_OK;
+}
+
+int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || !u || (reinterpret_cast<uintptr_t>(u) & 7u)) return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    if (p->kind != P2P_HELMHOLTZ || !(k == k) || !(fabsf(k) < 1.0e30f)) return P2P_ERR_INVALID_ARG;
+    int st = check_ws(p, ws, ws_bytes);
+    if (st) return st;
+    if (!p->tree_ready || !p->src_ready) return P2P_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ev_begin(p, P2P_PHASE_OPERATOR, s);
+    st = build_items(p, ws, s);
+    if (st) return st;
+    ev_begin(p, P2P_PHASE_KERNEL, s);
+    st = launch_helmholtz_kernel(p, loop_args(p, ws), at<int32_t>(ws, p->L.perm), k, static_cast<float2*>(u), s);
+    if (st) return st;
+    ev_end(p, P2P_PHASE_KERNEL, s);
+    ev_end(p, P2P_PHASE_OPERATOR, s);
+    return P2P_OK;
+}
+
+int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t* capacity) {
+    if (!h || !offset_bytes || !capacity) return P2P_ERR_INVALID_ARG;
+    const Plan* p = &h->p;
+    const Layout& L = p->L;
+    const bool red = p->layout == P2P_LAYOUT_REDUNDANT;
+    switch (which) {
+        case P2P_ARR_PERM: *offset_bytes = L.perm; *capacity = p->n; break;
+        case P2P_ARR_BOX_KEY: *offset_bytes = L.box_key; *capacity = p->box_cap; break;
+        case P2P_ARR_BOX_START: *offset_bytes = L.box_start; *capacity = p->box_cap + 1; break;
+        case P2P_ARR_NBR_START: *offset_bytes = L.nbr_start; *capacity = p->box_cap + 1; break;
+        case P2P_ARR_NBR_IDX: *offset_bytes = L.nbr_idx; *capacity = 27 * p->box_cap; break;
+        case P2P_ARR_RED_START:
+            if (!red) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.red_start; *capacity = p->box_cap + 1; break;
+        case P2P_ARR_RED_SELF:
+            if (!red) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.red_self; *capacity = p->box_cap; break;
+        case P2P_ARR_GATHER_IDX:
+            if (!red || !(p->flags & P2P_PLAN_GATHER_MAP)) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.gather; *capacity = p->red_cap; break;
+        case P2P_ARR_SORTED_KEY: *offset_bytes = L.sorted_key; *capacity = p->n; break;
+        default: return P2P_ERR_INVALID_ARG;
+    }
+    return P2P_OK;
+}
+
+int p2p_read_counters(const p2p_plan* h, const void* ws, int64_t* out, void* stream) {
+    if (!h || !ws || !out) return P2P_ERR_INVALID_ARG;
+    Header hdr;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&hdr, static_cast<const char*>(ws) + h->p.L.header, sizeof(Header), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess)
+        return P2P_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return P2P_ERR_CUDA;
+    out[P2P_CTR_N_BOXES] = hdr.n_boxes;
+    out[P2P_CTR_N_NBR] = hdr.n_nbr;
+    out[P2P_CTR_FLAGS] = hdr.flags;
+    out[P2P_CTR_TOTAL_SRC] = hdr.total_src;
+    out[P2P_CTR_PAIRS] = (int64_t)hdr.pairs_nS - h->p.n;
+    out[P2P_CTR_N_ITEMS] = hdr.n_items;
+    if (hdr.flags & P2P_FLAG_TIMEOUT) return P2P_ERR_TIMEOUT;
+    if (hdr.flags & P2P_FLAG_DOMAIN) return P2P_ERR_DOMAIN;
+    if (hdr.flags & P2P_FLAG_CAPACITY) return P2P_ERR_INVALID_ARG;
+    return P2P_OK;
+}
+
+int p2p_plan_timing(p2p_plan* h, float* ms_out) {
+    if (!h || !ms_out) return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    for (int ph = 0; ph < P2P_PHASE_COUNT; ++ph) {
+        ms_out[ph] = -1.0f;
+        if (!p->timing || !p->ev_valid[ph]) continue;
+        if (cudaEventSynchronize(p->ev[ph][1]) != cudaSuccess) return P2P_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->ev[ph][0], p->ev[ph][1]) != cudaSuccess) return P2P_ERR_CUDA;
+        ms_out[ph] = ms;
+    }
+    return P2P_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "p2p_gb300.h"
+
+namespace p2p {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// workspace header (first 1 KiB of the workspace)
+// ---------------------------------------------------------------------------
+constexpr int kCostClasses = 64;
+
+struct Header {
+    // tree section (written by the tree build / import)
+    int32_t n_boxes;
+    int32_t n_nbr;
+    uint32_t flags;
+    int32_t total_src;                 // sum_b S_b (redundant records)
+    int32_t tree_pad[12];
+    // operator section (zeroed at the start of each operator call), offset 64
+    unsigned long long pairs_nS;       // sum_b n_b S_b
+    int32_t n_items;
+    uint32_t work_ctr;
+    int32_t cls_cnt[kCostClasses];
+    int32_t cls_cursor[kCostClasses];
+};
+constexpr size_t kHeaderBytes = 1024;
+constexpr size_t kOpSectionOffset = 64;
+static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
+static_assert(offsetof(Header, pairs_nS) == kOpSectionOffset, "header layout");
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+struct Layout {                        // byte offsets inside the workspace
+    size_t header, keys_a, keys_b, vals_a, perm, sorted_key, hist, scan_tmp, flags,
+        box_key, box_start, table, nbr_cnt, nbr_start, nbr_idx, src, box_S, red_start,
+        red_self, red_src, gather, items, total;
+};
+
+struct Plan {
+    int kind;
+    int64_t n;
+    int level;
+    float lo[3];
+    float edge;
+    float scale;                       // (float)2^level / edge
+    int nrhs;
+    int layout;
+    unsigned flags;
+    int64_t box_cap;                   // min(n, 8^level)
+    int64_t items_cap;
+    int64_t red_cap;                   // 27 n records
+    int rec_words;                     // 16-byte words per source record
+    int sort_tiles;
+    int use_table;                     // dense key -> box table (level <= 8)
+    // tuning
+    int tpl;                           // targets per lane
+    int tile;                          // source records per stage
+    int ctas_per_sm;
+    Layout L;
+    // state
+    int tree_ready;
+    int src_ready;
+    // timing
+    cudaEvent_t ev[P2P_PHASE_COUNT][2];
+    int ev_valid[P2P_PHASE_COUNT];
+    int timing;
+};
+
+// launch accounting
+void count_launch(int k = 1);
+
+// error helper
+#define P2P_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return P2P_ERR_CUDA;         \
+    } while (0)
+
+#define P2P_LAUNCH_CHECK()                                  \
+    do {                                                    \
+        ::p2p::count_launch();                              \
+        cudaError_t _e = cudaGetLastError();                \
+        if (_e != cudaSuccess) return P2P_ERR_CUDA;         \
+    } while (0)
+
+template <typename T>
+inline T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+inline int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// ---------------------------------------------------------------------------
+// phases implemented in the other translation units
+// ---------------------------------------------------------------------------
+
+// exclusive scan of int32 in[0..n_cap) (elements at index >= *d_len read as 0
+// when d_len != nullptr) into out[0..n_cap]; out[n_cap] (and out[len]) is the
+// total, also stored to *d_total when non-null.  in may alias out.
+size_t scan_scratch_bytes(int64_t n_cap);
+int scan_exclusive(const int32_t* in, int32_t* out, int64_t n_cap, const int32_t* d_len,
+                   int32_t* d_total, int32_t* scratch, cudaStream_t s);
+
+int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s);
+int tree_import(Plan* p, const int32_t* perm, const int32_t* box_start, int32_t n_boxes,
+                const int32_t* nbr_start, const int32_t* nbr_idx, int32_t n_nbr, void* ws,
+                cudaStream_t s);
+int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaStream_t s);
+int build_items(Plan* p, void* ws, cudaStream_t s);
+struct LoopArgs;
+int launch_gravity_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps, float* phi, float* acc,
+                          cudaStream_t s);
+int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, float2* u,
+                            cudaStream_t s);
+
+// records
+inline int helmholtz_rec_words(int nrhs) { return 1 + (nrhs + 1) / 2; }
+
+}  // namespace p2p

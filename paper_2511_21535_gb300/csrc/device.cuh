@@ -1,0 +1,126 @@
+// Device-side helpers: warp/block scans, Morton keys, mbarrier and 1-D bulk
+// copy (TMA) wrappers written as inline PTX for sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace p2p {
+
+// ---------------------------------------------------------------------------
+// Morton (Z-order) keys: bit b of x, y, z -> key bits 3b, 3b+1, 3b+2
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {   // 10 bits -> every third bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__device__ __forceinline__ uint32_t compact3(uint32_t v) {  // inverse of spread3
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030c30c3u;
+    v = (v | (v >> 4)) & 0x0300f00fu;
+    v = (v | (v >> 8)) & 0x030000ffu;
+    v = (v | (v >> 16)) & 0x000003ffu;
+    return v;
+}
+__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// ---------------------------------------------------------------------------
+// scans
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t warp_incl_scan(int32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan for blockDim.x == NT (multiple of 32, <= 1024).
+// Returns the exclusive prefix; *total receives the block total.
+template <int NT>
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* total) {
+    __shared__ int32_t warp_off[32];
+    __shared__ int32_t block_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t inc = warp_incl_scan(v);
+    if (lane == 31) warp_off[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = (lane < NT / 32) ? warp_off[lane] : 0;
+        int32_t wi = warp_incl_scan(w);
+        warp_off[lane] = wi - w;
+        if (lane == 31) block_total = wi;
+    }
+    __syncthreads();
+    int32_t res = warp_off[warp] + inc - v;
+    int32_t tot = block_total;
+    __syncthreads();  // the shared slots may be reused by the next call
+    *total = tot;
+    return res;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + 1-D bulk async copy (global -> shared)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+// make mbarrier initialisation visible to the async (TMA) proxy
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bytes must be a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Warp-uniform bounded wait on an mbarrier phase.  Returns false if the
+// iteration limit expired (the caller records P2P_FLAG_TIMEOUT).
+constexpr uint32_t kWaitLimit = 1u << 24;
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0;; ++it) {
+        bool done = mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, done)) return true;
+        if (it >= kWaitLimit) return false;
+    }
+}
+
+}  // namespace p2p

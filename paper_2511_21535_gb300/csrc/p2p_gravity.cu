@@ -1,0 +1,144 @@
+// Softened-gravity P2P kernel (stellar dynamics, Section 5.2):
+//   phi_i = - sum_{j in near(i), j != i} m_j (r^2 + eps^2)^(-1/2)
+//   a_i   =   sum_{j in near(i), j != i} m_j (x_j - x_i) (r^2 + eps^2)^(-3/2)
+// Per pair: 3 FADD, 3 FFMA, 1 MUFU rsqrt, 3 FMUL, 1 FADD, 3 FFMA -> the
+// kernel is bound by the FP32 pipe.  Each tile's partial sums are folded into
+// compensated (Kahan) accumulators unless the plan asks for plain FP32.
+#include "common.cuh"
+#include "p2p_loop.cuh"
+
+namespace p2p {
+
+template <int K, bool COMP>
+struct GravityOp {
+    const float4* __restrict__ rec;
+    const int32_t* __restrict__ perm;
+    float eps2;
+    float* __restrict__ phi;
+    float* __restrict__ acc;
+
+    float tx[K], ty[K], tz[K];
+    int self[K];
+    float s[K][4], c[K][4], p[K][4];
+    int tbase, nt;
+
+    __device__ __forceinline__ void begin(int tb, int ntg, int sw_lo, int lane) {
+        tbase = tb;
+        nt = ntg;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (l < nt) r = rec[tb + l];
+            tx[k] = r.x;
+            ty[k] = r.y;
+            tz[k] = r.z;
+            self[k] = (l < nt) ? sw_lo + l : -1;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s[k][o] = c[k][o] = p[k][o] = 0.f;
+        }
+    }
+
+    template <bool CHECK>
+    __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
+#pragma unroll 4
+        for (int j = 0; j < cnt; ++j) {
+            const float4 src = sm[j];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float dx = src.x - tx[k];
+                const float dy = src.y - ty[k];
+                const float dz = src.z - tz[k];
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                float m = src.w;
+                if (CHECK) {
+                    const bool me = (rec0 + j) == self[k];
+                    m = me ? 0.f : m;
+                    r2 = me ? 1.f : r2;
+                }
+                const float inv = rsqrtf(r2);
+                const float mi = m * inv;
+                const float mi3 = mi * (inv * inv);
+                float (&acc_k)[4] = COMP ? p[k] : s[k];
+                acc_k[0] += mi;
+                acc_k[1] = fmaf(mi3, dx, acc_k[1]);
+                acc_k[2] = fmaf(mi3, dy, acc_k[2]);
+                acc_k[3] = fmaf(mi3, dz, acc_k[3]);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void tile(const float4* sm, int cnt, int rec0, bool chk) {
+        if (chk) body<true>(sm, cnt, rec0);
+        else body<false>(sm, cnt, rec0);
+        if (COMP) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    kahan_add(s[k][o], c[k][o], p[k][o]);
+                    p[k][o] = 0.f;
+                }
+        }
+    }
+
+    __device__ __forceinline__ void end(int lane) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            if (l < nt) {
+                const int64_t o = perm[tbase + l];
+                phi[o] = -(s[k][0] - c[k][0]);
+                acc[3 * o + 0] = s[k][1] - c[k][1];
+                acc[3 * o + 1] = s[k][2] - c[k][2];
+                acc[3 * o + 2] = s[k][3] - c[k][3];
+            }
+        }
+    }
+};
+
+template <int K, bool COMP>
+__global__ void __launch_bounds__(kLoopThreads, 4)
+    k_gravity(LoopArgs a, const int32_t* __restrict__ perm, float eps2, float* __restrict__ phi,
+              float* __restrict__ acc) {
+    GravityOp<K, COMP> op;
+    op.rec = a.rec;
+    op.perm = perm;
+    op.eps2 = eps2;
+    op.phi = phi;
+    op.acc = acc;
+    warp_item_loop<K>(a, op);
+}
+
+template <int K, bool COMP>
+static int launch_gravity(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps2, float* phi, float* acc,
+                          cudaStream_t s) {
+    auto kern = k_gravity<K, COMP>;
+    const size_t smem = loop_smem_bytes(a.tile, a.words);
+    P2P_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = p->ctas_per_sm;
+    if (per_sm <= 0) {
+        P2P_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem));
+        if (per_sm < 1) per_sm = 1;
+    }
+    kern<<<num_sms() * per_sm, kLoopThreads, smem, s>>>(a, perm, eps2, phi, acc);
+    P2P_LAUNCH_CHECK();
+    return P2P_OK;
+}
+
+int launch_gravity_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps, float* phi, float* acc,
+                          cudaStream_t s) {
+    const float eps2 = eps * eps;
+    const bool comp = !(p->flags & P2P_PLAN_PLAIN_FP32);
+    switch (p->tpl) {
+        case 1: return comp ? launch_gravity<1, true>(p, a, perm, eps2, phi, acc, s)
+                            : launch_gravity<1, false>(p, a, perm, eps2, phi, acc, s);
+        case 2: return comp ? launch_gravity<2, true>(p, a, perm, eps2, phi, acc, s)
+                            : launch_gravity<2, false>(p, a, perm, eps2, phi, acc, s);
+        case 4: return comp ? launch_gravity<4, true>(p, a, perm, eps2, phi, acc, s)
+                            : launch_gravity<4, false>(p, a, perm, eps2, phi, acc, s);
+        default: return P2P_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace p2p

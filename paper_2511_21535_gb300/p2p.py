@@ -1,0 +1,260 @@
+"""Thin Python binding of the C ABI in ``include/p2p_gb300.h``.
+
+Argument marshalling only: every step of the operator runs in the CUDA
+library.  PyTorch provides device memory (the workspace and the outputs) and
+the stream (the current torch stream).  If the compiled library is missing
+the first call raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+GRAVITY, HELMHOLTZ = 0, 1
+LAYOUTS = {"indirect": 0, "redundant": 1}
+PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING = 0x1, 0x2, 0x4
+FLAG_DOMAIN, FLAG_TIMEOUT, FLAG_CAPACITY = 0x1, 0x2, 0x4
+
+ARRAYS = {"perm": (0, torch.int32), "box_key": (1, torch.int32), "box_start": (2, torch.int32),
+          "nbr_start": (3, torch.int32), "nbr_idx": (4, torch.int32), "red_start": (5, torch.int32),
+          "red_self": (6, torch.int32), "gather_idx": (7, torch.int32), "sorted_key": (8, torch.int32)}
+COUNTERS = ("n_boxes", "n_nbr", "flags", "total_src", "pairs", "n_items")
+PHASES = ("tree", "restructure", "kernel", "operator")
+
+EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_destroy",
+           "p2p_plan_workspace_bytes", "p2p_plan_set_tuning", "p2p_tree_build", "p2p_tree_import",
+           "p2p_restructure", "p2p_gravity", "p2p_helmholtz", "p2p_plan_array", "p2p_read_counters",
+           "p2p_plan_timing", "p2p_launch_count")
+
+
+class P2PError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load the compiled library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P, I, I64, F, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_uint
+    SZ = ctypes.c_size_t
+    sig = {
+        "p2p_status_string": (ctypes.c_char_p, [I]),
+        "p2p_abi_version": (I, []),
+        "p2p_plan_create": (I, [ctypes.POINTER(P), I, I64, I, P, F, I, I, U]),
+        "p2p_plan_destroy": (I, [P]),
+        "p2p_plan_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
+        "p2p_plan_set_tuning": (I, [P, I, I, I]),
+        "p2p_tree_build": (I, [P, P, P, SZ, P]),
+        "p2p_tree_import": (I, [P, P, P, ctypes.c_int32, P, P, ctypes.c_int32, P, SZ, P]),
+        "p2p_restructure": (I, [P, P, P, P, SZ, P]),
+        "p2p_gravity": (I, [P, F, P, P, P, SZ, P]),
+        "p2p_helmholtz": (I, [P, F, P, P, SZ, P]),
+        "p2p_plan_array": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "p2p_read_counters": (I, [P, P, ctypes.POINTER(I64), P]),
+        "p2p_plan_timing": (I, [P, ctypes.POINTER(F)]),
+        "p2p_launch_count": (I64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().p2p_status_string(int(status)).decode()
+    except ImportError:
+        return "library not loaded"
+
+
+def launch_count() -> int:
+    return int(load().p2p_launch_count())
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise P2PError(st, what)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """One problem shape (n, level, domain, kernel, layout) and its workspace.
+
+    The workspace is one torch uint8 tensor on the plan's device; every
+    intermediate array of the pipeline lives inside it.
+    """
+
+    def __init__(self, kind: str, n: int, level: int, lo, edge: float, nrhs: int = 1,
+                 layout: str = "redundant", gather_map: bool = False, plain_fp32: bool = False,
+                 timing: bool = False, device=None, workspace: torch.Tensor | None = None):
+        lib = load()
+        self.kind = kind
+        self.n = int(n)
+        self.nrhs = int(nrhs)
+        self.level = int(level)
+        self.layout = layout
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        flags = (PLAN_GATHER_MAP if gather_map else 0) | (PLAN_PLAIN_FP32 if plain_fp32 else 0) | \
+                (PLAN_TIMING if timing else 0)
+        lo_arr = (ctypes.c_float * 3)(*[float(v) for v in lo])
+        h = ctypes.c_void_p()
+        kid = {"gravity": GRAVITY, "helmholtz": HELMHOLTZ}[kind]
+        _check(lib.p2p_plan_create(ctypes.byref(h), kid, self.n, self.level, lo_arr, float(edge),
+                                   self.nrhs, LAYOUTS[layout], flags), "p2p_plan_create")
+        self._h = h
+        nb = ctypes.c_size_t()
+        _check(lib.p2p_plan_workspace_bytes(h, ctypes.byref(nb)), "p2p_plan_workspace_bytes")
+        self.ws_bytes = int(nb.value)
+        if workspace is None:
+            workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        elif workspace.numel() < self.ws_bytes:
+            raise ValueError("workspace too small")
+        self.ws = workspace
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.p2p_plan_destroy(h)
+            self._h = None
+
+    # -- knobs --------------------------------------------------------------
+    def set_tuning(self, targets_per_lane: int, tile: int, ctas_per_sm: int = 0):
+        _check(load().p2p_plan_set_tuning(self._h, targets_per_lane, tile, ctas_per_sm), "p2p_plan_set_tuning")
+
+    # -- pipeline -----------------------------------------------------------
+    def _wsp(self):
+        return ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_size_t(self.ws.numel())
+
+    def tree_build(self, pos: torch.Tensor, stream=None):
+        _need(pos, torch.float32, (self.n, 3), self.device)
+        w, b = self._wsp()
+        _check(load().p2p_tree_build(self._h, _ptr(pos), w, b, _stream(stream)), "p2p_tree_build")
+
+    def tree_import(self, perm, box_start, nbr_start, nbr_idx, stream=None):
+        nb = int(box_start.numel()) - 1
+        ne = int(nbr_idx.numel())
+        for t in (perm, box_start, nbr_start, nbr_idx):
+            _need(t, torch.int32, None, self.device)
+        w, b = self._wsp()
+        _check(load().p2p_tree_import(self._h, _ptr(perm), _ptr(box_start), nb, _ptr(nbr_start), _ptr(nbr_idx),
+                                      ne, w, b, _stream(stream)), "p2p_tree_import")
+
+    def restructure(self, pos: torch.Tensor, strength: torch.Tensor, stream=None):
+        _need(pos, torch.float32, (self.n, 3), self.device)
+        if self.kind == "gravity":
+            _need(strength, torch.float32, (self.n,), self.device)
+        else:
+            _need(strength, torch.complex64, (self.nrhs, self.n), self.device)
+        w, b = self._wsp()
+        _check(load().p2p_restructure(self._h, _ptr(pos), _ptr(strength), w, b, _stream(stream)),
+               "p2p_restructure")
+
+    def gravity(self, eps: float, phi=None, acc=None, stream=None):
+        if phi is None:
+            phi = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        if acc is None:
+            acc = torch.empty(self.n, 3, dtype=torch.float32, device=self.device)
+        _need(phi, torch.float32, (self.n,), self.device)
+        _need(acc, torch.float32, (self.n, 3), self.device)
+        w, b = self._wsp()
+        _check(load().p2p_gravity(self._h, float(eps), _ptr(phi), _ptr(acc), w, b, _stream(stream)), "p2p_gravity")
+        return phi, acc
+
+    def helmholtz(self, k: float, u=None, stream=None):
+        if u is None:
+            u = torch.empty(self.nrhs, self.n, dtype=torch.complex64, device=self.device)
+        _need(u, torch.complex64, (self.nrhs, self.n), self.device)
+        w, b = self._wsp()
+        _check(load().p2p_helmholtz(self._h, float(k), _ptr(u), w, b, _stream(stream)), "p2p_helmholtz")
+        return u
+
+    # -- inspection ---------------------------------------------------------
+    def counters(self, stream=None, check: bool = False) -> dict:
+        out = (ctypes.c_int64 * len(COUNTERS))()
+        st = load().p2p_read_counters(self._h, ctypes.c_void_p(self.ws.data_ptr()), out, _stream(stream))
+        res = {k: int(v) for k, v in zip(COUNTERS, out)}
+        res["status"] = int(st)
+        if check:
+            _check(st, "p2p_read_counters")
+        return res
+
+    def array(self, name: str, length: int | None = None) -> torch.Tensor:
+        """A view of a workspace array (first `length` elements)."""
+        which, dtype = ARRAYS[name]
+        off, cap = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().p2p_plan_array(self._h, which, ctypes.byref(off), ctypes.byref(cap)), "p2p_plan_array")
+        length = int(cap.value) if length is None else int(length)
+        nbytes = length * 4
+        return self.ws[off.value: off.value + nbytes].view(dtype)
+
+    def timing(self) -> dict:
+        out = (ctypes.c_float * len(PHASES))()
+        _check(load().p2p_plan_timing(self._h, out), "p2p_plan_timing")
+        return {k: float(v) for k, v in zip(PHASES, out)}
+
+
+def _need(t, dtype, shape, device):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if t.device != device:
+        raise ValueError(f"expected a tensor on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+
+
+# ---------------------------------------------------------------------------
+# one-call conveniences: tree -> restructure -> operator
+# ---------------------------------------------------------------------------
+
+def gravity(pos, mass, level, lo, edge, eps, layout="redundant", plan: Plan | None = None):
+    """Softened-gravity near field (phi [n], acc [n,3]) in original particle order."""
+    plan = plan or Plan("gravity", pos.shape[0], level, lo, edge, layout=layout, device=pos.device)
+    plan.tree_build(pos)
+    plan.restructure(pos, mass)
+    return plan.gravity(eps)
+
+
+def helmholtz(pos, q, level, lo, edge, k, layout="redundant", plan: Plan | None = None):
+    """Helmholtz near field u [nrhs, n] (complex64) in original particle order."""
+    if q.dim() == 1:
+        q = q.unsqueeze(0)
+    plan = plan or Plan("helmholtz", pos.shape[0], level, lo, edge, nrhs=q.shape[0], layout=layout,
+                        device=pos.device)
+    plan.tree_build(pos)
+    plan.restructure(pos, q.contiguous())
+    return plan.helmholtz(k)

@@ -1,0 +1,102 @@
+"""The C ABI library loads and exports every entry point declared in
+include/*.h; host-side argument checks (no GPU work)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2511_21535_gb300 import build as cuda_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(p2p_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = cuda_build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for required in ("p2p_plan_create", "p2p_tree_build", "p2p_restructure", "p2p_gravity",
+                     "p2p_helmholtz", "p2p_read_counters"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_export():
+    from paper_2511_21535_gb300 import p2p
+    assert set(declared_functions()) <= set(p2p.EXPORTS)
+
+
+def _create(lib, kind=0, n=1000, level=3, lo=(0.0, 0.0, 0.0), edge=1.0, nrhs=1, layout=1, flags=0):
+    h = ctypes.c_void_p()
+    lo_arr = (ctypes.c_float * 3)(*lo)
+    lib.p2p_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_float, ctypes.c_int, ctypes.c_int, ctypes.c_uint]
+    st = lib.p2p_plan_create(ctypes.byref(h), kind, n, level, ctypes.cast(lo_arr, ctypes.c_void_p), edge, nrhs,
+                             layout, flags)
+    return st, h
+
+
+def test_plan_argument_checks(lib):
+    bad = [dict(n=0), dict(n=(1 << 26) + 1), dict(level=0), dict(level=11), dict(edge=0.0), dict(edge=-1.0),
+           dict(kind=2), dict(layout=3), dict(nrhs=2), dict(kind=1, nrhs=0), dict(kind=1, nrhs=17),
+           dict(flags=0x100), dict(lo=(float("nan"), 0.0, 0.0))]
+    for kw in bad:
+        st, h = _create(lib, **kw)
+        assert st == 1, kw
+        assert not h.value
+    st, h = _create(lib)
+    assert st == 0 and h.value
+    lib.p2p_plan_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+    nb = ctypes.c_size_t()
+    assert lib.p2p_plan_workspace_bytes(h, ctypes.byref(nb)) == 0
+    assert nb.value > 27 * 1000 * 16          # holds the redundant streams
+    lib.p2p_plan_set_tuning.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    assert lib.p2p_plan_set_tuning(h, 3, 64, 0) == 1
+    assert lib.p2p_plan_set_tuning(h, 2, 48, 0) == 1
+    assert lib.p2p_plan_set_tuning(h, 4, 32, 2) == 0
+    # operator before the tree: state error is checked before any device work
+    lib.p2p_gravity.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    assert lib.p2p_gravity(h, 1e-3, 256, 256, 0, 0, None) == 7      # no workspace
+    lib.p2p_plan_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.p2p_plan_destroy(h) == 0
+    assert lib.p2p_plan_destroy(None) == 0
+
+
+def test_workspace_layout_scales(lib):
+    lib.p2p_plan_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+    sizes = {}
+    for layout in (0, 1):
+        st, h = _create(lib, n=100000, level=5, layout=layout)
+        nb = ctypes.c_size_t()
+        lib.p2p_plan_workspace_bytes(h, ctypes.byref(nb))
+        sizes[layout] = nb.value
+        lib.p2p_plan_destroy(h)
+    # the redundant layout reserves 27 n records (16 B) beyond the indirect one
+    assert sizes[1] - sizes[0] >= 27 * 100000 * 16
+
+
+def test_status_strings(lib):
+    lib.p2p_status_string.restype = ctypes.c_char_p
+    for s in range(9):
+        assert lib.p2p_status_string(s)
+    assert lib.p2p_abi_version() == 1

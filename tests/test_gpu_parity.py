@@ -1,0 +1,301 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Structures (permutation, box bounds, neighbour lists, redundant stream
+bounds, gather map) must be bit-exact; sums must meet the relative-L2
+tolerances: 1e-5 for float32 real outputs (phi and acc separately), 2e-5
+for complex64 outputs, against the FP64 oracle on the same inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_21535_gb300 import p2p
+from paper_2511_21535_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL_REAL = 1e-5
+TOL_COMPLEX = 2e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_gravity(prob, dev, layout, tpl=None, tile=None, plain=False, gather=True):
+    plan = p2p.Plan("gravity", prob.n, prob.level, prob.lo, prob.edge, layout=layout, gather_map=gather,
+                    plain_fp32=plain, device=dev)
+    if tpl:
+        plan.set_tuning(tpl, tile or 64)
+    pos = torch.from_numpy(prob.pos).to(dev)
+    m = torch.from_numpy(prob.strength).to(dev)
+    plan.tree_build(pos)
+    plan.restructure(pos, m)
+    phi, acc = plan.gravity(prob.eps)
+    torch.cuda.synchronize()
+    return plan, phi.cpu().numpy(), acc.cpu().numpy()
+
+
+def run_helmholtz(prob, dev, layout, tpl=None, tile=None, plain=False):
+    plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
+                    gather_map=True, plain_fp32=plain, device=dev)
+    if tpl:
+        plan.set_tuning(tpl, tile or 64)
+    pos = torch.from_numpy(prob.pos).to(dev)
+    q = torch.from_numpy(prob.strength).to(dev)
+    plan.tree_build(pos)
+    plan.restructure(pos, q)
+    u = plan.helmholtz(prob.k)
+    torch.cuda.synchronize()
+    return plan, u.cpu().numpy()
+
+
+def check_structures(plan, prob, layout):
+    ref = oracle.tree(prob.pos, prob.level, prob.lo, prob.edge)
+    c = plan.counters(check=True)
+    B, E = ref["n_boxes"], ref["n_nbr"]
+    assert c["n_boxes"] == B
+    assert c["n_nbr"] == E
+    np.testing.assert_array_equal(plan.array("perm", prob.n).cpu().numpy(), ref["perm"])
+    np.testing.assert_array_equal(plan.array("box_key", B).cpu().numpy().view(np.uint32), ref["box_key"])
+    np.testing.assert_array_equal(plan.array("box_start", B + 1).cpu().numpy(), ref["box_start"])
+    np.testing.assert_array_equal(plan.array("nbr_start", B + 1).cpu().numpy(), ref["nbr_start"])
+    np.testing.assert_array_equal(plan.array("nbr_idx", E).cpu().numpy(), ref["nbr_idx"])
+    _, key = oracle.cells(prob.pos, prob.level, prob.lo, prob.edge)
+    np.testing.assert_array_equal(plan.array("sorted_key", prob.n).cpu().numpy().view(np.uint32),
+                                  key[ref["perm"]])
+    assert c["pairs"] == oracle.pair_count(prob.pos, prob.level, prob.lo, prob.edge)
+    if layout == "redundant":
+        r = oracle.redundant(ref)
+        assert c["total_src"] == r["total"]
+        np.testing.assert_array_equal(plan.array("red_start", B + 1).cpu().numpy(), r["red_start"])
+        np.testing.assert_array_equal(plan.array("red_self", B).cpu().numpy(), r["red_self"])
+        np.testing.assert_array_equal(plan.array("gather_idx", r["total"]).cpu().numpy().view(np.uint32),
+                                      r["gather_idx"])
+
+
+# ---------------------------------------------------------------------------
+# structures
+# ---------------------------------------------------------------------------
+
+STRUCT_CASES = {
+    "uniform_8192_L3": lambda: wl.uniform_gravity(),
+    "uniform_1_L2": lambda: wl.uniform_gravity(n=1, level=2),
+    "uniform_37_L1": lambda: wl.uniform_gravity(n=37, level=1),
+    "uniform_50000_L9_bsearch": lambda: wl.uniform_gravity(n=50000, level=9),
+    "plummer_60000_L6": lambda: wl.plummer_gravity(n=60000, level=6, eps=1e-3),
+    "grid_24": lambda: wl.grid_helmholtz(edge_points=24),
+    "grid_16": lambda: wl.grid_helmholtz(edge_points=16),
+}
+
+
+@pytest.mark.parametrize("name", sorted(STRUCT_CASES))
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+def test_structures_bit_exact(dev, name, layout):
+    prob = STRUCT_CASES[name]()
+    if prob.kind == "gravity":
+        plan, _, _ = run_gravity(prob, dev, layout)
+    else:
+        plan, _ = run_helmholtz(prob, dev, layout)
+    check_structures(plan, prob, layout)
+
+
+def test_sort_many_radix_passes(dev):
+    # level 10 = 30-bit keys, 4 passes; heavy ties
+    rng = np.random.default_rng(9)
+    pos = (rng.integers(0, 64, (200000, 3)) / 64.0 + 1e-4).astype(np.float32)
+    prob = wl.Problem("ties", pos, np.ones(200000, np.float32), 10, (0.0, 0.0, 0.0), 1.0, "gravity", eps=1e-3)
+    plan = p2p.Plan("gravity", prob.n, 10, prob.lo, prob.edge, layout="indirect", device=dev)
+    plan.tree_build(torch.from_numpy(pos).to(dev))
+    ref = oracle.tree(pos, 10, prob.lo, prob.edge)
+    np.testing.assert_array_equal(plan.array("perm", prob.n).cpu().numpy(), ref["perm"])
+    assert plan.counters(check=True)["n_boxes"] == ref["n_boxes"]
+
+
+def test_domain_error_is_reported(dev):
+    prob = wl.uniform_gravity(n=1000, level=3)
+    pos = prob.pos.copy()
+    pos[17, 1] = 1.5
+    plan = p2p.Plan("gravity", prob.n, prob.level, prob.lo, prob.edge, device=dev)
+    plan.tree_build(torch.from_numpy(pos).to(dev))
+    c = plan.counters()
+    assert c["flags"] & p2p.FLAG_DOMAIN
+    assert c["status"] == 6
+    # the next build of valid positions clears the flag
+    plan.tree_build(torch.from_numpy(prob.pos).to(dev))
+    assert plan.counters(check=True)["flags"] == 0
+
+
+def test_operator_before_tree_is_a_state_error(dev):
+    plan = p2p.Plan("gravity", 100, 2, (0, 0, 0), 1.0, device=dev)
+    with pytest.raises(p2p.P2PError) as e:
+        plan.gravity(1e-3)
+    assert e.value.status == 8
+
+
+# ---------------------------------------------------------------------------
+# gravity sums
+# ---------------------------------------------------------------------------
+
+GRAV_CASES = {
+    "uniform_8192_L3": lambda: wl.uniform_gravity(),
+    "uniform_20000_L4": lambda: wl.uniform_gravity(n=20000, level=4, seed=3),
+    "plummer_60000_L6": lambda: wl.plummer_gravity(n=60000, level=6, eps=1e-3, seed=1),
+    "uniform_5_L1": lambda: wl.uniform_gravity(n=5, level=1),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAV_CASES))
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+@pytest.mark.parametrize("tpl,tile", [(1, 32), (2, 64), (4, 64)])
+def test_gravity_parity(dev, name, layout, tpl, tile):
+    prob = GRAV_CASES[name]()
+    _, phi, acc = run_gravity(prob, dev, layout, tpl, tile)
+    ophi, oacc, _ = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps)
+    assert np.all(np.isfinite(phi)) and np.all(np.isfinite(acc))
+    assert rel_l2(phi, ophi) <= TOL_REAL
+    assert rel_l2(acc, oacc) <= TOL_REAL
+
+
+def test_gravity_layouts_agree_bitwise(dev):
+    # both layouts visit sources in the same order with the same tile cuts
+    # only when ranges align; they must at least agree to rounding
+    prob = wl.plummer_gravity(n=40000, level=5, eps=1e-3, seed=2)
+    _, p1, a1 = run_gravity(prob, dev, "indirect")
+    _, p2, a2 = run_gravity(prob, dev, "redundant")
+    assert rel_l2(p1, p2) < 1e-6 and rel_l2(a1, a2) < 1e-6
+
+
+def test_gravity_deterministic(dev):
+    prob = wl.plummer_gravity(n=40000, level=5, eps=1e-3, seed=4)
+    _, p1, a1 = run_gravity(prob, dev, "redundant")
+    _, p2, a2 = run_gravity(prob, dev, "redundant")
+    np.testing.assert_array_equal(p1, p2)
+    np.testing.assert_array_equal(a1, a2)
+
+
+def test_gravity_momentum_invariant(dev):
+    prob = wl.plummer_gravity(n=60000, level=6, eps=1e-3, seed=5)
+    _, _, acc = run_gravity(prob, dev, "redundant")
+    f = torch.from_numpy(acc).to(dev, torch.float64) * torch.from_numpy(prob.strength).to(dev, torch.float64)[:, None]
+    tot = f.sum(dim=0).abs().max().item()
+    assert tot <= 1e-6 * f.abs().sum().item()
+
+
+def test_compensated_beats_plain(dev):
+    prob = wl.plummer_gravity(n=60000, level=5, eps=1e-3, seed=6)
+    ophi, oacc, _ = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps)
+    _, pc, ac = run_gravity(prob, dev, "redundant")
+    _, pp, ap = run_gravity(prob, dev, "redundant", plain=True)
+    ec, ep = rel_l2(pc, ophi), rel_l2(pp, ophi)
+    assert ec <= TOL_REAL and ep <= 1e-4
+    assert ec <= ep
+
+
+# ---------------------------------------------------------------------------
+# Helmholtz sums
+# ---------------------------------------------------------------------------
+
+def random_helmholtz(n, level, nrhs, seed, k=2 * math.pi):
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 3), dtype=np.float32)
+    q = wl.complex_normal((nrhs, n), rng)
+    return wl.Problem("random_helm", pos, q, level, (0.0, 0.0, 0.0), 1.0, "helmholtz", k=float(np.float32(k)))
+
+
+HELM_CASES = {
+    "grid16_r1": lambda: wl.grid_helmholtz(edge_points=16, nrhs=1),
+    "grid24_r2": lambda: wl.grid_helmholtz(edge_points=24, nrhs=2, seed=1),
+    "grid16_r8": lambda: wl.grid_helmholtz(edge_points=16, nrhs=8, seed=2),
+    "random_r3": lambda: random_helmholtz(20000, 4, 3, 7),
+    "random_r5": lambda: random_helmholtz(3000, 3, 5, 8, k=20.0),
+    "random_r16": lambda: random_helmholtz(2000, 2, 16, 9),
+}
+
+
+@pytest.mark.parametrize("name", sorted(HELM_CASES))
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+@pytest.mark.parametrize("tpl,tile", [(1, 32), (2, 64)])
+def test_helmholtz_parity(dev, name, layout, tpl, tile):
+    prob = HELM_CASES[name]()
+    _, u = run_helmholtz(prob, dev, layout, tpl, tile)
+    ou, _ = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k)
+    assert np.all(np.isfinite(u))
+    assert rel_l2(u, ou) <= TOL_COMPLEX
+
+
+def test_helmholtz_precise_phase_path(dev):
+    # boxes of edge 1/4 with k = 60: k * rmax ~ 52 > 32 selects the accurate sine/cosine
+    prob = random_helmholtz(4000, 2, 1, 11, k=60.0)
+    _, u = run_helmholtz(prob, dev, "redundant")
+    ou, _ = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k)
+    assert rel_l2(u, ou) <= TOL_COMPLEX
+
+
+def test_helmholtz_reciprocity_gpu(dev):
+    prob = wl.grid_helmholtz(edge_points=24, nrhs=2, seed=3)
+    _, u = run_helmholtz(prob, dev, "redundant")
+    a, b = prob.strength[0].astype(np.complex128), prob.strength[1].astype(np.complex128)
+    lhs = np.sum(b * u[0].astype(np.complex128))
+    rhs = np.sum(a * u[1].astype(np.complex128))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads (sampled where the oracle cannot do everything)
+# ---------------------------------------------------------------------------
+
+def test_uniform_gravity_full(dev):
+    prob = wl.uniform_gravity()
+    for layout in ("indirect", "redundant"):
+        plan, phi, acc = run_gravity(prob, dev, layout)
+        ophi, oacc, pairs = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps)
+        assert plan.counters(check=True)["pairs"] == pairs == 2732724
+        assert rel_l2(phi, ophi) <= TOL_REAL and rel_l2(acc, oacc) <= TOL_REAL
+
+
+def test_grid_helmholtz_64_full(dev):
+    prob = wl.grid_helmholtz()
+    ou, pairs = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k)
+    assert pairs == 398426112
+    for layout in ("indirect", "redundant"):
+        plan, u = run_helmholtz(prob, dev, layout)
+        assert plan.counters(check=True)["pairs"] == pairs
+        assert rel_l2(u, ou) <= TOL_COMPLEX
+
+
+def _sample_targets(prob, plan, count, seed):
+    """Random targets plus every target of the most occupied box."""
+    rng = np.random.default_rng(seed)
+    bs = plan.array("box_start", plan.counters()["n_boxes"] + 1).cpu().numpy()
+    occ = np.diff(bs)
+    b = int(np.argmax(occ))
+    perm = plan.array("perm", prob.n).cpu().numpy()
+    heavy = perm[bs[b]:bs[b + 1]]
+    return np.unique(np.concatenate([rng.choice(prob.n, count, replace=False), heavy]))
+
+
+def test_plummer_gravity_full_sampled(dev):
+    prob = wl.plummer_gravity()
+    for layout in ("indirect", "redundant"):
+        plan, phi, acc = run_gravity(prob, dev, layout, gather=False)
+        tg = _sample_targets(prob, plan, 3000, 0)
+        ophi, oacc, _ = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps, targets=tg)
+        assert rel_l2(phi[tg], ophi) <= TOL_REAL
+        assert rel_l2(acc[tg], oacc) <= TOL_REAL
+        c = plan.counters(check=True)
+        assert c["n_boxes"] == oracle.tree(prob.pos, prob.level, prob.lo, prob.edge)["n_boxes"]
+
+
+def test_grid_helmholtz_128_sampled(dev):
+    prob = wl.grid_helmholtz(edge_points=128, seed=5)
+    plan, u = run_helmholtz(prob, dev, "redundant")
+    assert plan.counters(check=True)["pairs"] == 3399974912
+    tg = np.random.default_rng(1).choice(prob.n, 4000, replace=False)
+    ou, _ = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k, targets=tg)
+    assert rel_l2(u[:, tg], ou) <= TOL_COMPLEX
