@@ -66,7 +66,7 @@ def workload_config(prob, layout):
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -88,7 +88,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -98,25 +98,30 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and active throttle reasons of the samples taken in
+        [t0, t1] (host time of the timed region); if fewer than 3 fall inside,
+        the 3 samples closest to the window's end are used and "window" says so."""
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        rows = []
+        for ts, ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        window = "timed"
+        sel = [r for r in rows if t0 is None or (t0 - 0.15 <= r[0] <= t1 + 0.15)]
+        if len(sel) < 3 and rows:
+            window = "nearest to the timed region"
+            sel = sorted(rows, key=lambda r: abs(r[0] - (t1 or r[0])))[:3]
+        if not sel:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = sorted({nm for r in sel for nm, v in zip(names, r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": max(r[2] for r in sel),
+                "reasons": reasons, "samples": len(sel), "window": window}
 
 
 # ---------------------------------------------------------------------------
@@ -134,7 +139,7 @@ def run_gpu(args, rank, world, local_rank):
     plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
                     timing=True, device=dev)
     if args.tpl:
-        plan.set_tuning(args.tpl, args.tile)
+        plan.set_tuning(args.tpl, args.tile, args.ctas)
     pos = torch.from_numpy(prob.pos).to(dev)
     strength = torch.from_numpy(prob.strength).to(dev)
     out_a = torch.empty(prob.n, dtype=torch.float32, device=dev)
@@ -151,6 +156,11 @@ def run_gpu(args, rank, world, local_rank):
         else:
             plan.helmholtz(prob.k, out_u)
 
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_id = vis.split(",")[local_rank].strip() if vis else str(local_rank)
+    clk = ClockSampler(smi_id).__enter__()
+    time.sleep(0.5)
+    pipes = p2p.measure_pipes()
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -167,18 +177,19 @@ def run_gpu(args, rank, world, local_rank):
     launches0 = p2p.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     phases = {k: [] for k in p2p.PHASES}
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    smi_id = vis.split(",")[local_rank].strip() if vis else str(local_rank)
-    with ClockSampler(smi_id) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-            t = plan.timing()      # waits for this step's events
-            for k, v in t.items():
-                phases[k].append(v)
-        torch.cuda.synchronize()
+    t_start = time.time()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        t = plan.timing()      # waits for this step's events
+        for k, v in t.items():
+            phases[k].append(v)
+    torch.cuda.synchronize()
+    t_end = time.time()
+    time.sleep(0.3)
+    clk.__exit__(None, None, None)
     launches = p2p.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
@@ -231,18 +242,19 @@ def run_gpu(args, rank, world, local_rank):
     e2e_mean = sum(e2e_ms) / len(e2e_ms)
 
     kern_ms = sum(phases["kernel"]) / len(phases["kernel"])
-    csum = clk.summary()
-    f_mhz = csum["sm_mhz"] or 2070.0
+    csum = clk.summary(t_start, t_end)
+    f_mhz = csum["sm_mhz"] or pipes["sm_mhz"] or 2070.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mufu_rate = min(pipes["mufu_rsqrt"], pipes["mufu_sin"])
     if prob.kind == "helmholtz" and prob.nrhs <= 2:
         pipe, per_pair = "mufu", 3.0        # rsqrt, sin, cos per geometric pair
-        peak = MUFU_PER_SM_CLK * sms * f_mhz * 1e6 / per_pair
+        peak = mufu_rate * sms * f_mhz * 1e6 / per_pair
     elif prob.kind == "helmholtz":
         pipe, per_pair = "fp32", 12.0 + 4.0 * prob.nrhs
-        peak = FP32_PER_SM_CLK * sms * f_mhz * 1e6 / per_pair
+        peak = pipes["fp32"] * sms * f_mhz * 1e6 / per_pair
     else:
         pipe, per_pair = "fp32", 13.0
-        peak = FP32_PER_SM_CLK * sms * f_mhz * 1e6 / per_pair
+        peak = pipes["fp32"] * sms * f_mhz * 1e6 / per_pair
     achieved = geo_pairs / (kern_ms * 1e-3)
     result = {
         "metric": METRIC,
@@ -262,7 +274,9 @@ def run_gpu(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
         "roofline": {"bound": "alu", "pipe": pipe, "kernel": f"k_{prob.kind}", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
-                     "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms, "peak_source": "nominal unit counts"},
+                     "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms,
+                     "peak_source": "pipe rates measured by p2p_measure_pipes x SMs x sampled SM clock",
+                     "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in pipes.items()}},
         "phases_ms": {k: (sum(v) / len(v) if v else None) for k, v in phases.items()},
         "pairs_per_step": pairs,
         "gpu_launches": launches,
@@ -299,10 +313,21 @@ def _oracle_eval(oracle, prob, tg):
 
 
 def cpu_baseline(prob, seconds):
+    """The oracle as it stands, on random target samples, repeated until ~`seconds` of CPU work."""
     import oracle
     pairs, dt, nt = oracle_sample(prob, seconds)
+    rng = np.random.default_rng(7)
+    reps = 1
+    while dt < seconds:
+        tg = rng.choice(prob.n, nt, replace=False)
+        t0 = time.perf_counter()
+        _, p = _oracle_eval(oracle, prob, tg)
+        dt += time.perf_counter() - t0
+        pairs += p
+        reps += 1
     return {"value": pairs / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle on {nt} random targets of the same workload ({pairs} pairs, {dt:.2f} s)"}
+            "sample": f"FP64 oracle, {reps} x {nt} random targets of the same workload "
+                      f"({pairs} pairs in {dt:.1f} s)"}
 
 
 def run_reference(args, rank, world):
@@ -341,13 +366,14 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="grid_helmholtz")
     ap.add_argument("--layout", default="redundant", choices=["redundant", "indirect"])
     ap.add_argument("--tpl", type=int, default=0)
     ap.add_argument("--tile", type=int, default=64)
+    ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

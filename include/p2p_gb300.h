@@ -252,6 +252,18 @@ int p2p_plan_timing(p2p_plan* plan, float* ms_out);
 /* Number of kernels this library has launched in this process (all plans). */
 int64_t p2p_launch_count(void);
 
+/*
+ * Measured peak rates of the pipes that bind the P2P kernels (a measurement
+ * utility, not part of the operator; it allocates its own small scratch and
+ * synchronises).  On the current device, one CTA of 1024 threads per SM runs
+ * independent chains of one instruction kind; host double out[4]:
+ *   out[0]  FP32 FFMA lane-operations per SM per clock
+ *   out[1]  MUFU rsqrt.approx lane-operations per SM per clock
+ *   out[2]  MUFU sin.approx lane-operations per SM per clock
+ *   out[3]  SM clock in MHz during the FFMA run (clock64 span / event time)
+ */
+int p2p_measure_pipes(double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ PHASES = ("tree", "restructure", "kernel", "operator")
 EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_destroy",
            "p2p_plan_workspace_bytes", "p2p_plan_set_tuning", "p2p_tree_build", "p2p_tree_import",
            "p2p_restructure", "p2p_gravity", "p2p_helmholtz", "p2p_plan_array", "p2p_read_counters",
-           "p2p_plan_timing", "p2p_launch_count")
+           "p2p_plan_timing", "p2p_launch_count", "p2p_measure_pipes")
 
 
 class P2PError(RuntimeError):
@@ -74,6 +74,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_read_counters": (I, [P, P, ctypes.POINTER(I64), P]),
         "p2p_plan_timing": (I, [P, ctypes.POINTER(F)]),
         "p2p_launch_count": (I64, []),
+        "p2p_measure_pipes": (I, [ctypes.POINTER(ctypes.c_double), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -92,6 +93,13 @@ def status_string(status: int) -> str:
 
 def launch_count() -> int:
     return int(load().p2p_launch_count())
+
+
+def measure_pipes(stream=None) -> dict:
+    """FP32 and MUFU lane-ops per SM per clock, and the SM clock (MHz), measured on the device."""
+    out = (ctypes.c_double * 4)()
+    _check(load().p2p_measure_pipes(out, _stream(stream)), "p2p_measure_pipes")
+    return {"fp32": out[0], "mufu_rsqrt": out[1], "mufu_sin": out[2], "sm_mhz": out[3]}
 
 
 def _check(st: int, what: str):
