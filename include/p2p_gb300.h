@@ -264,6 +264,36 @@ int64_t p2p_launch_count(void);
  */
 int p2p_measure_pipes(double* out, void* stream);
 
+/*
+ * Gravity near field for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a library convenience.
+ *
+ * Some callers cannot call cudaMalloc where they need the operator (code
+ * under an allocator that forbids new device allocations, a plugin given
+ * only its input and output buffers, a pre-planned sequence that must not
+ * gain allocation calls).  This entry point runs the same pipeline and
+ * kernels as p2p_tree_build + p2p_restructure + p2p_gravity, with all scratch
+ * in one fixed device array inside the library, and allocates nothing.
+ *   pos float32 [n][3], mass float32 [n]   inputs (device, original order)
+ *   phi float32 [n], acc float32 [n][3]    outputs (device, original order)
+ *   level, lo (host float[3]), edge, eps, layout as for p2p_plan_create /
+ *   p2p_gravity.
+ * Limits: n <= P2P_NOALLOC_MAX_N, level <= P2P_NOALLOC_MAX_LEVEL; larger
+ * requests return P2P_ERR_UNSUPPORTED without touching the device.  The
+ * scratch (P2P_NOALLOC_SCRATCH_BYTES) exists on every GPU that loads the
+ * library, until the process exits.
+ * The first call on a device looks up the scratch array's device address
+ * (one cudaGetSymbolAddress per device); make that first call before any
+ * stream capture.  Every call shares the one array and leaves its contents
+ * behind; the call clears what it needs.  Calls whose GPU work overlaps
+ * (different streams or host threads) race on the scratch.
+ */
+#define P2P_NOALLOC_MAX_N 8192
+#define P2P_NOALLOC_MAX_LEVEL 4
+#define P2P_NOALLOC_SCRATCH_BYTES (4718592)  /* 4.5 MiB */
+int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t n, int level, const float* lo,
+                        float edge, float eps, int layout, float* phi, float* acc, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ PHASES = ("tree", "restructure", "kernel", "operator")
 EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_destroy",
            "p2p_plan_workspace_bytes", "p2p_plan_set_tuning", "p2p_tree_build", "p2p_tree_import",
            "p2p_restructure", "p2p_gravity", "p2p_helmholtz", "p2p_plan_array", "p2p_read_counters",
-           "p2p_plan_timing", "p2p_launch_count", "p2p_measure_pipes")
+           "p2p_plan_timing", "p2p_launch_count", "p2p_gravity_noalloc",
+           "p2p_measure_pipes")
 
 
 class P2PError(RuntimeError):
@@ -74,6 +75,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_read_counters": (I, [P, P, ctypes.POINTER(I64), P]),
         "p2p_plan_timing": (I, [P, ctypes.POINTER(F)]),
         "p2p_launch_count": (I64, []),
+        "p2p_gravity_noalloc": (I, [P, P, I64, I, P, F, F, I, P, P, P]),
         "p2p_measure_pipes": (I, [ctypes.POINTER(ctypes.c_double), P]),
     }
     for name, (res, args) in sig.items():
