@@ -139,7 +139,7 @@ def run_gpu(args, rank, world, local_rank):
     plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
                     timing=True, device=dev)
     if args.tpl:
-        plan.set_tuning(args.tpl, args.tile, args.ctas)
+        plan.set_tuning(args.tpl, args.tile, args.ctas, args.group)
     pos = torch.from_numpy(prob.pos).to(dev)
     strength = torch.from_numpy(prob.strength).to(dev)
     out_a = torch.empty(prob.n, dtype=torch.float32, device=dev)
@@ -374,6 +374,7 @@ def main():
     ap.add_argument("--tpl", type=int, default=0)
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--ctas", type=int, default=0)
+    ap.add_argument("--group", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -130,12 +130,15 @@ int p2p_plan_workspace_bytes(const p2p_plan* plan, size_t* bytes);
 
 /*
  * Tuning knobs (the autotuner's search space, Section 3.5: threads per box
- * and redundancy grain).  targets_per_lane: 1, 2 or 4 targets held in
- * registers by each lane; a warp owns 32*targets_per_lane targets of one box.
- * tile: source records per shared-memory stage (32 or 64).  ctas_per_sm: 0 =
- * as many as fit.  Returns P2P_ERR_INVALID_ARG on values outside these sets.
+ * and redundancy grain).  targets_per_lane: 1, 2 or 4 (4: gravity only)
+ * targets held in registers by each lane; a work item is 32*targets_per_lane
+ * targets of one box.  tile: source records per shared-memory stage (32 or
+ * 64).  ctas_per_sm: 0 = as many as fit.  warps_per_item: 1, 2 or 4 warps
+ * share one item, splitting its source tiles and adding their partial sums
+ * in warp order.  Returns P2P_ERR_INVALID_ARG on values outside these sets.
  */
-int p2p_plan_set_tuning(p2p_plan* plan, int targets_per_lane, int tile, int ctas_per_sm);
+int p2p_plan_set_tuning(p2p_plan* plan, int targets_per_lane, int tile, int ctas_per_sm,
+                        int warps_per_item);
 
 /*
  * Collect, part 1 -- build the leaf-box structure from positions:

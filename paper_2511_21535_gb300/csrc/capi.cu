@@ -156,6 +156,7 @@ int p2p_plan_create(p2p_plan** out, int kind, int64_t n, int level, const float*
         p->tile = nrhs >= 4 ? 32 : 64;
     }
     p->ctas_per_sm = 0;
+    p->group = 4;
     p->items_cap = p->box_cap + (n + 31) / 32 + 1;
     compute_layout(p);
     p->timing = (flags & P2P_PLAN_TIMING) ? 1 : 0;
@@ -190,15 +191,18 @@ int p2p_plan_workspace_bytes(const p2p_plan* h, size_t* bytes) {
     return P2P_OK;
 }
 
-int p2p_plan_set_tuning(p2p_plan* h, int targets_per_lane, int tile, int ctas_per_sm) {
+int p2p_plan_set_tuning(p2p_plan* h, int targets_per_lane, int tile, int ctas_per_sm, int warps_per_item) {
     if (!h) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     const bool tpl_ok = targets_per_lane == 1 || targets_per_lane == 2 ||
                         (targets_per_lane == 4 && p->kind == P2P_GRAVITY);
-    if (!tpl_ok || (tile != 32 && tile != 64) || ctas_per_sm < 0 || ctas_per_sm > 32) return P2P_ERR_INVALID_ARG;
+    const bool g_ok = warps_per_item == 1 || warps_per_item == 2 || warps_per_item == 4;
+    if (!tpl_ok || !g_ok || (tile != 32 && tile != 64) || ctas_per_sm < 0 || ctas_per_sm > 32)
+        return P2P_ERR_INVALID_ARG;
     p->tpl = targets_per_lane;
     p->tile = tile;
     p->ctas_per_sm = ctas_per_sm;
+    p->group = warps_per_item;
     return P2P_OK;
 }
 
@@ -249,7 +253,7 @@ int p2p_gravity(p2p_plan* h, float eps, float* phi, float* acc, void* ws, size_t
     if (!p->tree_ready || !p->src_ready) return P2P_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ev_begin(p, P2P_PHASE_OPERATOR, s);
-    st = build_items(p, ws, s);
+    st = build_items(p, ws, 32 * p->tpl, s);
     if (st) return st;
     ev_begin(p, P2P_PHASE_KERNEL, s);
     st = launch_gravity_kernel(p, loop_args(p, ws), at<int32_t>(ws, p->L.perm), eps, phi, acc, s);
@@ -268,7 +272,7 @@ int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void
     if (!p->tree_ready || !p->src_ready) return P2P_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ev_begin(p, P2P_PHASE_OPERATOR, s);
-    st = build_items(p, ws, s);
+    st = build_items(p, ws, 32 * helmholtz_targets_per_lane(p, k), s);
     if (st) return st;
     ev_begin(p, P2P_PHASE_KERNEL, s);
     st = launch_helmholtz_kernel(p, loop_args(p, ws), at<int32_t>(ws, p->L.perm), k, static_cast<float2*>(u), s);

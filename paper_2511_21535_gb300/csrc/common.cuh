@@ -63,6 +63,7 @@ struct Plan {
     int tpl;                           // targets per lane
     int tile;                          // source records per stage
     int ctas_per_sm;
+    int group;                         // warps cooperating on one work item
     Layout L;
     // state
     int tree_ready;
@@ -120,7 +121,9 @@ int tree_import(Plan* p, const int32_t* perm, const int32_t* box_start, int32_t 
                 const int32_t* nbr_start, const int32_t* nbr_idx, int32_t n_nbr, void* ws,
                 cudaStream_t s);
 int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaStream_t s);
-int build_items(Plan* p, void* ws, cudaStream_t s);
+// work items of up to tt targets (tt = 32 * the kernel's targets per lane)
+int build_items(Plan* p, void* ws, int tt, cudaStream_t s);
+int helmholtz_targets_per_lane(const Plan* p, float k);
 struct LoopArgs;
 int launch_gravity_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps, float* phi, float* acc,
                           cudaStream_t s);

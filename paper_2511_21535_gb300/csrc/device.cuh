@@ -68,6 +68,32 @@ __device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* total) {
 }
 
 // ---------------------------------------------------------------------------
+// MUFU approximations, flush-to-zero forms (the kernels' arguments are normal
+// numbers: r^2 >= eps^2 or the squared distance of distinct points, and the
+// phase k r); the non-FTZ forms add denormal handling around each MUFU op
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// named barrier over `threads` threads (id 1..15; id 0 is __syncthreads)
+__device__ __forceinline__ void named_bar_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // mbarrier + 1-D bulk async copy (global -> shared)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -125,6 +125,7 @@ extern "C" int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t 
     p.tpl = 2;
     p.tile = 64;
     p.ctas_per_sm = 0;
+    p.group = 4;
     p.items_cap = p.box_cap + (n + 31) / 32 + 1;
     noalloc_layout(&p);
     if (p.L.total > (size_t)P2P_NOALLOC_SCRATCH_BYTES) return P2P_ERR_UNSUPPORTED;
@@ -137,7 +138,7 @@ extern "C" int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t 
     if (st) return st;
     st = restructure(&p, pos, mass, ws, s);
     if (st) return st;
-    st = build_items(&p, ws, s);
+    st = build_items(&p, ws, 32 * p.tpl, s);
     if (st) return st;
     LoopArgs a;
     a.rec = at<float4>(ws, p.L.src);

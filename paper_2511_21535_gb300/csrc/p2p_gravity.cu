@@ -11,6 +11,8 @@ namespace p2p {
 
 template <int K, bool COMP>
 struct GravityOp {
+    static constexpr int kOuts = 4 * K;   // floats per lane exchanged between cooperating warps
+
     const float4* __restrict__ rec;
     const int32_t* __restrict__ perm;
     float eps2;
@@ -56,7 +58,7 @@ struct GravityOp {
                     m = me ? 0.f : m;
                     r2 = me ? 1.f : r2;
                 }
-                const float inv = rsqrtf(r2);
+                const float inv = rsqrt_approx(r2);
                 const float mi = m * inv;
                 const float mi3 = mi * (inv * inv);
                 float (&acc_k)[4] = COMP ? p[k] : s[k];
@@ -82,6 +84,29 @@ struct GravityOp {
         }
     }
 
+    // partial exchange between the warps of a group: layout [value][lane]
+    __device__ __forceinline__ void store_partial(float* dst, int lane) const {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) dst[(k * 4 + o) * 32 + lane] = s[k][o] - c[k][o];
+    }
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                s[k][o] -= c[k][o];
+                c[k][o] = 0.f;
+            }
+    }
+    __device__ __forceinline__ void add_partial(const float* src, int lane) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s[k][o] += src[(k * 4 + o) * 32 + lane];
+    }
+
     __device__ __forceinline__ void end(int lane) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -97,7 +122,7 @@ struct GravityOp {
     }
 };
 
-template <int K, bool COMP>
+template <int K, int G, bool COMP>
 __global__ void __launch_bounds__(kLoopThreads, 4)
     k_gravity(LoopArgs a, const int32_t* __restrict__ perm, float eps2, float* __restrict__ phi,
               float* __restrict__ acc) {
@@ -107,14 +132,14 @@ __global__ void __launch_bounds__(kLoopThreads, 4)
     op.eps2 = eps2;
     op.phi = phi;
     op.acc = acc;
-    warp_item_loop<K>(a, op);
+    warp_item_loop<K, G>(a, op);
 }
 
-template <int K, bool COMP>
+template <int K, int G, bool COMP>
 static int launch_gravity(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps2, float* phi, float* acc,
                           cudaStream_t s) {
-    auto kern = k_gravity<K, COMP>;
-    const size_t smem = loop_smem_bytes(a.tile, a.words);
+    auto kern = k_gravity<K, G, COMP>;
+    const size_t smem = loop_smem_bytes(a.tile, a.words, GravityOp<K, COMP>::kOuts, G);
     P2P_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = p->ctas_per_sm;
     if (per_sm <= 0) {
@@ -126,17 +151,28 @@ static int launch_gravity(const Plan* p, const LoopArgs& a, const int32_t* perm,
     return P2P_OK;
 }
 
+template <int G>
+static int launch_gravity_g(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps2, float* phi, float* acc,
+                            bool comp, cudaStream_t s) {
+    switch (p->tpl) {
+        case 1: return comp ? launch_gravity<1, G, true>(p, a, perm, eps2, phi, acc, s)
+                            : launch_gravity<1, G, false>(p, a, perm, eps2, phi, acc, s);
+        case 2: return comp ? launch_gravity<2, G, true>(p, a, perm, eps2, phi, acc, s)
+                            : launch_gravity<2, G, false>(p, a, perm, eps2, phi, acc, s);
+        case 4: return comp ? launch_gravity<4, G, true>(p, a, perm, eps2, phi, acc, s)
+                            : launch_gravity<4, G, false>(p, a, perm, eps2, phi, acc, s);
+        default: return P2P_ERR_INVALID_ARG;
+    }
+}
+
 int launch_gravity_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps, float* phi, float* acc,
                           cudaStream_t s) {
     const float eps2 = eps * eps;
     const bool comp = !(p->flags & P2P_PLAN_PLAIN_FP32);
-    switch (p->tpl) {
-        case 1: return comp ? launch_gravity<1, true>(p, a, perm, eps2, phi, acc, s)
-                            : launch_gravity<1, false>(p, a, perm, eps2, phi, acc, s);
-        case 2: return comp ? launch_gravity<2, true>(p, a, perm, eps2, phi, acc, s)
-                            : launch_gravity<2, false>(p, a, perm, eps2, phi, acc, s);
-        case 4: return comp ? launch_gravity<4, true>(p, a, perm, eps2, phi, acc, s)
-                            : launch_gravity<4, false>(p, a, perm, eps2, phi, acc, s);
+    switch (p->group) {
+        case 1: return launch_gravity_g<1>(p, a, perm, eps2, phi, acc, comp, s);
+        case 2: return launch_gravity_g<2>(p, a, perm, eps2, phi, acc, comp, s);
+        case 4: return launch_gravity_g<4>(p, a, perm, eps2, phi, acc, comp, s);
         default: return P2P_ERR_INVALID_ARG;
     }
 }

@@ -1,16 +1,22 @@
 // The P2P compute loop shared by the gravity and Helmholtz kernels.
 //
-// Work unit: one warp owns one item = (target box b, up to 32*K of its
-// targets), K targets per lane held in registers.  The warp streams the
-// item's sources through a two-stage shared-memory ring filled by 1-D bulk
-// asynchronous copies (cp.async.bulk, the TMA engine) that one lane issues
-// while the warp computes the previous stage; an mbarrier per stage signals
-// arrival.  Sources are read as ranges of 16-byte records:
+// Work unit: one item = (target box b, up to 32*K of its targets), K targets
+// per lane held in registers, processed by a group of G warps (G = 1, 2 or
+// 4).  Every warp of the group holds the same targets; the item's source
+// tiles are dealt round-robin to the group's warps, and at the end the warps'
+// partial sums are added in warp order through shared memory (deterministic).
+// Several warps per item give the persistent grid several items per worker,
+// which is what keeps the SMs evenly loaded when items are few and equal.
+//
+// Each warp streams its tiles through a two-stage shared-memory ring filled
+// by 1-D bulk asynchronous copies (cp.async.bulk, the TMA engine) that one
+// lane issues while the warp computes the previous stage; an mbarrier per
+// stage signals arrival.  Sources are read as ranges of 16-byte records:
 //   redundant layout: one range, the box's contiguous stream (Section 5.2.1);
 //   indirect layout:  one range per neighbour box in the box-ordered array.
 // Items are taken from a global counter (persistent grid, longest-first
 // order prepared by the restructuring pass).  Outputs are owned by exactly
-// one warp, so no atomics touch results and the result does not depend on
+// one group, so no atomics touch results and the result does not depend on
 // the schedule.
 //
 // The self pair is excluded by identity: each target knows the record index
@@ -41,27 +47,64 @@ struct LoopArgs {
     Header* hdr;
 };
 
-inline size_t loop_smem_bytes(int tile, int words) {
-    return (size_t)kLoopWarps * (2 * (size_t)tile * words * 16 + kBarBytes);
+// dynamic shared memory: per warp two stages + mbarriers, then (G > 1) the
+// partial-sum exchange area of `outs` floats per lane
+inline size_t loop_smem_bytes(int tile, int words, int outs, int group) {
+    size_t b = (size_t)kLoopWarps * (2 * (size_t)tile * words * 16 + kBarBytes);
+    if (group > 1) b += (size_t)kLoopWarps * 32 * outs * sizeof(float);
+    return b;
 }
 
-template <int K, class Op>
+// position in the item's tile sequence: range r, offset o; (s, c) = range start/count
+struct TileCursor {
+    int r, o, s, c;
+    __device__ __forceinline__ void settle(int nr, int rs, int rc) {  // first non-empty range from r on
+        for (; r < nr; ++r) {
+            s = __shfl_sync(FULL, rs, r);
+            c = __shfl_sync(FULL, rc, r);
+            if (c > 0) break;
+        }
+    }
+    __device__ __forceinline__ void next(int nr, int rs, int rc, int tile) {
+        o += tile;
+        if (o >= c) {
+            o = 0;
+            ++r;
+            settle(nr, rs, rc);
+        }
+    }
+};
+
+template <int G>
+__device__ __forceinline__ void group_sync(int group) {
+    if (G == 1) __syncwarp();
+    else if (G == kLoopWarps) __syncthreads();
+    else named_bar_sync(1 + group, 32 * G);
+}
+
+template <int K, int G, class Op>
 __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
+    static_assert(G == 1 || G == 2 || G == 4, "group size");
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int item_slot[kLoopWarps];
+    __shared__ volatile int abort_flag[kLoopWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int group = warp / G, gw = warp % G;
     const uint32_t stage_bytes = (uint32_t)a.tile * a.words * 16u;
     unsigned char* wb = smem_raw + (size_t)warp * (2 * stage_bytes + kBarBytes);
     float4* stage0 = reinterpret_cast<float4*>(wb);
     float4* stage1 = reinterpret_cast<float4*>(wb + stage_bytes);
     uint64_t* bar = reinterpret_cast<uint64_t*>(wb + 2 * stage_bytes);
+    float* partial = reinterpret_cast<float*>(smem_raw + (size_t)kLoopWarps * (2 * stage_bytes + kBarBytes));
     if (lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
+        if (gw == 0) abort_flag[group] = 0;
     }
     __syncwarp();
 
-    if (a.hdr->flags & P2P_FLAG_CAPACITY) return;  // restructuring was skipped
+    if (a.hdr->flags & P2P_FLAG_CAPACITY) return;  // restructuring was skipped (uniform)
     const int32_t n_items = a.hdr->n_items;
     const bool redundant = a.red != nullptr;
     const float4* base = redundant ? a.red : a.rec;
@@ -69,8 +112,15 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
 
     for (;;) {
         int item = 0;
-        if (lane == 0) item = (int)atomicAdd(&a.hdr->work_ctr, 1u);
-        item = __shfl_sync(FULL, item, 0);
+        if (G == 1) {
+            if (lane == 0) item = (int)atomicAdd(&a.hdr->work_ctr, 1u);
+            item = __shfl_sync(FULL, item, 0);
+        } else {
+            if (gw == 0 && lane == 0) item_slot[group] = (int)atomicAdd(&a.hdr->work_ctr, 1u);
+            group_sync<G>(group);
+            item = item_slot[group];
+            if (abort_flag[group]) item = n_items;
+        }
         if (item >= n_items) break;
         const int2 it = a.items[item];
         const int b = it.x, t0 = it.y;
@@ -97,65 +147,63 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
         const int sw_lo = self_base + t0, sw_hi = sw_lo + nt;
         op.begin(bs + t0, nt, sw_lo, lane);
 
-        // producer and consumer cursors over (range, offset); empty ranges skipped
-        int p_r = 0, p_o = 0, p_s = 0, p_c = 0;
-        int c_r = 0, c_o = 0, c_s = 0, c_c = 0;
-        while (p_r < nr) {
-            p_s = __shfl_sync(FULL, rs, p_r);
-            p_c = __shfl_sync(FULL, rc, p_r);
-            if (p_c > 0) break;
-            ++p_r;
-        }
-        c_r = p_r; c_s = p_s; c_c = p_c;
+        // this warp's tiles: gw, gw + G, gw + 2G, ... of the item's tile sequence
+        TileCursor pc{0, 0, 0, 0};
+        pc.settle(nr, rs, rc);
+        for (int g = 0; g < gw && pc.r < nr; ++g) pc.next(nr, rs, rc, a.tile);
+        TileCursor cc = pc;
 
         auto issue = [&]() {
-            const int cnt = min(a.tile, p_c - p_o);
+            const int cnt = min(a.tile, pc.c - pc.o);
             const uint32_t bytes = (uint32_t)cnt * (uint32_t)a.words * 16u;
             const int st = pseq & 1;
             if (lane == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive_expect_tx(&bar[st], bytes);
-                bulk_g2s(st ? stage1 : stage0, base + (int64_t)(p_s + p_o) * a.words, bytes, &bar[st]);
+                bulk_g2s(st ? stage1 : stage0, base + (int64_t)(pc.s + pc.o) * a.words, bytes, &bar[st]);
             }
             ++pseq;
-            p_o += a.tile;
-            if (p_o >= p_c) {
-                p_o = 0;
-                for (++p_r; p_r < nr; ++p_r) {
-                    p_s = __shfl_sync(FULL, rs, p_r);
-                    p_c = __shfl_sync(FULL, rc, p_r);
-                    if (p_c > 0) break;
-                }
-            }
+            for (int g = 0; g < G && pc.r < nr; ++g) pc.next(nr, rs, rc, a.tile);
         };
 
-        if (p_r < nr) issue();
-        while (c_r < nr) {
-            if (p_r < nr) issue();
+        bool failed = false;
+        if (pc.r < nr) issue();
+        while (cc.r < nr) {
+            if (pc.r < nr) issue();
             const int st = cseq & 1;
             if (!warp_wait(&bar[st], (cseq >> 1) & 1)) {
-                // give up: flag, let copies in flight land (bounded), leave
-                if (lane == 0) atomicOr(&a.hdr->flags, P2P_FLAG_TIMEOUT);
-                for (uint32_t q = cseq; q < pseq; ++q) warp_wait(&bar[q & 1], (q >> 1) & 1);
-                return;
+                failed = true;
+                break;
             }
-            const int cnt = min(a.tile, c_c - c_o);
-            const int rec0 = c_s + c_o;
+            const int cnt = min(a.tile, cc.c - cc.o);
+            const int rec0 = cc.s + cc.o;
             const bool chk = rec0 < sw_hi && rec0 + cnt > sw_lo;
             op.tile(st ? stage1 : stage0, cnt, rec0, chk);
             __syncwarp();
             ++cseq;
-            c_o += a.tile;
-            if (c_o >= c_c) {
-                c_o = 0;
-                for (++c_r; c_r < nr; ++c_r) {
-                    c_s = __shfl_sync(FULL, rs, c_r);
-                    c_c = __shfl_sync(FULL, rc, c_r);
-                    if (c_c > 0) break;
-                }
-            }
+            for (int g = 0; g < G && cc.r < nr; ++g) cc.next(nr, rs, rc, a.tile);
         }
-        op.end(lane);
+        if (failed) {
+            // give up: flag, let copies in flight land (bounded), leave after this item
+            if (lane == 0) atomicOr(&a.hdr->flags, P2P_FLAG_TIMEOUT);
+            for (uint32_t q = cseq; q < pseq; ++q) warp_wait(&bar[q & 1], (q >> 1) & 1);
+            if (G == 1) return;
+            if (lane == 0) abort_flag[group] = 1;
+        }
+        if (G == 1) {
+            op.end(lane);
+        } else {
+            float* mine = partial + (size_t)warp * Op::kOuts * 32;
+            if (gw != 0) op.store_partial(mine, lane);
+            group_sync<G>(group);
+            if (gw == 0) {
+                op.fold();
+                for (int w = 1; w < G; ++w) op.add_partial(mine + (size_t)w * Op::kOuts * 32, lane);
+                op.end(lane);
+            }
+            group_sync<G>(group);
+            if (abort_flag[group]) return;
+        }
     }
 }
 

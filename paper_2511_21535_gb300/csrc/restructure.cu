@@ -213,11 +213,10 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
     return P2P_OK;
 }
 
-int build_items(Plan* p, void* ws, cudaStream_t s) {
+int build_items(Plan* p, void* ws, int tt, cudaStream_t s) {
     const Layout& L = p->L;
     Header* hdr = at<Header>(ws, L.header);
     const int64_t bc = p->box_cap;
-    const int tt = 32 * p->tpl;
     int32_t* S = at<int32_t>(ws, L.box_S);
     P2P_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(hdr) + kOpSectionOffset, 0,
                                  sizeof(Header) - kOpSectionOffset, s));

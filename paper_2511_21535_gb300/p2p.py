@@ -65,7 +65,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_plan_create": (I, [ctypes.POINTER(P), I, I64, I, P, F, I, I, U]),
         "p2p_plan_destroy": (I, [P]),
         "p2p_plan_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
-        "p2p_plan_set_tuning": (I, [P, I, I, I]),
+        "p2p_plan_set_tuning": (I, [P, I, I, I, I]),
         "p2p_tree_build": (I, [P, P, P, SZ, P]),
         "p2p_tree_import": (I, [P, P, P, ctypes.c_int32, P, P, ctypes.c_int32, P, SZ, P]),
         "p2p_restructure": (I, [P, P, P, P, SZ, P]),
@@ -159,8 +159,9 @@ class Plan:
             self._h = None
 
     # -- knobs --------------------------------------------------------------
-    def set_tuning(self, targets_per_lane: int, tile: int, ctas_per_sm: int = 0):
-        _check(load().p2p_plan_set_tuning(self._h, targets_per_lane, tile, ctas_per_sm), "p2p_plan_set_tuning")
+    def set_tuning(self, targets_per_lane: int, tile: int, ctas_per_sm: int = 0, warps_per_item: int = 4):
+        _check(load().p2p_plan_set_tuning(self._h, targets_per_lane, tile, ctas_per_sm, warps_per_item),
+               "p2p_plan_set_tuning")
 
     # -- pipeline -----------------------------------------------------------
     def _wsp(self):

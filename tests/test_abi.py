@@ -69,10 +69,11 @@ def test_plan_argument_checks(lib):
     nb = ctypes.c_size_t()
     assert lib.p2p_plan_workspace_bytes(h, ctypes.byref(nb)) == 0
     assert nb.value > 27 * 1000 * 16          # holds the redundant streams
-    lib.p2p_plan_set_tuning.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-    assert lib.p2p_plan_set_tuning(h, 3, 64, 0) == 1
-    assert lib.p2p_plan_set_tuning(h, 2, 48, 0) == 1
-    assert lib.p2p_plan_set_tuning(h, 4, 32, 2) == 0
+    lib.p2p_plan_set_tuning.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
+    assert lib.p2p_plan_set_tuning(h, 3, 64, 0, 1) == 1
+    assert lib.p2p_plan_set_tuning(h, 2, 48, 0, 1) == 1
+    assert lib.p2p_plan_set_tuning(h, 2, 64, 0, 3) == 1
+    assert lib.p2p_plan_set_tuning(h, 4, 32, 2, 4) == 0
     # operator before the tree: state error is checked before any device work
     lib.p2p_gravity.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]

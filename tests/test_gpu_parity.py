@@ -27,11 +27,11 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def run_gravity(prob, dev, layout, tpl=None, tile=None, plain=False, gather=True):
+def run_gravity(prob, dev, layout, tpl=None, tile=None, plain=False, gather=True, group=4):
     plan = p2p.Plan("gravity", prob.n, prob.level, prob.lo, prob.edge, layout=layout, gather_map=gather,
                     plain_fp32=plain, device=dev)
     if tpl:
-        plan.set_tuning(tpl, tile or 64)
+        plan.set_tuning(tpl, tile or 64, 0, group)
     pos = torch.from_numpy(prob.pos).to(dev)
     m = torch.from_numpy(prob.strength).to(dev)
     plan.tree_build(pos)
@@ -41,11 +41,11 @@ def run_gravity(prob, dev, layout, tpl=None, tile=None, plain=False, gather=True
     return plan, phi.cpu().numpy(), acc.cpu().numpy()
 
 
-def run_helmholtz(prob, dev, layout, tpl=None, tile=None, plain=False):
+def run_helmholtz(prob, dev, layout, tpl=None, tile=None, plain=False, group=4):
     plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
                     gather_map=True, plain_fp32=plain, device=dev)
     if tpl:
-        plan.set_tuning(tpl, tile or 64)
+        plan.set_tuning(tpl, tile or 64, 0, group)
     pos = torch.from_numpy(prob.pos).to(dev)
     q = torch.from_numpy(prob.strength).to(dev)
     plan.tree_build(pos)
@@ -152,10 +152,10 @@ GRAV_CASES = {
 
 @pytest.mark.parametrize("name", sorted(GRAV_CASES))
 @pytest.mark.parametrize("layout", ["indirect", "redundant"])
-@pytest.mark.parametrize("tpl,tile", [(1, 32), (2, 64), (4, 64)])
-def test_gravity_parity(dev, name, layout, tpl, tile):
+@pytest.mark.parametrize("tpl,tile,group", [(1, 32, 1), (2, 64, 2), (4, 64, 4), (2, 32, 4)])
+def test_gravity_parity(dev, name, layout, tpl, tile, group):
     prob = GRAV_CASES[name]()
-    _, phi, acc = run_gravity(prob, dev, layout, tpl, tile)
+    _, phi, acc = run_gravity(prob, dev, layout, tpl, tile, group=group)
     ophi, oacc, _ = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps)
     assert np.all(np.isfinite(phi)) and np.all(np.isfinite(acc))
     assert rel_l2(phi, ophi) <= TOL_REAL
@@ -220,19 +220,29 @@ HELM_CASES = {
 
 @pytest.mark.parametrize("name", sorted(HELM_CASES))
 @pytest.mark.parametrize("layout", ["indirect", "redundant"])
-@pytest.mark.parametrize("tpl,tile", [(1, 32), (2, 64)])
-def test_helmholtz_parity(dev, name, layout, tpl, tile):
+@pytest.mark.parametrize("tpl,tile,group", [(1, 32, 1), (2, 64, 2), (2, 64, 4), (1, 64, 4)])
+def test_helmholtz_parity(dev, name, layout, tpl, tile, group):
     prob = HELM_CASES[name]()
-    _, u = run_helmholtz(prob, dev, layout, tpl, tile)
+    _, u = run_helmholtz(prob, dev, layout, tpl, tile, group=group)
     ou, _ = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k)
     assert np.all(np.isfinite(u))
     assert rel_l2(u, ou) <= TOL_COMPLEX
 
 
-def test_helmholtz_precise_phase_path(dev):
+@pytest.mark.parametrize("group", [1, 4])
+def test_helmholtz_plain_fp32(dev, group):
+    prob = wl.grid_helmholtz(edge_points=24, nrhs=3, seed=6)
+    ou, _ = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k)
+    _, uc = run_helmholtz(prob, dev, "redundant", 2, 64, group=group)
+    _, up = run_helmholtz(prob, dev, "redundant", 2, 64, plain=True, group=group)
+    assert rel_l2(uc, ou) <= TOL_COMPLEX and rel_l2(up, ou) <= 1e-4
+
+
+@pytest.mark.parametrize("tpl,group", [(1, 1), (2, 4), (2, 2)])
+def test_helmholtz_precise_phase_path(dev, tpl, group):
     # boxes of edge 1/4 with k = 60: k * rmax ~ 52 > 32 selects the accurate sine/cosine
     prob = random_helmholtz(4000, 2, 1, 11, k=60.0)
-    _, u = run_helmholtz(prob, dev, "redundant")
+    _, u = run_helmholtz(prob, dev, "redundant", tpl, 64, group=group)
     ou, _ = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k)
     assert rel_l2(u, ou) <= TOL_COMPLEX
 
