@@ -6,5 +6,5 @@ code with the library.  See ``p2p_oracle.c`` for the definitions it follows.
 """
 from .oracle import (  # noqa: F401
     build, load, num_threads, morton, unmorton, cells, tree, redundant,
-    gravity, helmholtz, pair_count,
+    gravity, helmholtz, pair_count, helmholtz_adjoint, gravity_adjoint,
 )

@@ -50,8 +50,10 @@ def load():
         lib.orc_gravity.argtypes = [P, P, I64, I, P, F, F, P, I64, P, P, P]
         lib.orc_helmholtz.argtypes = [P, P, I, I64, I, P, F, F, P, I64, P, P]
         lib.orc_pair_count.argtypes = [P, I64, I, P, F, P]
+        lib.orc_helmholtz_adjoint.argtypes = [P, P, P, I, I64, I, P, F, F, P, P]
+        lib.orc_gravity_adjoint.argtypes = [P, P, P, P, I64, I, P, F, F, P, P]
         for f in ("orc_cells", "orc_tree", "orc_redundant", "orc_gravity", "orc_helmholtz",
-                  "orc_pair_count"):
+                  "orc_pair_count", "orc_helmholtz_adjoint", "orc_gravity_adjoint"):
             getattr(lib, f).restype = I
         _lib = lib
     return _lib
@@ -180,3 +182,32 @@ def pair_count(pos, level, lo, edge) -> int:
     _check(load().orc_pair_count(_p(pos), pos.shape[0], level, _p(lo), float(edge),
                                  ctypes.byref(p)), "pair_count")
     return p.value
+
+
+def helmholtz_adjoint(pos, q, gbar, level, lo, edge, k):
+    """(grad_q [nrhs, n] complex128, grad_x [n, 3] float64) for gbar = dL/du [nrhs, n]."""
+    pos = np.ascontiguousarray(pos, np.float32)
+    q = np.ascontiguousarray(np.atleast_2d(q), np.complex64)
+    gbar = np.ascontiguousarray(np.atleast_2d(gbar), np.complex64)
+    nrhs, n = q.shape
+    gq = np.zeros((nrhs, n, 2), np.float64)
+    gx = np.zeros((n, 3), np.float64)
+    lo = _lo(lo)
+    _check(load().orc_helmholtz_adjoint(_p(pos), _p(q.view(np.float32)), _p(gbar.view(np.float32)), nrhs, n, level,
+                                        _p(lo), float(edge), float(k), _p(gq), _p(gx)), "helmholtz_adjoint")
+    return gq[..., 0] + 1j * gq[..., 1], gx
+
+
+def gravity_adjoint(pos, mass, gphi, gacc, level, lo, edge, eps):
+    """(grad_m [n] float64, grad_x [n, 3] float64) for gphi = dL/dphi, gacc = dL/da."""
+    pos = np.ascontiguousarray(pos, np.float32)
+    mass = np.ascontiguousarray(mass, np.float32)
+    gphi = np.ascontiguousarray(gphi, np.float32)
+    gacc = np.ascontiguousarray(gacc, np.float32)
+    n = pos.shape[0]
+    gm = np.zeros(n, np.float64)
+    gx = np.zeros((n, 3), np.float64)
+    lo = _lo(lo)
+    _check(load().orc_gravity_adjoint(_p(pos), _p(mass), _p(gphi), _p(gacc), n, level, _p(lo), float(edge),
+                                      float(eps), _p(gm), _p(gx)), "gravity_adjoint")
+    return gm, gx

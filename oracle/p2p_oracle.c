@@ -386,3 +386,115 @@ int orc_pair_count(const float* pos, int64_t n, int level, const float* lo, floa
     orc_ctx_free(&c);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* adjoints (gradients of a real loss L through the P2P sums)                */
+/* ------------------------------------------------------------------------- */
+/*
+ * Convention: for a complex quantity z the gradient is dL/dRe z + i dL/dIm z.
+ * The DBIM solver of Section 5.1 is a gradient-based inverse-scattering loop;
+ * these are the gradients of the near-field operator it needs.
+ *
+ * Helmholtz, given gbar = dL/du ([nrhs][n] complex):
+ *   grad_q_k   = sum_{j in near(k), j != k} conj(G(x_k - x_j)) gbar_j
+ *   grad_x_k   = Re sum_{j in near(k), j != k} sum_r
+ *                  (conj(gbar_k) q_j + conj(gbar_j) q_k) grad G(x_k - x_j)
+ *   grad G(v)  = G(|v|) (i k - 1/|v|) v / |v|
+ * (u_i depends on x_k through the pairs (k, j) and (i, k); G is even and
+ *  grad G odd, so both pair orders collapse into one sum over k's neighbours.)
+ */
+int orc_helmholtz_adjoint(const float* pos, const float* q, const float* gbar, int nrhs, int64_t n,
+                          int level, const float* lo, float edge, float k, double* grad_q,
+                          double* grad_x) {
+    if (nrhs < 1) return ORC_ERR_ARG;
+    orc_ctx c;
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    if (st != ORC_OK) return st;
+    const double kk = (double)k;
+    const double inv4pi = 1.0 / (4.0 * ORC_PI);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < n; ++t) {
+        const int64_t i = t;
+        int32_t b = c.box_of[i];
+        double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int r = 0; r < nrhs; ++r) { grad_q[2 * (r * n + i)] = 0.0; grad_q[2 * (r * n + i) + 1] = 0.0; }
+        for (int32_t e = c.nbr_start[b]; e < c.nbr_start[b + 1]; ++e) {
+            int32_t nbox = c.nbr_idx[e];
+            for (int32_t s = c.box_start[nbox]; s < c.box_start[nbox + 1]; ++s) {
+                int64_t j = c.perm[s];
+                if (j == i) continue;
+                /* v = x_i - x_j */
+                double vx = xi - (double)pos[3 * j], vy = yi - (double)pos[3 * j + 1], vz = zi - (double)pos[3 * j + 2];
+                double r = sqrt(vx * vx + vy * vy + vz * vz);
+                double gre = cos(kk * r) * inv4pi / r, gim = sin(kk * r) * inv4pi / r;
+                /* dG/dr = G (i k - 1/r) */
+                double dre = -gre / r - kk * gim, dim = -gim / r + kk * gre;
+                double coef = 0.0;
+                for (int rr = 0; rr < nrhs; ++rr) {
+                    double qjr = q[2 * (rr * n + j)], qji = q[2 * (rr * n + j) + 1];
+                    double qir = q[2 * (rr * n + i)], qii = q[2 * (rr * n + i) + 1];
+                    double bjr = gbar[2 * (rr * n + j)], bji = gbar[2 * (rr * n + j) + 1];
+                    double bir = gbar[2 * (rr * n + i)], bii = gbar[2 * (rr * n + i) + 1];
+                    /* grad_q_i += conj(G) gbar_j */
+                    grad_q[2 * (rr * n + i)] += gre * bjr + gim * bji;
+                    grad_q[2 * (rr * n + i) + 1] += gre * bji - gim * bjr;
+                    /* A = conj(gbar_i) q_j + conj(gbar_j) q_i */
+                    double ar = bir * qjr + bii * qji + bjr * qir + bji * qii;
+                    double ai = bir * qji - bii * qjr + bjr * qii - bji * qir;
+                    coef += ar * dre - ai * dim;           /* Re(A dG/dr) */
+                }
+                gx += coef * vx / r; gy += coef * vy / r; gz += coef * vz / r;
+            }
+        }
+        grad_x[3 * i] = gx; grad_x[3 * i + 1] = gy; grad_x[3 * i + 2] = gz;
+    }
+    orc_ctx_free(&c);
+    return ORC_OK;
+}
+
+/*
+ * Softened gravity, given gphi = dL/dphi [n] and gacc = dL/da [n][3] (real):
+ * with d = x_j - x_k and h^2 = r^2 + eps^2,
+ *   grad_m_k = sum_{j in near(k), j != k} [ -gphi_j h^-1 - gacc_j . d h^-3 ]
+ *   grad_x_k = sum_{j in near(k), j != k} [ -h^-3 d (gphi_k m_j + gphi_j m_k)
+ *                                           + J(d) (m_k gacc_j - m_j gacc_k) ]
+ *   J(d) v   = h^-3 v - 3 h^-5 d (d . v)   (Jacobian of d h^-3)
+ */
+int orc_gravity_adjoint(const float* pos, const float* mass, const float* gphi, const float* gacc,
+                        int64_t n, int level, const float* lo, float edge, float eps,
+                        double* grad_m, double* grad_x) {
+    orc_ctx c;
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    if (st != ORC_OK) return st;
+    const double e2 = (double)eps * (double)eps;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n; ++k) {
+        int32_t b = c.box_of[k];
+        double xk = pos[3 * k], yk = pos[3 * k + 1], zk = pos[3 * k + 2];
+        double mk = mass[k], gpk = gphi[k];
+        double gak[3] = {gacc[3 * k], gacc[3 * k + 1], gacc[3 * k + 2]};
+        double gm = 0.0, gx[3] = {0.0, 0.0, 0.0};
+        for (int32_t e = c.nbr_start[b]; e < c.nbr_start[b + 1]; ++e) {
+            int32_t nbox = c.nbr_idx[e];
+            for (int32_t s = c.box_start[nbox]; s < c.box_start[nbox + 1]; ++s) {
+                int64_t j = c.perm[s];
+                if (j == k) continue;
+                double d[3] = {(double)pos[3 * j] - xk, (double)pos[3 * j + 1] - yk, (double)pos[3 * j + 2] - zk};
+                double h2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + e2;
+                double h1 = 1.0 / sqrt(h2), h3 = h1 / h2, h5 = h3 / h2;
+                double mj = mass[j], gpj = gphi[j];
+                double gaj[3] = {gacc[3 * j], gacc[3 * j + 1], gacc[3 * j + 2]};
+                gm += -gpj * h1 - (gaj[0] * d[0] + gaj[1] * d[1] + gaj[2] * d[2]) * h3;
+                double s1 = gpk * mj + gpj * mk;
+                double v[3] = {mk * gaj[0] - mj * gak[0], mk * gaj[1] - mj * gak[1], mk * gaj[2] - mj * gak[2]};
+                double dv = d[0] * v[0] + d[1] * v[1] + d[2] * v[2];
+                for (int a = 0; a < 3; ++a) gx[a] += -h3 * d[a] * s1 + h3 * v[a] - 3.0 * h5 * d[a] * dv;
+            }
+        }
+        grad_m[k] = gm;
+        grad_x[3 * k] = gx[0]; grad_x[3 * k + 1] = gx[1]; grad_x[3 * k + 2] = gx[2];
+    }
+    orc_ctx_free(&c);
+    return ORC_OK;
+}

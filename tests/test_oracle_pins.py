@@ -286,3 +286,103 @@ def test_grid_translation_invariance():
     a = u[4:8, 4:8, 4:8]
     for (z, y, x) in ((8, 8, 8), (4, 12, 8), (12, 4, 16)):
         np.testing.assert_allclose(u[z:z + 4, y:y + 4, x:x + 4], a, rtol=1e-6, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# adjoints: pinned by finite differences of the forward sums and by the
+# dot-product identity (not by re-deriving the adjoint formulas)
+# ---------------------------------------------------------------------------
+
+def lattice_points(n, level, seed, min_sep=0.04):
+    """Points on a 2^-16 lattice, at least min_sep apart and away from box faces,
+    so that +-2^-17 perturbations are exact in float32 and keep the tree."""
+    rng = np.random.default_rng(seed)
+    side = 1 << level
+    pts = []
+    while len(pts) < n:
+        p = rng.uniform(0.05, 0.95, 3)
+        cellpos = p * side - np.floor(p * side)
+        if np.any(cellpos < 0.01) or np.any(cellpos > 0.99):
+            continue
+        if pts and np.min(np.linalg.norm(np.array(pts) - p, axis=1)) < min_sep:
+            continue
+        pts.append(p)
+    return (np.round(np.array(pts) * 65536.0) / 65536.0).astype(np.float32)
+
+
+FD_DELTA = np.float32(2.0 ** -17)
+
+
+def test_helmholtz_adjoint_dot_product():
+    p = wl.grid_helmholtz(edge_points=16, nrhs=2, seed=11)
+    rng = np.random.default_rng(12)
+    y = wl.complex_normal((2, p.n), rng)
+    u, _ = oracle.helmholtz(p.pos, p.strength, p.level, p.lo, p.edge, p.k)
+    gq, _ = oracle.helmholtz_adjoint(p.pos, p.strength, y, p.level, p.lo, p.edge, p.k)
+    lhs = np.real(np.vdot(y.astype(np.complex128), u))       # Re <y, P q>
+    rhs = np.real(np.vdot(gq, p.strength.astype(np.complex128)))   # Re <P^H y, q>
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_helmholtz_adjoint_finite_differences(nrhs):
+    level, n = 2, 120
+    pos = lattice_points(n, level, 21 + nrhs)
+    rng = np.random.default_rng(5)
+    q = wl.complex_normal((nrhs, n), rng)
+    y = wl.complex_normal((nrhs, n), rng)
+    k = np.float32(2 * math.pi * 2.0)
+    gq, gx = oracle.helmholtz_adjoint(pos, q, y, level, (0, 0, 0), 1.0, k)
+
+    def loss(pp, qq):
+        u, _ = oracle.helmholtz(pp, qq, level, (0, 0, 0), 1.0, k)
+        return float(np.real(np.sum(np.conj(y.astype(np.complex128)) * u)))
+
+    for i in (0, 7, 55, 119):
+        for a in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, a] += FD_DELTA
+            pm[i, a] -= FD_DELTA
+            fd = (loss(pp, q) - loss(pm, q)) / (2 * float(FD_DELTA))
+            assert abs(fd - gx[i, a]) <= 1e-5 * max(1.0, np.abs(gx).max()), (i, a, fd, gx[i, a])
+    # L is linear in q: central differences in Re/Im q are exact up to rounding
+    for i in (3, 90):
+        for r in range(nrhs):
+            for unit in (1.0, 1j):
+                qp, qm = q.copy(), q.copy()
+                qp[r, i] += np.complex64(0.5 * unit)
+                qm[r, i] -= np.complex64(0.5 * unit)
+                step = complex(qp[r, i]) - complex(qm[r, i])       # the float32-rounded step
+                step = step.real if unit == 1.0 else step.imag
+                fd = (loss(pos, qp) - loss(pos, qm)) / step
+                ref = gq[r, i].real if unit == 1.0 else gq[r, i].imag
+                assert abs(fd - ref) <= 1e-10 * max(1.0, abs(ref))
+
+
+def test_gravity_adjoint_finite_differences():
+    level, n = 2, 150
+    pos = lattice_points(n, level, 31)
+    rng = np.random.default_rng(6)
+    mass = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    gphi = rng.standard_normal(n).astype(np.float32)
+    gacc = rng.standard_normal((n, 3)).astype(np.float32)
+    eps = np.float32(0.02)
+    gm, gx = oracle.gravity_adjoint(pos, mass, gphi, gacc, level, (0, 0, 0), 1.0, eps)
+
+    def loss(pp, mm):
+        phi, acc, _ = oracle.gravity(pp, mm, level, (0, 0, 0), 1.0, eps)
+        return float(np.sum(gphi.astype(np.float64) * phi) + np.sum(gacc.astype(np.float64) * acc))
+
+    for i in (0, 9, 77, 149):
+        for a in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, a] += FD_DELTA
+            pm[i, a] -= FD_DELTA
+            fd = (loss(pp, mass) - loss(pm, mass)) / (2 * float(FD_DELTA))
+            assert abs(fd - gx[i, a]) <= 1e-5 * max(1.0, np.abs(gx).max()), (i, a, fd, gx[i, a])
+        # linear in m: exact central difference with an exactly representable step
+        mp, mm_ = mass.copy(), mass.copy()
+        mp[i] += np.float32(0.25)
+        mm_[i] -= np.float32(0.25)
+        fd = (loss(pos, mp) - loss(pos, mm_)) / 0.5
+        assert abs(fd - gm[i]) <= 1e-9 * max(1.0, abs(gm[i]))
