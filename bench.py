@@ -31,6 +31,25 @@ sys.path.insert(0, ROOT)
 from paper_2511_21535_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "P2P pair-interactions/s"
+KERNEL_SOURCES = {"helmholtz": ["common.cuh", "device.cuh", "p2p_loop.cuh", "p2p_helmholtz.cuh", "p2p_helmholtz.cu"],
+                  "gravity": ["common.cuh", "device.cuh", "p2p_loop.cuh", "p2p_gravity.cu"]}
+
+
+def kernel_traffic(kind: str, workload: str, layout: str):
+    """DRAM bytes per launch from the committed ncu capture, if the kernel's
+    sources are unchanged since that capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "kernel_traffic.json")
+    try:
+        rec = json.load(open(path)).get(f"k_{kind}")
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("workload") != workload or rec.get("layout") != layout:
+        return None
+    h = hashlib.sha256()
+    for f in rec["source_files"]:
+        h.update(open(os.path.join(ROOT, "paper_2511_21535_gb300", "csrc", f), "rb").read())
+    return rec["dram_bytes_per_launch"] if h.hexdigest()[:16] == rec["source_hash"] else None
 L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
 MUFU_PER_SM_CLK = 16           # nominal XU (MUFU) throughput per SM per clock
 FP32_PER_SM_CLK = 128
@@ -148,14 +167,17 @@ def run_gpu(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        plan.tree_build(pos)
-        plan.restructure(pos, strength)
-        if prob.kind == "gravity":
-            plan.gravity(prob.eps, out_a, out_b)
-        else:
-            plan.helmholtz(prob.k, out_u)
+    def make_step(pl):
+        def step():
+            pl.tree_build(pos)
+            pl.restructure(pos, strength)
+            if prob.kind == "gravity":
+                pl.gravity(prob.eps, out_a, out_b)
+            else:
+                pl.helmholtz(prob.k, out_u)
+        return step
 
+    step = make_step(plan)
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     smi_id = vis.split(",")[local_rank].strip() if vis else str(local_rank)
     clk = ClockSampler(smi_id).__enter__()
@@ -169,6 +191,30 @@ def run_gpu(args, rank, world, local_rank):
     pairs = cnt["pairs"] * (prob.nrhs if prob.kind == "helmholtz" else 1)
     geo_pairs = cnt["pairs"]
 
+    # optionally capture the whole step (tree, restructuring, operator) in one CUDA graph
+    run, graph, graph_note, launches_per_replay = step, None, None, None
+    if args.graph:
+        try:
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                step()
+            stream.wait_stream(side)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            l0 = p2p.launch_count()
+            with torch.cuda.graph(graph):
+                step()
+            launches_per_replay = p2p.launch_count() - l0
+            for _ in range(args.warmup):
+                graph.replay()
+            torch.cuda.synchronize()
+            run = graph.replay
+            graph_note = "whole step captured in one CUDA graph"
+        except Exception as e:  # report and fall back to stream launches
+            graph, run = None, step
+            graph_note = f"graph capture failed: {type(e).__name__}: {e}"[:200]
+
     dist = world > 1
     if dist:
         import torch.distributed as td
@@ -181,16 +227,28 @@ def run_gpu(args, rank, world, local_rank):
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        step()
+        run()
         ev[i][1].record(stream)
-        t = plan.timing()      # waits for this step's events
-        for k, v in t.items():
-            phases[k].append(v)
+        if graph is None:
+            t = plan.timing()      # waits for this step's events
+            for k, v in t.items():
+                phases[k].append(v)
     torch.cuda.synchronize()
+    if graph is not None:
+        # event timing inside a graph replay is not available: phase times
+        # come from the same step launched on the stream, right after
+        for _ in range(min(args.steps, 50)):
+            flush.zero_()
+            step()
+            for k, v in plan.timing().items():
+                phases[k].append(v)
+        torch.cuda.synchronize()
     t_end = time.time()
     time.sleep(0.3)
     clk.__exit__(None, None, None)
     launches = p2p.launch_count() - launches0
+    if graph is not None:
+        launches = launches_per_replay * args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
     if dist:
@@ -273,13 +331,15 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": world * pairs / (e2e_mean * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
         "roofline": {"bound": "alu", "pipe": pipe, "kernel": f"k_{prob.kind}", "achieved": achieved / 1e9,
-                     "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak,
+                     "traffic": kernel_traffic(prob.kind, prob.name, layout),
                      "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms,
                      "peak_source": "pipe rates measured by p2p_measure_pipes x SMs x sampled SM clock",
                      "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in pipes.items()}},
         "phases_ms": {k: (sum(v) / len(v) if v else None) for k, v in phases.items()},
         "pairs_per_step": pairs,
         "gpu_launches": launches,
+        "graph": graph_note,
         "clocks": csum,
     }
     return result, prob
@@ -376,6 +436,7 @@ def main():
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--group", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -83,6 +83,7 @@ typedef enum { P2P_LAYOUT_INDIRECT = 0, P2P_LAYOUT_REDUNDANT = 1 } p2p_layout;
 #define P2P_PLAN_GATHER_MAP  0x1u  /* restructuring also writes the gather map      */
 #define P2P_PLAN_PLAIN_FP32  0x2u  /* plain FP32 accumulation (default: compensated) */
 #define P2P_PLAN_TIMING      0x4u  /* record CUDA events around each phase           */
+#define P2P_PLAN_ADJOINT     0x8u  /* size the workspace for the adjoint records     */
 
 /* device flag bits (p2p_read_counters: counters[P2P_CTR_FLAGS]) */
 #define P2P_FLAG_DOMAIN   0x1u     /* a position was outside the domain             */
@@ -194,6 +195,39 @@ int p2p_gravity(p2p_plan* plan, float eps, float* phi, float* acc, void* ws, siz
  * library routines.
  */
 int p2p_helmholtz(p2p_plan* plan, float k, void* u, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Adjoint of p2p_helmholtz: gradients of a real loss L given gbar = dL/du
+ * (complex convention: dL/dRe + i dL/dIm, as PyTorch).  Pair terms are
+ * recomputed (nothing from the forward call is reused but the tree):
+ *   grad_q_k   = sum_{j in near(k), j != k} conj(G(x_k - x_j)) gbar_j
+ *   grad_pos_k = Re sum_{j in near(k), j != k} sum_r (conj(gbar_k) q_j + conj(gbar_j) q_k)
+ *                   G (i k - 1/r) (x_k - x_j)/r,     r = |x_k - x_j|
+ * This is the gradient the DBIM inverse solver (Section 5.1) needs.
+ *   pos       float32 [n][3]; q complex64 [nrhs][n] (needed only for grad_pos)
+ *   gbar      complex64 [nrhs][n]
+ *   grad_q    complex64 [nrhs][n] or NULL;  grad_pos float32 [n][3] or NULL
+ * With grad_pos == NULL this is the forward operator with k -> -k on gbar.
+ * With grad_pos the plan must have P2P_PLAN_ADJOINT (else
+ * P2P_ERR_UNSUPPORTED).  Needs the tree; overwrites the restructured
+ * records, so run p2p_restructure again before the next p2p_helmholtz.
+ */
+int p2p_helmholtz_adjoint(p2p_plan* plan, float k, const float* pos, const void* q, const void* gbar,
+                          void* grad_q, float* grad_pos, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Adjoint of p2p_gravity, given grad_phi = dL/dphi [n] and grad_acc = dL/da
+ * [n][3] (float32): with d = x_j - x_k, h^2 = r^2 + eps^2,
+ *   grad_mass_k = sum_j [ -grad_phi_j h^-1 - (grad_acc_j . d) h^-3 ]
+ *   grad_pos_k  = sum_j [ -h^-3 d (grad_phi_k m_j + grad_phi_j m_k)
+ *                         + h^-3 v - 3 h^-5 d (d . v) ],  v = m_k grad_acc_j - m_j grad_acc_k
+ * over j in near(k), j != k.  grad_mass [n] / grad_pos [n][3] may be NULL
+ * (not both).  The plan must have P2P_PLAN_ADJOINT.  Needs the tree;
+ * overwrites the restructured records.
+ */
+int p2p_gravity_adjoint(p2p_plan* plan, float eps, const float* pos, const float* mass,
+                        const float* grad_phi, const float* grad_acc, float* grad_mass,
+                        float* grad_pos, void* ws, size_t ws_bytes, void* stream);
 
 /* identifiers of workspace arrays for p2p_plan_array */
 typedef enum {

@@ -43,13 +43,13 @@ static void compute_layout(Plan* p) {
     L.nbr_cnt = take(bc * 4);
     L.nbr_start = take((bc + 1) * 4);
     L.nbr_idx = take((size_t)27 * bc * 4);
-    L.src = take((size_t)n * p->rec_words * 16);
+    L.src = take((size_t)n * p->rec_alloc_words * 16);
     L.box_S = take((bc + 1) * 4);
     L.items = take((size_t)p->items_cap * 8);
     if (p->layout == P2P_LAYOUT_REDUNDANT) {
         L.red_start = take((bc + 1) * 4);
         L.red_self = take(bc * 4);
-        L.red_src = take((size_t)p->red_cap * p->rec_words * 16);
+        L.red_src = take((size_t)p->red_cap * p->rec_alloc_words * 16);
         L.gather = (p->flags & P2P_PLAN_GATHER_MAP) ? take((size_t)p->red_cap * 4) : 0;
     } else {
         L.red_start = L.red_self = L.red_src = L.gather = 0;
@@ -72,13 +72,14 @@ static void ev_end(Plan* p, int ph, cudaStream_t s) {
     }
 }
 
-static LoopArgs loop_args(const Plan* p, void* ws) {
+static LoopArgs loop_args(const Plan* p, void* ws, int words) {
     const Layout& L = p->L;
     LoopArgs a;
     a.rec = at<float4>(ws, L.src);
     a.red = (p->layout == P2P_LAYOUT_REDUNDANT) ? at<float4>(ws, L.red_src) : nullptr;
-    a.words = p->rec_words;
-    a.tile = p->tile;
+    a.words = words;
+    // wide adjoint records: keep a stage within ~2.5 KB
+    a.tile = (words * p->tile > 160) ? 32 : p->tile;
     a.box_start = at<int32_t>(ws, L.box_start);
     a.nbr_start = at<int32_t>(ws, L.nbr_start);
     a.nbr_idx = at<int32_t>(ws, L.nbr_idx);
@@ -127,7 +128,8 @@ int p2p_plan_create(p2p_plan** out, int kind, int64_t n, int level, const float*
     if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT) return P2P_ERR_INVALID_ARG;
     if (kind == P2P_GRAVITY && nrhs != 1) return P2P_ERR_INVALID_ARG;
     if (nrhs < 1 || nrhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
-    if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING)) return P2P_ERR_INVALID_ARG;
+    if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING | P2P_PLAN_ADJOINT))
+        return P2P_ERR_INVALID_ARG;
     p2p_plan* h = new (std::nothrow) p2p_plan;
     if (!h) return P2P_ERR_OOM;
     Plan* p = &h->p;
@@ -145,6 +147,9 @@ int p2p_plan_create(p2p_plan** out, int kind, int64_t n, int level, const float*
     p->box_cap = n < boxes ? n : boxes;
     p->red_cap = 27 * n;
     p->rec_words = (kind == P2P_GRAVITY) ? 1 : helmholtz_rec_words(nrhs);
+    p->rec_alloc_words = p->rec_words;
+    if (flags & P2P_PLAN_ADJOINT)
+        p->rec_alloc_words = (kind == P2P_GRAVITY) ? kGravityAdjointWords : helmholtz_adjoint_words(nrhs);
     p->sort_tiles = (int)((n + 2047) / 2048);
     p->use_table = level <= 8;
     // defaults; p2p_plan_set_tuning / the autotuner may change them
@@ -256,7 +261,7 @@ int p2p_gravity(p2p_plan* h, float eps, float* phi, float* acc, void* ws, size_t
     st = build_items(p, ws, 32 * p->tpl, s);
     if (st) return st;
     ev_begin(p, P2P_PHASE_KERNEL, s);
-    st = launch_gravity_kernel(p, loop_args(p, ws), at<int32_t>(ws, p->L.perm), eps, phi, acc, s);
+    st = launch_gravity_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), eps, phi, acc, s);
     if (st) return st;
     ev_end(p, P2P_PHASE_KERNEL, s);
     ev_end(p, P2P_PHASE_OPERATOR, s);
@@ -275,11 +280,67 @@ int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void
     st = build_items(p, ws, 32 * helmholtz_targets_per_lane(p, k), s);
     if (st) return st;
     ev_begin(p, P2P_PHASE_KERNEL, s);
-    st = launch_helmholtz_kernel(p, loop_args(p, ws), at<int32_t>(ws, p->L.perm), k, static_cast<float2*>(u), s);
+    st = launch_helmholtz_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), k, static_cast<float2*>(u), s);
     if (st) return st;
     ev_end(p, P2P_PHASE_KERNEL, s);
     ev_end(p, P2P_PHASE_OPERATOR, s);
     return P2P_OK;
+}
+
+int p2p_helmholtz_adjoint(p2p_plan* h, float k, const float* pos, const void* q, const void* gbar, void* grad_q,
+                          float* grad_pos, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || !pos || !gbar || (!grad_q && !grad_pos)) return P2P_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(gbar) & 7u) || (reinterpret_cast<uintptr_t>(grad_q) & 7u) ||
+        (reinterpret_cast<uintptr_t>(grad_pos) & 3u) || (reinterpret_cast<uintptr_t>(pos) & 3u))
+        return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    if (p->kind != P2P_HELMHOLTZ || !(k == k) || !(fabsf(k) < 1.0e30f)) return P2P_ERR_INVALID_ARG;
+    int st = check_ws(p, ws, ws_bytes);
+    if (st) return st;
+    if (!p->tree_ready) return P2P_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!grad_pos) {
+        // grad_q = conj(P) gbar = P(-k) gbar: the forward operator on gbar
+        st = restructure(p, pos, gbar, ws, s);
+        if (st) return st;
+        st = build_items(p, ws, 32 * helmholtz_targets_per_lane(p, -k), s);
+        if (st) return st;
+        st = launch_helmholtz_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), -k,
+                                     static_cast<float2*>(grad_q), s);
+        p->src_ready = 0;   // the records hold gbar, not the forward sources
+        return st;
+    }
+    if (!q || (reinterpret_cast<uintptr_t>(q) & 7u)) return P2P_ERR_INVALID_ARG;
+    int words = 0;
+    st = restructure_adjoint(p, pos, q, gbar, nullptr, ws, &words, s);
+    if (st) return st;
+    st = build_items(p, ws, 32, s);
+    if (st) return st;
+    return launch_helmholtz_adjoint_kernel(p, loop_args(p, ws, words), at<int32_t>(ws, p->L.perm), k,
+                                           helmholtz_needs_precise(p, k), static_cast<float2*>(grad_q), grad_pos, s);
+}
+
+int p2p_gravity_adjoint(p2p_plan* h, float eps, const float* pos, const float* mass, const float* grad_phi,
+                        const float* grad_acc, float* grad_mass, float* grad_pos, void* ws, size_t ws_bytes,
+                        void* stream) {
+    if (!h || !pos || !mass || !grad_phi || !grad_acc || (!grad_mass && !grad_pos)) return P2P_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(pos) | reinterpret_cast<uintptr_t>(mass) | reinterpret_cast<uintptr_t>(grad_phi) |
+         reinterpret_cast<uintptr_t>(grad_acc) | reinterpret_cast<uintptr_t>(grad_mass) |
+         reinterpret_cast<uintptr_t>(grad_pos)) & 3u)
+        return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    if (p->kind != P2P_GRAVITY || !(eps >= 0.0f) || !(eps < 1.0e19f)) return P2P_ERR_INVALID_ARG;
+    int st = check_ws(p, ws, ws_bytes);
+    if (st) return st;
+    if (!p->tree_ready) return P2P_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int words = 0;
+    st = restructure_adjoint(p, pos, mass, grad_phi, grad_acc, ws, &words, s);
+    if (st) return st;
+    st = build_items(p, ws, 32 * gravity_adjoint_targets_per_lane(p), s);
+    if (st) return st;
+    return launch_gravity_adjoint_kernel(p, loop_args(p, ws, words), at<int32_t>(ws, p->L.perm), eps, grad_mass,
+                                         grad_pos, s);
 }
 
 int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t* capacity) {

@@ -16,23 +16,27 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kCostClasses = 64;
 
 struct Header {
-    // tree section (written by the tree build / import)
+    // tree section (written by the tree build / import), offset 0
     int32_t n_boxes;
     int32_t n_nbr;
     uint32_t flags;
-    int32_t total_src;                 // sum_b S_b (redundant records)
-    int32_t tree_pad[12];
-    // operator section (zeroed at the start of each operator call), offset 64
+    int32_t tree_pad[13];
+    // restructuring section (zeroed at the start of each restructuring), offset 64
     unsigned long long pairs_nS;       // sum_b n_b S_b
+    int32_t total_src;                 // sum_b S_b (redundant records)
+    int32_t restr_pad[13];
+    // operator section (zeroed at the start of each operator call), offset 128
     int32_t n_items;
     uint32_t work_ctr;
     int32_t cls_cnt[kCostClasses];
     int32_t cls_cursor[kCostClasses];
 };
 constexpr size_t kHeaderBytes = 1024;
-constexpr size_t kOpSectionOffset = 64;
+constexpr size_t kRestrSectionOffset = 64;
+constexpr size_t kOpSectionOffset = 128;
 static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
-static_assert(offsetof(Header, pairs_nS) == kOpSectionOffset, "header layout");
+static_assert(offsetof(Header, pairs_nS) == kRestrSectionOffset, "header layout");
+static_assert(offsetof(Header, n_items) == kOpSectionOffset, "header layout");
 
 // ---------------------------------------------------------------------------
 // plan
@@ -56,7 +60,8 @@ struct Plan {
     int64_t box_cap;                   // min(n, 8^level)
     int64_t items_cap;
     int64_t red_cap;                   // 27 n records
-    int rec_words;                     // 16-byte words per source record
+    int rec_words;                     // 16-byte words per source record (forward)
+    int rec_alloc_words;               // words per record the workspace holds (>= adjoint records)
     int sort_tiles;
     int use_table;                     // dense key -> box table (level <= 8)
     // tuning
@@ -116,15 +121,27 @@ size_t scan_scratch_bytes(int64_t n_cap);
 int scan_exclusive(const int32_t* in, int32_t* out, int64_t n_cap, const int32_t* d_len,
                    int32_t* d_total, int32_t* scratch, cudaStream_t s);
 
+struct LoopArgs;
 int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s);
 int tree_import(Plan* p, const int32_t* perm, const int32_t* box_start, int32_t n_boxes,
                 const int32_t* nbr_start, const int32_t* nbr_idx, int32_t n_nbr, void* ws,
                 cudaStream_t s);
 int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaStream_t s);
+// adjoint records: Helmholtz [pos | q | gbar] (a = q, b = gbar), gravity [pos m | gphi gacc]
+// (a = mass, b = grad_phi, c = grad_acc); returns the record width in words via *words
+int restructure_adjoint(Plan* p, const float* pos, const void* a, const void* b, const void* c, void* ws,
+                        int* words, cudaStream_t s);
+int launch_helmholtz_adjoint_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, bool precise,
+                                    float2* grad_q, float* grad_x, cudaStream_t s);
+int launch_gravity_adjoint_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps, float* grad_m,
+                                  float* grad_x, cudaStream_t s);
+int gravity_adjoint_targets_per_lane(const Plan* p);
+bool helmholtz_needs_precise(const Plan* p, float k);
+inline int helmholtz_adjoint_words(int nrhs) { return 1 + 2 * ((nrhs + 1) / 2); }
+constexpr int kGravityAdjointWords = 2;
 // work items of up to tt targets (tt = 32 * the kernel's targets per lane)
 int build_items(Plan* p, void* ws, int tt, cudaStream_t s);
 int helmholtz_targets_per_lane(const Plan* p, float k);
-struct LoopArgs;
 int launch_gravity_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps, float* phi, float* acc,
                           cudaStream_t s);
 int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, float2* u,

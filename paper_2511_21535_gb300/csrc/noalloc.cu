@@ -120,6 +120,7 @@ extern "C" int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t 
     p.box_cap = n < boxes ? n : boxes;
     p.red_cap = 27 * n;
     p.rec_words = 1;
+    p.rec_alloc_words = 1;
     p.sort_tiles = (int)((n + 2047) / 2048);
     p.use_table = 1;
     p.tpl = 2;

@@ -32,7 +32,7 @@ int launch_helm_fast(const Plan* p, const LoopArgs& a, const int32_t* perm, floa
 // this range); beyond it the accurate library routine is used.
 constexpr float kFastPhaseMax = 32.0f;
 
-static bool needs_precise(const Plan* p, float k) {
+bool helmholtz_needs_precise(const Plan* p, float k) {
     const float box = p->edge / (float)(1 << p->level);
     const float rmax = 2.0f * box * 1.7320508f;
     return fabsf(k) * rmax > kFastPhaseMax;
@@ -40,14 +40,14 @@ static bool needs_precise(const Plan* p, float k) {
 
 int helmholtz_targets_per_lane(const Plan* p, float k) {
     const bool comp = !(p->flags & P2P_PLAN_PLAIN_FP32);
-    if (needs_precise(p, k) || !comp) return 1;   // the variant kernels hold one target per lane
+    if (helmholtz_needs_precise(p, k) || !comp) return 1;   // the variant kernels hold one target per lane
     return p->tpl >= 2 ? 2 : 1;
 }
 
 int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, float2* u,
                             cudaStream_t s) {
     const bool comp = !(p->flags & P2P_PLAN_PLAIN_FP32);
-    const bool precise = needs_precise(p, k);
+    const bool precise = helmholtz_needs_precise(p, k);
     // passes of 8, 4, 2, 1 right-hand sides; every pass but the last starts at an even index
     int r0 = 0;
     while (r0 < p->nrhs) {

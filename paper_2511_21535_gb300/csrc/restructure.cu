@@ -13,6 +13,8 @@
 // Source record formats (16-byte words):
 //   gravity    [x, y, z, m]
 //   Helmholtz  [x, y, z, 0] then nrhs complex q values packed two per word
+#include <algorithm>
+
 #include "common.cuh"
 #include "device.cuh"
 
@@ -44,57 +46,101 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
     }
 }
 
-// Per-box statistics and the cost-class histogram of the work items.
-// S[b] = sum of occupancies of b's neighbours; self[b] = offset of b's own
+__global__ void k_records_helm_adjoint(const float* __restrict__ pos, const float2* __restrict__ q,
+                                       const float2* __restrict__ gbar, const int32_t* __restrict__ perm, int64_t n,
+                                       int nrhs, int words, float4* __restrict__ rec) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+    float4* r = rec + s * words;
+    const int half = (nrhs + 1) / 2;
+    r[0] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], 0.0f);
+    for (int w = 0; w < half; ++w) {
+        const int r0 = 2 * w, r1 = r0 + 1;
+        const float2 a = q[(int64_t)r0 * n + i];
+        const float2 b = (r1 < nrhs) ? q[(int64_t)r1 * n + i] : make_float2(0.0f, 0.0f);
+        r[1 + w] = make_float4(a.x, a.y, b.x, b.y);
+        const float2 c = gbar[(int64_t)r0 * n + i];
+        const float2 d = (r1 < nrhs) ? gbar[(int64_t)r1 * n + i] : make_float2(0.0f, 0.0f);
+        r[1 + half + w] = make_float4(c.x, c.y, d.x, d.y);
+    }
+}
+
+__global__ void k_records_grav_adjoint(const float* __restrict__ pos, const float* __restrict__ mass,
+                                       const float* __restrict__ gphi, const float* __restrict__ gacc,
+                                       const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+    rec[2 * s] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass[i]);
+    rec[2 * s + 1] = make_float4(gphi[i], gacc[3 * i], gacc[3 * i + 1], gacc[3 * i + 2]);
+}
+
+// Per-box statistics, one warp per box (lane e reads neighbour e):
+// S[b] = sum of the occupancies of b's neighbours; self[b] = offset of b's own
 // particles in its stream (neighbours are ascending, so it is the sum over
-// neighbours with a smaller index).
+// neighbours with a smaller index); the pair count sum_b n_b S_b.
 __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ box_start,
                                                   const int32_t* __restrict__ nbr_start,
                                                   const int32_t* __restrict__ nbr_idx, Header* hdr,
-                                                  int64_t box_cap, int tt, int32_t* __restrict__ S,
-                                                  int32_t* __restrict__ self_off) {
-    __shared__ int32_t cls[kCostClasses];
+                                                  int32_t* __restrict__ S, int32_t* __restrict__ self_off) {
     __shared__ unsigned long long pairs_s;
+    if (threadIdx.x == 0) pairs_s = 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nb = hdr->n_boxes;
+    unsigned long long pairs = 0ull;
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
+        const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+        int32_t cnt = 0, lower = 0;
+        if (lane < ne) {
+            const int32_t c = nbr_idx[e0 + lane];
+            cnt = box_start[c + 1] - box_start[c];
+            lower = c < b ? cnt : 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt += __shfl_xor_sync(FULL, cnt, o);
+            lower += __shfl_xor_sync(FULL, lower, o);
+        }
+        if (lane == 0) {
+            S[b] = cnt;
+            if (self_off) self_off[b] = lower;
+            pairs += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)cnt;
+        }
+    }
+    if (lane == 0 && pairs) atomicAdd(&pairs_s, pairs);
+    __syncthreads();
+    if (threadIdx.x == 0 && pairs_s) atomicAdd(&hdr->pairs_nS, pairs_s);
+}
+
+__device__ __forceinline__ int cost_class(int32_t nt, int32_t sb) {
+    const unsigned long long cost = (unsigned long long)nt * (unsigned long long)max(sb, 1);
+    return 63 - __clzll(cost);
+}
+
+// Cost-class histogram of the work items (items of up to tt targets).
+__global__ void __launch_bounds__(256) k_items_count(const int32_t* __restrict__ box_start,
+                                                    const int32_t* __restrict__ S, Header* hdr, int64_t box_cap,
+                                                    int tt) {
+    __shared__ int32_t cls[kCostClasses];
     __shared__ int32_t items_s;
     for (int c = threadIdx.x; c < kCostClasses; c += blockDim.x) cls[c] = 0;
-    if (threadIdx.x == 0) {
-        pairs_s = 0ull;
-        items_s = 0;
-    }
+    if (threadIdx.x == 0) items_s = 0;
     __syncthreads();
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t nb = hdr->n_boxes;
-    if (b < box_cap) {
-        if (b >= nb) {
-            S[b] = 0;
-        } else {
-            int32_t sb = 0, so = 0;
-            for (int32_t e = nbr_start[b]; e < nbr_start[b + 1]; ++e) {
-                const int32_t c = nbr_idx[e];
-                const int32_t cnt = box_start[c + 1] - box_start[c];
-                if (c < b) so += cnt;
-                sb += cnt;
-            }
-            S[b] = sb;
-            if (self_off) self_off[b] = so;
-            const int32_t occ = box_start[b + 1] - box_start[b];
-            atomicAdd(&pairs_s, (unsigned long long)occ * (unsigned long long)sb);
-            int32_t ni = 0;
-            for (int32_t t0 = 0; t0 < occ; t0 += tt, ++ni) {
-                const int32_t nt = min(tt, occ - t0);
-                const unsigned long long cost = (unsigned long long)nt * (unsigned long long)max(sb, 1);
-                atomicAdd(&cls[63 - __clzll(cost)], 1);
-            }
-            atomicAdd(&items_s, ni);
-        }
+    if (b < box_cap && b < hdr->n_boxes) {
+        const int32_t occ = box_start[b + 1] - box_start[b];
+        const int32_t sb = S[b];
+        int32_t ni = 0;
+        for (int32_t t0 = 0; t0 < occ; t0 += tt, ++ni) atomicAdd(&cls[cost_class(min(tt, occ - t0), sb)], 1);
+        atomicAdd(&items_s, ni);
     }
     __syncthreads();
     for (int c = threadIdx.x; c < kCostClasses; c += blockDim.x)
         if (cls[c]) atomicAdd(&hdr->cls_cnt[c], cls[c]);
-    if (threadIdx.x == 0) {
-        if (pairs_s) atomicAdd(&hdr->pairs_nS, pairs_s);
-        if (items_s) atomicAdd(&hdr->n_items, items_s);
-    }
+    if (threadIdx.x == 0 && items_s) atomicAdd(&hdr->n_items, items_s);
 }
 
 // Place each item in its cost class, heaviest class first.  Blocks reserve a
@@ -119,11 +165,8 @@ __global__ void __launch_bounds__(256) k_items_fill(const int32_t* __restrict__ 
     int32_t occ = 0, sb = 0;
     if (active) {
         occ = box_start[b + 1] - box_start[b];
-        sb = max(S[b], 1);
-        for (int32_t t0 = 0; t0 < occ; t0 += tt) {
-            const unsigned long long cost = (unsigned long long)min(tt, occ - t0) * (unsigned long long)sb;
-            atomicAdd(&local_cnt[63 - __clzll(cost)], 1);
-        }
+        sb = S[b];
+        for (int32_t t0 = 0; t0 < occ; t0 += tt) atomicAdd(&local_cnt[cost_class(min(tt, occ - t0), sb)], 1);
     }
     __syncthreads();
     if (threadIdx.x < kCostClasses && local_cnt[threadIdx.x])
@@ -131,8 +174,7 @@ __global__ void __launch_bounds__(256) k_items_fill(const int32_t* __restrict__ 
     __syncthreads();
     if (active) {
         for (int32_t t0 = 0; t0 < occ; t0 += tt) {
-            const unsigned long long cost = (unsigned long long)min(tt, occ - t0) * (unsigned long long)sb;
-            const int c = 63 - __clzll(cost);
+            const int c = cost_class(min(tt, occ - t0), sb);
             const int32_t pos = cls_base[c] + atomicAdd(&local_cur[c], 1);
             items[pos] = make_int2((int32_t)b, t0);
         }
@@ -167,7 +209,15 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
             const int64_t nw = (int64_t)cnt * words;
             const float4* src = rec + (int64_t)s0 * words;
             float4* dst = red + out * words;
-            for (int64_t w = lane; w < nw; w += 32) dst[w] = src[w];
+            int64_t w = lane;
+            for (; w + 224 < nw; w += 256) {  // eight independent 16-byte loads in flight per lane
+                float4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldg(src + w + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) __stcs(dst + w + 32 * u, v[u]);  // streamed: read later by TMA
+            }
+            for (; w < nw; w += 32) __stcs(dst + w, __ldg(src + w));
             if (gather)
                 for (int32_t l = lane; l < cnt; l += 32) gather[out + l] = (uint32_t)(s0 + l);
             out += cnt;
@@ -175,9 +225,37 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
     }
 }
 
-int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaStream_t s) {
+// box statistics, and for the redundant layout the per-box streams of the
+// records already written in box order (words per record)
+static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
     const Layout& L = p->L;
     Header* hdr = at<Header>(ws, L.header);
+    const int64_t bc = p->box_cap;
+    float4* rec = at<float4>(ws, L.src);
+    const bool red = p->layout == P2P_LAYOUT_REDUNDANT;
+    int32_t* S = at<int32_t>(ws, L.box_S);
+    P2P_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(hdr) + kRestrSectionOffset, 0,
+                                 kOpSectionOffset - kRestrSectionOffset, s));
+    const unsigned sbl = (unsigned)std::min<int64_t>(blocks_for(bc * 32, 256), (int64_t)num_sms() * 16);
+    k_box_stats<<<sbl, 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+                                    at<int32_t>(ws, L.nbr_idx), hdr, S, red ? at<int32_t>(ws, L.red_self) : nullptr);
+    P2P_LAUNCH_CHECK();
+    if (red) {
+        int32_t* red_start = at<int32_t>(ws, L.red_start);
+        int st = scan_exclusive(S, red_start, bc, &hdr->n_boxes, &hdr->total_src, at<int32_t>(ws, L.scan_tmp), s);
+        if (st) return st;
+        const int sms = num_sms();
+        k_red_gather<<<sms * 8, 256, 0, s>>>(rec, words, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+                                            at<int32_t>(ws, L.nbr_idx), red_start, hdr, p->red_cap,
+                                            at<float4>(ws, L.red_src),
+                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr);
+        P2P_LAUNCH_CHECK();
+    }
+    return P2P_OK;
+}
+
+int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaStream_t s) {
+    const Layout& L = p->L;
     const int64_t n = p->n;
     const int32_t* perm = at<int32_t>(ws, L.perm);
     float4* rec = at<float4>(ws, L.src);
@@ -188,40 +266,46 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
                                                               p->nrhs, p->rec_words, rec);
     }
     P2P_LAUNCH_CHECK();
-    if (p->layout == P2P_LAYOUT_REDUNDANT) {
-        const int64_t bc = p->box_cap;
-        int32_t* S = at<int32_t>(ws, L.box_S);
-        int32_t* red_start = at<int32_t>(ws, L.red_start);
-        int32_t* red_self = at<int32_t>(ws, L.red_self);
-        // box statistics also fill the operator section; it is cleared again by the operator call
-        P2P_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(hdr) + kOpSectionOffset, 0,
-                                     sizeof(Header) - kOpSectionOffset, s));
-        k_box_stats<<<blocks_for(bc, 256), 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
-                                                       at<int32_t>(ws, L.nbr_idx), hdr, bc, 32 * p->tpl, S,
-                                                       red_self);
-        P2P_LAUNCH_CHECK();
-        int st = scan_exclusive(S, red_start, bc, &hdr->n_boxes, &hdr->total_src, at<int32_t>(ws, L.scan_tmp), s);
-        if (st) return st;
-        const int sms = num_sms();
-        k_red_gather<<<sms * 8, 256, 0, s>>>(rec, p->rec_words, at<int32_t>(ws, L.box_start),
-                                            at<int32_t>(ws, L.nbr_start), at<int32_t>(ws, L.nbr_idx), red_start,
-                                            hdr, p->red_cap, at<float4>(ws, L.red_src),
-                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr);
-        P2P_LAUNCH_CHECK();
-    }
+    int st = restructure_tail(p, ws, p->rec_words, s);
+    if (st) return st;
     p->src_ready = 1;
     return P2P_OK;
+}
+
+int restructure_adjoint(Plan* p, const float* pos, const void* a, const void* b, const void* c, void* ws, int* words,
+                        cudaStream_t s) {
+    const Layout& L = p->L;
+    const int64_t n = p->n;
+    const int32_t* perm = at<int32_t>(ws, L.perm);
+    float4* rec = at<float4>(ws, L.src);
+    int w;
+    if (p->kind == P2P_GRAVITY) {
+        w = kGravityAdjointWords;
+        if (w > p->rec_alloc_words) return P2P_ERR_UNSUPPORTED;
+        k_records_grav_adjoint<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float*>(a),
+                                                                 static_cast<const float*>(b),
+                                                                 static_cast<const float*>(c), perm, n, rec);
+    } else {
+        w = helmholtz_adjoint_words(p->nrhs);
+        if (w > p->rec_alloc_words) return P2P_ERR_UNSUPPORTED;
+        k_records_helm_adjoint<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float2*>(a),
+                                                                 static_cast<const float2*>(b), perm, n, p->nrhs, w,
+                                                                 rec);
+    }
+    P2P_LAUNCH_CHECK();
+    p->src_ready = 0;   // the forward records are overwritten
+    *words = w;
+    return restructure_tail(p, ws, w, s);
 }
 
 int build_items(Plan* p, void* ws, int tt, cudaStream_t s) {
     const Layout& L = p->L;
     Header* hdr = at<Header>(ws, L.header);
     const int64_t bc = p->box_cap;
-    int32_t* S = at<int32_t>(ws, L.box_S);
+    const int32_t* S = at<int32_t>(ws, L.box_S);
     P2P_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(hdr) + kOpSectionOffset, 0,
                                  sizeof(Header) - kOpSectionOffset, s));
-    k_box_stats<<<blocks_for(bc, 256), 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
-                                                   at<int32_t>(ws, L.nbr_idx), hdr, bc, tt, S, nullptr);
+    k_items_count<<<blocks_for(bc, 256), 256, 0, s>>>(at<int32_t>(ws, L.box_start), S, hdr, bc, tt);
     P2P_LAUNCH_CHECK();
     k_items_fill<<<blocks_for(bc, 256), 256, 0, s>>>(at<int32_t>(ws, L.box_start), S, hdr, bc, tt,
                                                     at<int2>(ws, L.items));

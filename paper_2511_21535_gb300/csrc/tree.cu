@@ -8,6 +8,8 @@
 //
 // Everything runs on the caller's stream with device-side counts: no host
 // synchronisation, so the build can be captured in a CUDA graph.
+#include <algorithm>
+
 #include "common.cuh"
 #include "device.cuh"
 
@@ -164,44 +166,48 @@ __device__ __forceinline__ int32_t find_box(uint32_t key, const uint32_t* __rest
     return (lo < nb && box_key[lo] == key) ? lo : -1;
 }
 
-// count mode (nbr_start == nullptr): cnt[b] = |N(b)|; write mode: fill nbr_idx
-__global__ void k_neighbours(const uint32_t* __restrict__ box_key, const Header* hdr, int64_t box_cap, int level,
-                             const int32_t* __restrict__ table, int32_t* __restrict__ cnt,
-                             const int32_t* __restrict__ nbr_start, int32_t* __restrict__ nbr_idx) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= box_cap) return;
-    const int32_t nb = hdr->n_boxes;
-    if (b >= nb) {
-        if (!nbr_start) cnt[b] = 0;
-        return;
-    }
+// One warp per box: lane l < 27 examines the neighbour cell at offset
+// (l % 3 - 1, l / 3 % 3 - 1, l / 9 - 1) and looks it up; the found box
+// indices are ranked across the warp so the list is written ascending.
+// count mode (nbr_start == nullptr): cnt[b] = |N(b)|; write mode: fill nbr_idx.
+__device__ __forceinline__ void neighbours_of(int64_t b, const uint32_t* __restrict__ box_key, int32_t nb, int level,
+                                             const int32_t* __restrict__ table, int32_t* __restrict__ cnt,
+                                             const int32_t* __restrict__ nbr_start, int32_t* __restrict__ nbr_idx,
+                                             int lane) {
     const uint32_t key = box_key[b];
     const int32_t cx = (int32_t)compact3(key), cy = (int32_t)compact3(key >> 1), cz = (int32_t)compact3(key >> 2);
     const int32_t side = 1 << level;
-    int32_t found[27];
-    int nf = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int32_t x = cx + dx, y = cy + dy, z = cz + dz;
-                if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) continue;
-                const int32_t c = find_box(morton3(x, y, z), box_key, nb, table);
-                if (c >= 0) {
-                    // insertion into the ascending list
-                    int j = nf++;
-                    while (j > 0 && found[j - 1] > c) {
-                        found[j] = found[j - 1];
-                        --j;
-                    }
-                    found[j] = c;
-                }
-            }
-    if (!nbr_start) {
-        cnt[b] = nf;
-    } else {
-        const int32_t o = nbr_start[b];
-        for (int j = 0; j < nf; ++j) nbr_idx[o + j] = found[j];
+    int32_t c = -1;
+    if (lane < 27) {
+        const int32_t x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+        if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side)
+            c = find_box(morton3(x, y, z), box_key, nb, table);
     }
+    const unsigned found = __ballot_sync(FULL, c >= 0);
+    if (!nbr_start) {
+        if (lane == 0) cnt[b] = __popc(found);
+        return;
+    }
+    int rank = 0;  // found indices are distinct: rank = how many are smaller
+#pragma unroll
+    for (int j = 0; j < 27; ++j) {
+        const int32_t v = __shfl_sync(FULL, c, j);
+        rank += (v >= 0 && v < c) ? 1 : 0;
+    }
+    if (c >= 0) nbr_idx[nbr_start[b] + rank] = c;
+}
+
+// Grid-stride over the boxes that exist (the count is on the device); the
+// count array needs no zeros beyond it because its scan reads only n_boxes.
+__global__ void __launch_bounds__(256) k_neighbours(const uint32_t* __restrict__ box_key, const Header* hdr,
+                                                   int level, const int32_t* __restrict__ table,
+                                                   int32_t* __restrict__ cnt, const int32_t* __restrict__ nbr_start,
+                                                   int32_t* __restrict__ nbr_idx) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nb = hdr->n_boxes;
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps)
+        neighbours_of(b, box_key, nb, level, table, cnt, nbr_start, nbr_idx, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -213,7 +219,7 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     const Layout& L = p->L;
     Header* hdr = at<Header>(ws, L.header);
     const int64_t n = p->n;
-    // clear the tree section of the header (counts and flags)
+    // clear the tree and restructuring sections of the header (counts and flags)
     P2P_CUDA_TRY(cudaMemsetAsync(hdr, 0, kOpSectionOffset, s));
 
     uint32_t* ka = at<uint32_t>(ws, L.keys_a);
@@ -279,11 +285,12 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     int32_t* ncnt = at<int32_t>(ws, L.nbr_cnt);
     int32_t* nstart = at<int32_t>(ws, L.nbr_start);
     int32_t* nidx = at<int32_t>(ws, L.nbr_idx);
-    k_neighbours<<<blocks_for(bc, 128), 128, 0, s>>>(box_key, hdr, bc, p->level, table, ncnt, nullptr, nullptr);
+    const unsigned nbl = (unsigned)std::min<int64_t>(blocks_for(bc * 32, 256), (int64_t)num_sms() * 16);
+    k_neighbours<<<nbl, 256, 0, s>>>(box_key, hdr, p->level, table, ncnt, nullptr, nullptr);
     P2P_LAUNCH_CHECK();
     st = scan_exclusive(ncnt, nstart, bc, &hdr->n_boxes, &hdr->n_nbr, scratch, s);
     if (st) return st;
-    k_neighbours<<<blocks_for(bc, 128), 128, 0, s>>>(box_key, hdr, bc, p->level, table, ncnt, nstart, nidx);
+    k_neighbours<<<nbl, 256, 0, s>>>(box_key, hdr, p->level, table, ncnt, nstart, nidx);
     P2P_LAUNCH_CHECK();
     p->tree_ready = 1;
     p->src_ready = 0;

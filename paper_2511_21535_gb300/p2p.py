@@ -16,7 +16,7 @@ from . import build as _build
 
 GRAVITY, HELMHOLTZ = 0, 1
 LAYOUTS = {"indirect": 0, "redundant": 1}
-PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING = 0x1, 0x2, 0x4
+PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING, PLAN_ADJOINT = 0x1, 0x2, 0x4, 0x8
 FLAG_DOMAIN, FLAG_TIMEOUT, FLAG_CAPACITY = 0x1, 0x2, 0x4
 
 ARRAYS = {"perm": (0, torch.int32), "box_key": (1, torch.int32), "box_start": (2, torch.int32),
@@ -29,7 +29,7 @@ EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_
            "p2p_plan_workspace_bytes", "p2p_plan_set_tuning", "p2p_tree_build", "p2p_tree_import",
            "p2p_restructure", "p2p_gravity", "p2p_helmholtz", "p2p_plan_array", "p2p_read_counters",
            "p2p_plan_timing", "p2p_launch_count", "p2p_gravity_noalloc",
-           "p2p_measure_pipes")
+           "p2p_measure_pipes", "p2p_helmholtz_adjoint", "p2p_gravity_adjoint")
 
 
 class P2PError(RuntimeError):
@@ -77,6 +77,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_launch_count": (I64, []),
         "p2p_gravity_noalloc": (I, [P, P, I64, I, P, F, F, I, P, P, P]),
         "p2p_measure_pipes": (I, [ctypes.POINTER(ctypes.c_double), P]),
+        "p2p_helmholtz_adjoint": (I, [P, F, P, P, P, P, P, P, SZ, P]),
+        "p2p_gravity_adjoint": (I, [P, F, P, P, P, P, P, P, P, SZ, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -127,7 +129,8 @@ class Plan:
 
     def __init__(self, kind: str, n: int, level: int, lo, edge: float, nrhs: int = 1,
                  layout: str = "redundant", gather_map: bool = False, plain_fp32: bool = False,
-                 timing: bool = False, device=None, workspace: torch.Tensor | None = None):
+                 timing: bool = False, adjoint: bool = False, device=None,
+                 workspace: torch.Tensor | None = None):
         lib = load()
         self.kind = kind
         self.n = int(n)
@@ -136,7 +139,7 @@ class Plan:
         self.layout = layout
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         flags = (PLAN_GATHER_MAP if gather_map else 0) | (PLAN_PLAIN_FP32 if plain_fp32 else 0) | \
-                (PLAN_TIMING if timing else 0)
+                (PLAN_TIMING if timing else 0) | (PLAN_ADJOINT if adjoint else 0)
         lo_arr = (ctypes.c_float * 3)(*[float(v) for v in lo])
         h = ctypes.c_void_p()
         kid = {"gravity": GRAVITY, "helmholtz": HELMHOLTZ}[kind]
@@ -210,6 +213,35 @@ class Plan:
         _check(load().p2p_helmholtz(self._h, float(k), _ptr(u), w, b, _stream(stream)), "p2p_helmholtz")
         return u
 
+    def helmholtz_adjoint(self, k: float, pos, gbar, q=None, want_q: bool = True, want_pos: bool = False,
+                          stream=None):
+        """(grad_q [nrhs, n] complex64 or None, grad_pos [n, 3] float32 or None) for gbar = dL/du."""
+        _need(pos, torch.float32, (self.n, 3), self.device)
+        _need(gbar, torch.complex64, (self.nrhs, self.n), self.device)
+        gq = torch.empty(self.nrhs, self.n, dtype=torch.complex64, device=self.device) if want_q else None
+        gx = torch.empty(self.n, 3, dtype=torch.float32, device=self.device) if want_pos else None
+        if want_pos:
+            _need(q, torch.complex64, (self.nrhs, self.n), self.device)
+        w, b = self._wsp()
+        _check(load().p2p_helmholtz_adjoint(self._h, float(k), _ptr(pos), _ptr(q if want_pos else None), _ptr(gbar),
+                                            _ptr(gq), _ptr(gx), w, b, _stream(stream)), "p2p_helmholtz_adjoint")
+        return gq, gx
+
+    def gravity_adjoint(self, eps: float, pos, mass, grad_phi, grad_acc, want_mass: bool = True,
+                        want_pos: bool = True, stream=None):
+        """(grad_mass [n] or None, grad_pos [n, 3] or None) for grad_phi = dL/dphi, grad_acc = dL/da."""
+        _need(pos, torch.float32, (self.n, 3), self.device)
+        _need(mass, torch.float32, (self.n,), self.device)
+        _need(grad_phi, torch.float32, (self.n,), self.device)
+        _need(grad_acc, torch.float32, (self.n, 3), self.device)
+        gm = torch.empty(self.n, dtype=torch.float32, device=self.device) if want_mass else None
+        gx = torch.empty(self.n, 3, dtype=torch.float32, device=self.device) if want_pos else None
+        w, b = self._wsp()
+        _check(load().p2p_gravity_adjoint(self._h, float(eps), _ptr(pos), _ptr(mass), _ptr(grad_phi),
+                                          _ptr(grad_acc), _ptr(gm), _ptr(gx), w, b, _stream(stream)),
+               "p2p_gravity_adjoint")
+        return gm, gx
+
     # -- inspection ---------------------------------------------------------
     def counters(self, stream=None, check: bool = False) -> dict:
         out = (ctypes.c_int64 * len(COUNTERS))()
@@ -269,3 +301,69 @@ def helmholtz(pos, q, level, lo, edge, k, layout="redundant", plan: Plan | None 
     plan.tree_build(pos)
     plan.restructure(pos, q.contiguous())
     return plan.helmholtz(k)
+
+
+# ---------------------------------------------------------------------------
+# differentiable operators (hand-written adjoint kernels behind autograd)
+# ---------------------------------------------------------------------------
+
+class _HelmholtzFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pos, q, plan, k):
+        plan.tree_build(pos)
+        plan.restructure(pos, q)
+        u = plan.helmholtz(k)
+        ctx.save_for_backward(pos, q)
+        ctx.plan, ctx.k = plan, k
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        pos, q = ctx.saved_tensors
+        want_pos, want_q = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (want_pos or want_q):
+            return None, None, None, None
+        plan = ctx.plan
+        plan.tree_build(pos)          # the plan may have served other calls since the forward
+        gq, gx = plan.helmholtz_adjoint(ctx.k, pos, grad_u.contiguous(), q, want_q=want_q, want_pos=want_pos)
+        return gx, gq, None, None
+
+
+class _GravityFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pos, mass, plan, eps):
+        plan.tree_build(pos)
+        plan.restructure(pos, mass)
+        phi, acc = plan.gravity(eps)
+        ctx.save_for_backward(pos, mass)
+        ctx.plan, ctx.eps = plan, eps
+        return phi, acc
+
+    @staticmethod
+    def backward(ctx, grad_phi, grad_acc):
+        pos, mass = ctx.saved_tensors
+        want_pos, want_m = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (want_pos or want_m):
+            return None, None, None, None
+        if grad_phi is None:
+            grad_phi = torch.zeros_like(mass)
+        if grad_acc is None:
+            grad_acc = torch.zeros_like(pos)
+        plan = ctx.plan
+        plan.tree_build(pos)
+        gm, gx = plan.gravity_adjoint(ctx.eps, pos, mass, grad_phi.contiguous(), grad_acc.contiguous(),
+                                      want_mass=want_m, want_pos=want_pos)
+        return gx, gm, None, None
+
+
+def helmholtz_p2p(pos, q, plan: Plan, k: float):
+    """Differentiable Helmholtz near field u = P(pos) q; gradients flow to q and pos
+    through the adjoint kernels.  The plan must be created with adjoint=True for
+    position gradients."""
+    return _HelmholtzFn.apply(pos, q, plan, k)
+
+
+def gravity_p2p(pos, mass, plan: Plan, eps: float):
+    """Differentiable softened gravity (phi, acc); gradients flow to mass and pos.
+    The plan must be created with adjoint=True."""
+    return _GravityFn.apply(pos, mass, plan, eps)
