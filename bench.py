@@ -346,6 +346,91 @@ def run_gpu(args, rank, world, local_rank):
 
 
 # ---------------------------------------------------------------------------
+# batched forward + adjoint (64 uneven grid instances x 8 RHS) vs plain launches
+# ---------------------------------------------------------------------------
+
+def batched_vs_plain(dev, steps: int, layout: str = "auto"):
+    """One CUDA-graph launch computing u = P q and g = conj(P) y for all 64
+    instances, against per-instance plans doing restructure + forward +
+    adjoint with their own launches; both compensated FP32."""
+    import torch
+    from paper_2511_21535_gb300 import p2p
+    probs = wl.batched_helmholtz()
+    nrhs = probs[0].nrhs
+    k = probs[0].k
+    rng = np.random.default_rng(123)
+    batch = p2p.Batch([(p.n, p.level, p.lo, p.edge) for p in probs], nrhs, k, pair=True, layout=layout, device=dev)
+    pos = torch.from_numpy(np.concatenate([p.pos for p in probs])).to(dev)
+    q = torch.from_numpy(np.concatenate([p.strength for p in probs], axis=1)).to(dev)
+    y = torch.from_numpy(wl.complex_normal((nrhs, batch.N), rng)).to(dev)
+    t0 = time.perf_counter()
+    batch.build(pos)
+    build_s = time.perf_counter() - t0
+    best = batch.autotune(pos, q, y)
+    u, g = batch.capture(pos, q, y)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        batch.launch()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lb = p2p.launch_count()
+    a.record(stream)
+    for _ in range(steps):
+        batch.launch()
+    b.record(stream)
+    b.synchronize()
+    batched_ms = a.elapsed_time(b) / steps
+    batched_kernels = (p2p.launch_count() - lb) // steps
+    pairs = batch.counters()["pairs"]
+
+    # plain: one plan per instance, three calls per product
+    plans, per = [], []
+    for i, pr in enumerate(probs):
+        o0, o1 = batch.offsets[i], batch.offsets[i + 1]
+        pl = p2p.Plan("helmholtz", pr.n, pr.level, pr.lo, pr.edge, nrhs=nrhs, layout="indirect", device=dev)
+        pp = pos[o0:o1].contiguous()
+        pl.tree_build(pp)
+        per.append((pp, q[:, o0:o1].contiguous(), y[:, o0:o1].contiguous(),
+                    torch.empty(nrhs, pr.n, dtype=torch.complex64, device=dev)))
+        plans.append(pl)
+
+    def plain_step():
+        outs = []
+        for pl, (pp, qi, yi, ui) in zip(plans, per):
+            pl.restructure(pp, qi)
+            pl.helmholtz(k, ui)
+            gi, _ = pl.helmholtz_adjoint(k, pp, yi, want_q=True, want_pos=False)
+            outs.append((ui, gi))
+        return outs
+
+    for _ in range(2):
+        outs = plain_step()
+    torch.cuda.synchronize()
+    l0 = p2p.launch_count()
+    a.record(stream)
+    for _ in range(steps):
+        outs = plain_step()
+    b.record(stream)
+    b.synchronize()
+    plain_ms = a.elapsed_time(b) / steps
+    plain_launches = (p2p.launch_count() - l0) // steps
+    # equal accuracy: both against each other (same per-pair arithmetic)
+    uc = torch.cat([o[0] for o in outs], dim=1)
+    gc = torch.cat([o[1] for o in outs], dim=1)
+    diff_u = float(torch.linalg.vector_norm(u - uc) / torch.linalg.vector_norm(uc))
+    diff_g = float(torch.linalg.vector_norm(g - gc) / torch.linalg.vector_norm(gc))
+    return {"workload": "64 grid instances (edges 16-64, 4^3 leaves, lambda/10), 8 RHS, forward + adjoint",
+            "n_total": batch.N, "geometric_pairs": pairs, "rhs_pairs_per_step": pairs * nrhs * 2,
+            "batched_ms": batched_ms, "plain_ms": plain_ms, "speedup": plain_ms / batched_ms,
+            "batched_pairs_per_s": pairs * nrhs * 2 / (batched_ms * 1e-3),
+            "plain_pairs_per_s": pairs * nrhs * 2 / (plain_ms * 1e-3),
+            "batched_graph_launches_per_step": 1, "batched_kernels_per_step": int(batched_kernels),
+            "plain_kernels_per_step": int(plain_launches),
+            "rel_l2_batched_vs_plain": {"u": diff_u, "g": diff_g}, "autotune": best,
+            "build_s": build_s}
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
@@ -437,6 +522,8 @@ def main():
     ap.add_argument("--group", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -459,7 +546,14 @@ def main():
         td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     from paper_2511_21535_gb300 import build as cuda_build
     cuda_build.build()
+    if args.batched_only:
+        import torch as _t
+        print(json.dumps(batched_vs_plain(_t.device("cuda", local_rank), 10)))
+        return
     res, prob = run_gpu(args, rank, world, local_rank)
+    if not args.no_batched:
+        import torch as _t
+        res["batched"] = batched_vs_plain(_t.device("cuda", local_rank), 10)
     if rank == 0:
         if not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)

@@ -77,7 +77,7 @@ typedef enum {
 } p2p_status;
 
 typedef enum { P2P_GRAVITY = 0, P2P_HELMHOLTZ = 1 } p2p_kernel_kind;
-typedef enum { P2P_LAYOUT_INDIRECT = 0, P2P_LAYOUT_REDUNDANT = 1 } p2p_layout;
+typedef enum { P2P_LAYOUT_INDIRECT = 0, P2P_LAYOUT_REDUNDANT = 1, P2P_LAYOUT_AUTO = 2 } p2p_layout;
 
 /* plan flags */
 #define P2P_PLAN_GATHER_MAP  0x1u  /* restructuring also writes the gather map      */
@@ -228,6 +228,62 @@ int p2p_helmholtz_adjoint(p2p_plan* plan, float k, const float* pos, const void*
 int p2p_gravity_adjoint(p2p_plan* plan, float eps, const float* pos, const float* mass,
                         const float* grad_phi, const float* grad_acc, float* grad_mass,
                         float* grad_pos, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Batched near field: many independent Helmholtz instances (uneven sizes and
+ * box occupancies) with nrhs right-hand sides each, run by ONE persistent
+ * kernel over a work list spanning all instances, optionally captured in a
+ * CUDA graph.  This answers the many small launches of the paper's PhotoNs
+ * port (Section 5.2, Section 5.2.3 item 4); each instance's tree is built once
+ * because the geometry is fixed across solver iterations (Section 5.1).
+ *
+ * Data of the batch is CONCATENATED: instance i owns particles
+ * [off_i, off_i + n_i) of every array (off = prefix sums of n); positions are
+ * float32 [N][3]; right-hand sides complex64 [nrhs][N].
+ *
+ *   p2p_batch_create   host only.  n/level/edge: host arrays [n_instances];
+ *                      lo: host float [n_instances][3] (boxing domain of each
+ *                      instance, as for p2p_plan_create).  pair != 0: every
+ *                      run computes the forward product u = P q AND the
+ *                      adjoint product g = conj(P) y (one operator of 2 nrhs
+ *                      right-hand sides, since conj(P) y = conj(P conj y)).
+ *                      layout: INDIRECT, REDUNDANT or AUTO (the workspace
+ *                      holds redundant streams; p2p_batch_autotune chooses).
+ *                      flags: 0 or P2P_PLAN_PLAIN_FP32.  Helmholtz only
+ *                      (P2P_ERR_UNSUPPORTED otherwise).
+ *   p2p_batch_build    builds every instance's tree and merges them into one
+ *                      box structure; synchronises the stream once per
+ *                      instance (set-up, not the hot path).
+ *   p2p_batch_run      restructuring + one operator launch for all
+ *                      instances: u [nrhs][N] (and g [nrhs][N] if pair).
+ *   p2p_batch_set_tuning / p2p_batch_autotune
+ *                      the tuning space (layout, targets per lane, tile,
+ *                      warps per item); the autotuner times every candidate
+ *                      with CUDA events on the given buffers, keeps the
+ *                      fastest and returns best[5] = {layout, targets/lane,
+ *                      tile, ctas/SM, warps/item} and its time; synchronises.
+ *   p2p_batch_capture  captures p2p_batch_run on these buffers into a CUDA
+ *                      graph (on an internal stream); p2p_batch_launch then
+ *                      replays it on any stream.
+ */
+typedef struct p2p_batch p2p_batch;
+int p2p_batch_create(p2p_batch** out, int kind, int n_instances, const int64_t* n, const int* level,
+                     const float* lo, const float* edge, int nrhs, int pair, int layout, unsigned flags);
+int p2p_batch_destroy(p2p_batch* batch);
+int p2p_batch_workspace_bytes(const p2p_batch* batch, size_t* bytes);
+int p2p_batch_build(p2p_batch* batch, const float* pos, void* ws, size_t ws_bytes, void* stream);
+int p2p_batch_set_tuning(p2p_batch* batch, int layout, int targets_per_lane, int tile, int ctas_per_sm,
+                         int warps_per_item);
+int p2p_batch_run(p2p_batch* batch, float k, const float* pos, const void* q, const void* y, void* u,
+                  void* g, void* ws, size_t ws_bytes, void* stream);
+int p2p_batch_autotune(p2p_batch* batch, float k, const float* pos, const void* q, const void* y,
+                       void* u, void* g, void* ws, size_t ws_bytes, void* stream, int* best,
+                       float* best_ms);
+int p2p_batch_capture(p2p_batch* batch, float k, const float* pos, const void* q, const void* y,
+                      void* u, void* g, void* ws, size_t ws_bytes);
+int p2p_batch_launch(p2p_batch* batch, void* stream);
+/* counters of the combined structure (as p2p_read_counters; pairs are geometric) */
+int p2p_batch_counters(const p2p_batch* batch, const void* ws, int64_t* out, void* stream);
 
 /* identifiers of workspace arrays for p2p_plan_array */
 typedef enum {

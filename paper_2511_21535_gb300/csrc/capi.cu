@@ -16,7 +16,7 @@ void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-static void compute_layout(Plan* p) {
+void compute_layout(Plan* p) {
     Layout& L = p->L;
     const int64_t n = p->n;
     const int64_t bc = p->box_cap;
@@ -57,7 +57,7 @@ static void compute_layout(Plan* p) {
     L.total = off;
 }
 
-static int check_ws(const Plan* p, const void* ws, size_t ws_bytes) {
+int check_ws(const Plan* p, const void* ws, size_t ws_bytes) {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < p->L.total) return P2P_ERR_WORKSPACE;
     return P2P_OK;
 }
@@ -72,7 +72,7 @@ static void ev_end(Plan* p, int ph, cudaStream_t s) {
     }
 }
 
-static LoopArgs loop_args(const Plan* p, void* ws, int words) {
+LoopArgs loop_args(const Plan* p, void* ws, int words) {
     const Layout& L = p->L;
     LoopArgs a;
     a.rec = at<float4>(ws, L.src);
@@ -88,6 +88,56 @@ static LoopArgs loop_args(const Plan* p, void* ws, int words) {
     a.items = at<int2>(ws, L.items);
     a.hdr = at<Header>(ws, L.header);
     return a;
+}
+
+
+int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float edge, int nrhs, int layout,
+              unsigned flags) {
+    if (kind != P2P_GRAVITY && kind != P2P_HELMHOLTZ) return P2P_ERR_INVALID_ARG;
+    if (n < 1 || n > P2P_MAX_N) return P2P_ERR_INVALID_ARG;
+    if (level < 1 || level > P2P_MAX_LEVEL) return P2P_ERR_INVALID_ARG;
+    if (!lo || !(edge > 0.0f) || !(edge < 3.0e38f)) return P2P_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!(lo[a] == lo[a]) || lo[a] > 3.0e38f || lo[a] < -3.0e38f) return P2P_ERR_INVALID_ARG;
+    if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT) return P2P_ERR_INVALID_ARG;
+    if (kind == P2P_GRAVITY && nrhs != 1) return P2P_ERR_INVALID_ARG;
+    if (nrhs < 1 || nrhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
+    if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING | P2P_PLAN_ADJOINT))
+        return P2P_ERR_INVALID_ARG;
+    *p = Plan{};
+    p->kind = kind;
+    p->n = n;
+    p->level = level;
+    for (int a = 0; a < 3; ++a) p->lo[a] = lo[a];
+    p->edge = edge;
+    p->scale = (float)(1 << level) / edge;
+    p->nrhs = nrhs;
+    p->layout = layout;
+    p->flags = flags;
+    const int64_t boxes = (int64_t)1 << (3 * level);
+    p->box_cap = n < boxes ? n : boxes;
+    p->red_cap = 27 * n;
+    p->rec_words = (kind == P2P_GRAVITY) ? 1 : helmholtz_rec_words(nrhs);
+    p->rec_alloc_words = p->rec_words;
+    if (flags & P2P_PLAN_ADJOINT)
+        p->rec_alloc_words = (kind == P2P_GRAVITY) ? kGravityAdjointWords : helmholtz_adjoint_words(nrhs);
+    p->sort_tiles = (int)((n + 2047) / 2048);
+    p->use_table = level <= 8;
+    // defaults; p2p_plan_set_tuning / the autotuner may change them
+    if (kind == P2P_GRAVITY) {
+        p->tpl = 2;
+        p->tile = 64;
+    } else {
+        p->tpl = nrhs >= 4 ? 1 : 2;
+        p->tile = nrhs >= 4 ? 32 : 64;
+    }
+    p->ctas_per_sm = 0;
+    p->group = 4;
+    p->split = nrhs;
+    p->rmax = 2.0f * (edge / (float)(1 << level)) * 1.7320508f;
+    p->items_cap = p->box_cap + (n + 31) / 32 + 1;
+    compute_layout(p);
+    return P2P_OK;
 }
 
 }  // namespace p2p
@@ -119,51 +169,13 @@ int p2p_plan_create(p2p_plan** out, int kind, int64_t n, int level, const float*
                     int layout, unsigned flags) {
     if (!out) return P2P_ERR_INVALID_ARG;
     *out = nullptr;
-    if (kind != P2P_GRAVITY && kind != P2P_HELMHOLTZ) return P2P_ERR_INVALID_ARG;
-    if (n < 1 || n > P2P_MAX_N) return P2P_ERR_INVALID_ARG;
-    if (level < 1 || level > P2P_MAX_LEVEL) return P2P_ERR_INVALID_ARG;
-    if (!lo || !(edge > 0.0f) || !(edge < 3.0e38f)) return P2P_ERR_INVALID_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (!(lo[a] == lo[a]) || lo[a] > 3.0e38f || lo[a] < -3.0e38f) return P2P_ERR_INVALID_ARG;
-    if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT) return P2P_ERR_INVALID_ARG;
-    if (kind == P2P_GRAVITY && nrhs != 1) return P2P_ERR_INVALID_ARG;
-    if (nrhs < 1 || nrhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
-    if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING | P2P_PLAN_ADJOINT))
-        return P2P_ERR_INVALID_ARG;
+    Plan tmp{};
+    int st = plan_init(&tmp, kind, n, level, lo, edge, nrhs, layout, flags);
+    if (st) return st;
     p2p_plan* h = new (std::nothrow) p2p_plan;
     if (!h) return P2P_ERR_OOM;
+    h->p = tmp;
     Plan* p = &h->p;
-    *p = Plan{};
-    p->kind = kind;
-    p->n = n;
-    p->level = level;
-    for (int a = 0; a < 3; ++a) p->lo[a] = lo[a];
-    p->edge = edge;
-    p->scale = (float)(1 << level) / edge;
-    p->nrhs = nrhs;
-    p->layout = layout;
-    p->flags = flags;
-    const int64_t boxes = (int64_t)1 << (3 * level);
-    p->box_cap = n < boxes ? n : boxes;
-    p->red_cap = 27 * n;
-    p->rec_words = (kind == P2P_GRAVITY) ? 1 : helmholtz_rec_words(nrhs);
-    p->rec_alloc_words = p->rec_words;
-    if (flags & P2P_PLAN_ADJOINT)
-        p->rec_alloc_words = (kind == P2P_GRAVITY) ? kGravityAdjointWords : helmholtz_adjoint_words(nrhs);
-    p->sort_tiles = (int)((n + 2047) / 2048);
-    p->use_table = level <= 8;
-    // defaults; p2p_plan_set_tuning / the autotuner may change them
-    if (kind == P2P_GRAVITY) {
-        p->tpl = 2;
-        p->tile = 64;
-    } else {
-        p->tpl = nrhs >= 4 ? 1 : 2;
-        p->tile = nrhs >= 4 ? 32 : 64;
-    }
-    p->ctas_per_sm = 0;
-    p->group = 4;
-    p->items_cap = p->box_cap + (n + 31) / 32 + 1;
-    compute_layout(p);
     p->timing = (flags & P2P_PLAN_TIMING) ? 1 : 0;
     if (p->timing) {
         for (int ph = 0; ph < P2P_PHASE_COUNT; ++ph)
@@ -280,7 +292,8 @@ int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void
     st = build_items(p, ws, 32 * helmholtz_targets_per_lane(p, k), s);
     if (st) return st;
     ev_begin(p, P2P_PHASE_KERNEL, s);
-    st = launch_helmholtz_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), k, static_cast<float2*>(u), s);
+    st = launch_helmholtz_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), k,
+                                 HelmOut{static_cast<float2*>(u), nullptr, p->nrhs}, s);
     if (st) return st;
     ev_end(p, P2P_PHASE_KERNEL, s);
     ev_end(p, P2P_PHASE_OPERATOR, s);
@@ -306,7 +319,7 @@ int p2p_helmholtz_adjoint(p2p_plan* h, float k, const float* pos, const void* q,
         st = build_items(p, ws, 32 * helmholtz_targets_per_lane(p, -k), s);
         if (st) return st;
         st = launch_helmholtz_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), -k,
-                                     static_cast<float2*>(grad_q), s);
+                                     HelmOut{static_cast<float2*>(grad_q), nullptr, p->nrhs}, s);
         p->src_ready = 0;   // the records hold gbar, not the forward sources
         return st;
     }

@@ -69,6 +69,8 @@ struct Plan {
     int tile;                          // source records per stage
     int ctas_per_sm;
     int group;                         // warps cooperating on one work item
+    int split;                         // Helmholtz RHS from here on form a conjugated second output
+    float rmax;                        // largest distance between points of neighbouring boxes
     Layout L;
     // state
     int tree_ready;
@@ -122,11 +124,18 @@ int scan_exclusive(const int32_t* in, int32_t* out, int64_t n_cap, const int32_t
                    int32_t* d_total, int32_t* scratch, cudaStream_t s);
 
 struct LoopArgs;
+int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float edge, int nrhs, int layout,
+              unsigned flags);
+void compute_layout(Plan* p);
+int check_ws(const Plan* p, const void* ws, size_t ws_bytes);
+LoopArgs loop_args(const Plan* p, void* ws, int words);
 int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s);
 int tree_import(Plan* p, const int32_t* perm, const int32_t* box_start, int32_t n_boxes,
                 const int32_t* nbr_start, const int32_t* nbr_idx, int32_t n_nbr, void* ws,
                 cudaStream_t s);
-int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaStream_t s);
+// strength2 (Helmholtz, optional): right-hand sides from p->split on are conj(strength2)
+int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaStream_t s,
+                const void* strength2 = nullptr);
 // adjoint records: Helmholtz [pos | q | gbar] (a = q, b = gbar), gravity [pos m | gphi gacc]
 // (a = mass, b = grad_phi, c = grad_acc); returns the record width in words via *words
 int restructure_adjoint(Plan* p, const float* pos, const void* a, const void* b, const void* c, void* ws,
@@ -144,7 +153,13 @@ int build_items(Plan* p, void* ws, int tt, cudaStream_t s);
 int helmholtz_targets_per_lane(const Plan* p, float k);
 int launch_gravity_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps, float* phi, float* acc,
                           cudaStream_t s);
-int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, float2* u,
+// u: RHS r < split -> u[r]; r >= split -> u2[r - split], conjugated
+struct HelmOut {
+    float2* u;
+    float2* u2;
+    int split;
+};
+int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, HelmOut out,
                             cudaStream_t s);
 
 // records

@@ -127,6 +127,8 @@ extern "C" int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t 
     p.tile = 64;
     p.ctas_per_sm = 0;
     p.group = 4;
+    p.split = 1;
+    p.rmax = 2.0f * (edge / (float)(1 << level)) * 1.7320508f;
     p.items_cap = p.box_cap + (n + 31) / 32 + 1;
     noalloc_layout(&p);
     if (p.L.total > (size_t)P2P_NOALLOC_SCRATCH_BYTES) return P2P_ERR_UNSUPPORTED;

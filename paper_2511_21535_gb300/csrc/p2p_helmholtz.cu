@@ -5,7 +5,7 @@
 namespace p2p {
 
 template <int K, int G>
-static int fast_kg(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, float2* u,
+static int fast_kg(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                    cudaStream_t s) {
     switch (R) {
         case 1: return launch_helm<K, G, 1, true, false>(p, a, perm, kk, r0, u, s);
@@ -16,7 +16,7 @@ static int fast_kg(const Plan* p, const LoopArgs& a, const int32_t* perm, float 
     }
 }
 
-int launch_helm_fast(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, float2* u,
+int launch_helm_fast(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                      cudaStream_t s) {
     const int K = p->tpl >= 2 ? 2 : 1;
     switch (p->group) {
@@ -32,11 +32,7 @@ int launch_helm_fast(const Plan* p, const LoopArgs& a, const int32_t* perm, floa
 // this range); beyond it the accurate library routine is used.
 constexpr float kFastPhaseMax = 32.0f;
 
-bool helmholtz_needs_precise(const Plan* p, float k) {
-    const float box = p->edge / (float)(1 << p->level);
-    const float rmax = 2.0f * box * 1.7320508f;
-    return fabsf(k) * rmax > kFastPhaseMax;
-}
+bool helmholtz_needs_precise(const Plan* p, float k) { return fabsf(k) * p->rmax > kFastPhaseMax; }
 
 int helmholtz_targets_per_lane(const Plan* p, float k) {
     const bool comp = !(p->flags & P2P_PLAN_PLAIN_FP32);
@@ -44,7 +40,7 @@ int helmholtz_targets_per_lane(const Plan* p, float k) {
     return p->tpl >= 2 ? 2 : 1;
 }
 
-int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, float2* u,
+int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, HelmOut u,
                             cudaStream_t s) {
     const bool comp = !(p->flags & P2P_PLAN_PLAIN_FP32);
     const bool precise = helmholtz_needs_precise(p, k);

@@ -26,7 +26,7 @@ struct HelmOp {
     int qw0;            // first q word of this pass inside a record
     int64_t n;
     int r0;             // first right-hand side of this pass
-    float2* __restrict__ u;
+    HelmOut out;
 
     float tx[K], ty[K], tz[K];
     int self[K];
@@ -156,9 +156,12 @@ struct HelmOp {
             if (l < nt) {
                 const int64_t o = perm[tbase + l];
 #pragma unroll
-                for (int q = 0; q < R; ++q)
-                    u[(int64_t)(r0 + q) * n + o] =
-                        make_float2((sr[k][q] - cr[k][q]) * inv4pi, (si[k][q] - ci[k][q]) * inv4pi);
+                for (int q = 0; q < R; ++q) {
+                    const float re = (sr[k][q] - cr[k][q]) * inv4pi, im = (si[k][q] - ci[k][q]) * inv4pi;
+                    const int r = r0 + q;
+                    if (r < out.split) out.u[(int64_t)r * n + o] = make_float2(re, im);
+                    else out.u2[(int64_t)(r - out.split) * n + o] = make_float2(re, -im);
+                }
             }
         }
     }
@@ -166,8 +169,7 @@ struct HelmOp {
 
 template <int K, int G, int R, bool COMP, bool PRECISE>
 __global__ void __launch_bounds__(kLoopThreads, 4)
-    k_helmholtz(LoopArgs a, const int32_t* __restrict__ perm, float kk, int qw0, int64_t n, int r0,
-                float2* __restrict__ u) {
+    k_helmholtz(LoopArgs a, const int32_t* __restrict__ perm, float kk, int qw0, int64_t n, int r0, HelmOut out) {
     HelmOp<K, R, COMP, PRECISE> op;
     op.rec = a.rec;
     op.perm = perm;
@@ -176,12 +178,12 @@ __global__ void __launch_bounds__(kLoopThreads, 4)
     op.qw0 = qw0;
     op.n = n;
     op.r0 = r0;
-    op.u = u;
+    op.out = out;
     warp_item_loop<K, G>(a, op);
 }
 
 template <int K, int G, int R, bool COMP, bool PRECISE>
-int launch_helm(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, float2* u, cudaStream_t s) {
+int launch_helm(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, HelmOut u, cudaStream_t s) {
     auto kern = k_helmholtz<K, G, R, COMP, PRECISE>;
     const size_t smem = loop_smem_bytes(a.tile, a.words, HelmOp<K, R, COMP, PRECISE>::kOuts, G);
     P2P_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -197,11 +199,11 @@ int launch_helm(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk,
 }
 
 // per-variant dispatchers (each in its own translation unit)
-int launch_helm_fast(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, float2* u,
+int launch_helm_fast(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                      cudaStream_t s);
-int launch_helm_plain(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, float2* u,
+int launch_helm_plain(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                       cudaStream_t s);
-int launch_helm_precise(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, float2* u,
+int launch_helm_precise(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                         cudaStream_t s);
 
 }  // namespace p2p

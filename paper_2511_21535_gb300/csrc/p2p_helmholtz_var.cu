@@ -6,7 +6,7 @@
 namespace p2p {
 
 template <int G, bool COMP, bool PRECISE>
-static int var_g(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, float2* u,
+static int var_g(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                  cudaStream_t s) {
     switch (R) {
         case 1: return launch_helm<1, G, 1, COMP, PRECISE>(p, a, perm, kk, r0, u, s);
@@ -17,13 +17,13 @@ static int var_g(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk
     }
 }
 
-int launch_helm_plain(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, float2* u,
+int launch_helm_plain(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                       cudaStream_t s) {
     return p->group >= 2 ? var_g<4, false, false>(p, a, perm, kk, r0, R, u, s)
                          : var_g<1, false, false>(p, a, perm, kk, r0, R, u, s);
 }
 
-int launch_helm_precise(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, float2* u,
+int launch_helm_precise(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                         cudaStream_t s) {
     const bool comp = !(p->flags & P2P_PLAN_PLAIN_FP32);
     if (p->group >= 2)

@@ -30,9 +30,18 @@ __global__ void k_records_gravity(const float* __restrict__ pos, const float* __
     rec[s] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass[i]);
 }
 
+// right-hand side r of particle i: q[r] for r < split, conj(q2[r - split]) after
+// (a forward+adjoint pair runs as one operator: conj(P) y = conj(P conj(y)))
+__device__ __forceinline__ float2 rhs_value(const float2* __restrict__ q, const float2* __restrict__ q2, int split,
+                                            int64_t n, int r, int64_t i) {
+    if (r < split) return q[(int64_t)r * n + i];
+    const float2 v = q2[(int64_t)(r - split) * n + i];
+    return make_float2(v.x, -v.y);
+}
+
 __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2* __restrict__ q,
-                                    const int32_t* __restrict__ perm, int64_t n, int nrhs, int words,
-                                    float4* __restrict__ rec) {
+                                    const float2* __restrict__ q2, int split, const int32_t* __restrict__ perm,
+                                    int64_t n, int nrhs, int words, float4* __restrict__ rec) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm[s];
@@ -40,8 +49,8 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
     r[0] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], 0.0f);
     for (int w = 1; w < words; ++w) {
         const int r0 = 2 * (w - 1), r1 = r0 + 1;
-        const float2 a = q[(int64_t)r0 * n + i];
-        const float2 b = (r1 < nrhs) ? q[(int64_t)r1 * n + i] : make_float2(0.0f, 0.0f);
+        const float2 a = rhs_value(q, q2, split, n, r0, i);
+        const float2 b = (r1 < nrhs) ? rhs_value(q, q2, split, n, r1, i) : make_float2(0.0f, 0.0f);
         r[w] = make_float4(a.x, a.y, b.x, b.y);
     }
 }
@@ -254,7 +263,7 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
     return P2P_OK;
 }
 
-int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaStream_t s) {
+int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaStream_t s, const void* strength2) {
     const Layout& L = p->L;
     const int64_t n = p->n;
     const int32_t* perm = at<int32_t>(ws, L.perm);
@@ -262,7 +271,9 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
     if (p->kind == P2P_GRAVITY) {
         k_records_gravity<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float*>(strength), perm, n, rec);
     } else {
-        k_records_helmholtz<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float2*>(strength), perm, n,
+        const int split = strength2 ? p->split : p->nrhs;
+        k_records_helmholtz<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float2*>(strength),
+                                                              static_cast<const float2*>(strength2), split, perm, n,
                                                               p->nrhs, p->rec_words, rec);
     }
     P2P_LAUNCH_CHECK();

@@ -15,7 +15,7 @@ import torch
 from . import build as _build
 
 GRAVITY, HELMHOLTZ = 0, 1
-LAYOUTS = {"indirect": 0, "redundant": 1}
+LAYOUTS = {"indirect": 0, "redundant": 1, "auto": 2}
 PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING, PLAN_ADJOINT = 0x1, 0x2, 0x4, 0x8
 FLAG_DOMAIN, FLAG_TIMEOUT, FLAG_CAPACITY = 0x1, 0x2, 0x4
 
@@ -29,7 +29,10 @@ EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_
            "p2p_plan_workspace_bytes", "p2p_plan_set_tuning", "p2p_tree_build", "p2p_tree_import",
            "p2p_restructure", "p2p_gravity", "p2p_helmholtz", "p2p_plan_array", "p2p_read_counters",
            "p2p_plan_timing", "p2p_launch_count", "p2p_gravity_noalloc",
-           "p2p_measure_pipes", "p2p_helmholtz_adjoint", "p2p_gravity_adjoint")
+           "p2p_measure_pipes", "p2p_helmholtz_adjoint", "p2p_gravity_adjoint",
+           "p2p_batch_create", "p2p_batch_destroy", "p2p_batch_workspace_bytes", "p2p_batch_build",
+           "p2p_batch_set_tuning", "p2p_batch_run", "p2p_batch_autotune", "p2p_batch_capture",
+           "p2p_batch_launch", "p2p_batch_counters")
 
 
 class P2PError(RuntimeError):
@@ -79,6 +82,16 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_measure_pipes": (I, [ctypes.POINTER(ctypes.c_double), P]),
         "p2p_helmholtz_adjoint": (I, [P, F, P, P, P, P, P, P, SZ, P]),
         "p2p_gravity_adjoint": (I, [P, F, P, P, P, P, P, P, P, SZ, P]),
+        "p2p_batch_create": (I, [ctypes.POINTER(P), I, I, P, P, P, P, I, I, I, U]),
+        "p2p_batch_destroy": (I, [P]),
+        "p2p_batch_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
+        "p2p_batch_build": (I, [P, P, P, SZ, P]),
+        "p2p_batch_set_tuning": (I, [P, I, I, I, I, I]),
+        "p2p_batch_run": (I, [P, F, P, P, P, P, P, P, SZ, P]),
+        "p2p_batch_autotune": (I, [P, F, P, P, P, P, P, P, SZ, P, ctypes.POINTER(I), ctypes.POINTER(F)]),
+        "p2p_batch_capture": (I, [P, F, P, P, P, P, P, P, SZ]),
+        "p2p_batch_launch": (I, [P, P]),
+        "p2p_batch_counters": (I, [P, P, ctypes.POINTER(I64), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -367,3 +380,105 @@ def gravity_p2p(pos, mass, plan: Plan, eps: float):
     """Differentiable softened gravity (phi, acc); gradients flow to mass and pos.
     The plan must be created with adjoint=True."""
     return _GravityFn.apply(pos, mass, plan, eps)
+
+
+# ---------------------------------------------------------------------------
+# batched instances: one persistent launch (optionally one CUDA graph)
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """Many Helmholtz instances with concatenated data; see p2p_batch_* in the header.
+
+    instances: sequence of (n, level, lo, edge).  pair=True computes u = P q and
+    g = conj(P) y in the same launch.
+    """
+
+    def __init__(self, instances, nrhs: int, k: float, pair: bool = False, layout: str = "auto",
+                 plain_fp32: bool = False, device=None):
+        lib = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.nrhs, self.k, self.pair = int(nrhs), float(k), bool(pair)
+        I = len(instances)
+        n = (ctypes.c_int64 * I)(*[int(x[0]) for x in instances])
+        lv = (ctypes.c_int * I)(*[int(x[1]) for x in instances])
+        lo = (ctypes.c_float * (3 * I))(*[float(v) for x in instances for v in x[2]])
+        ed = (ctypes.c_float * I)(*[float(x[3]) for x in instances])
+        self.sizes = [int(x[0]) for x in instances]
+        self.offsets = [0]
+        for s_ in self.sizes:
+            self.offsets.append(self.offsets[-1] + s_)
+        self.N = self.offsets[-1]
+        h = ctypes.c_void_p()
+        _check(lib.p2p_batch_create(ctypes.byref(h), HELMHOLTZ, I, n, lv, lo, ed, self.nrhs, 1 if pair else 0,
+                                    LAYOUTS[layout], PLAN_PLAIN_FP32 if plain_fp32 else 0), "p2p_batch_create")
+        self._h = h
+        nb = ctypes.c_size_t()
+        _check(lib.p2p_batch_workspace_bytes(h, ctypes.byref(nb)), "p2p_batch_workspace_bytes")
+        self.ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        self._bufs = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.p2p_batch_destroy(h)
+            self._h = None
+
+    def _w(self):
+        return ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_size_t(self.ws.numel())
+
+    def build(self, pos, stream=None):
+        _need(pos, torch.float32, (self.N, 3), self.device)
+        w, b = self._w()
+        _check(load().p2p_batch_build(self._h, _ptr(pos), w, b, _stream(stream)), "p2p_batch_build")
+
+    def _args(self, pos, q, y, u, g):
+        _need(pos, torch.float32, (self.N, 3), self.device)
+        _need(q, torch.complex64, (self.nrhs, self.N), self.device)
+        if u is None:
+            u = torch.empty(self.nrhs, self.N, dtype=torch.complex64, device=self.device)
+        if self.pair:
+            _need(y, torch.complex64, (self.nrhs, self.N), self.device)
+            if g is None:
+                g = torch.empty(self.nrhs, self.N, dtype=torch.complex64, device=self.device)
+        return u, g
+
+    def run(self, pos, q, y=None, u=None, g=None, stream=None):
+        u, g = self._args(pos, q, y, u, g)
+        w, b = self._w()
+        _check(load().p2p_batch_run(self._h, self.k, _ptr(pos), _ptr(q), _ptr(y), _ptr(u), _ptr(g), w, b,
+                                    _stream(stream)), "p2p_batch_run")
+        return (u, g) if self.pair else u
+
+    def set_tuning(self, layout: str, targets_per_lane: int, tile: int, warps_per_item: int, ctas_per_sm: int = 0):
+        _check(load().p2p_batch_set_tuning(self._h, LAYOUTS[layout], targets_per_lane, tile, ctas_per_sm,
+                                           warps_per_item), "p2p_batch_set_tuning")
+
+    def autotune(self, pos, q, y=None, u=None, g=None, stream=None) -> dict:
+        u, g = self._args(pos, q, y, u, g)
+        best = (ctypes.c_int * 5)()
+        ms = ctypes.c_float()
+        w, b = self._w()
+        _check(load().p2p_batch_autotune(self._h, self.k, _ptr(pos), _ptr(q), _ptr(y), _ptr(u), _ptr(g), w, b,
+                                         _stream(stream), best, ctypes.byref(ms)), "p2p_batch_autotune")
+        inv = {v: k_ for k_, v in LAYOUTS.items()}
+        return {"layout": inv[best[0]], "targets_per_lane": best[1], "tile": best[2], "warps_per_item": best[4],
+                "ms": ms.value}
+
+    def capture(self, pos, q, y=None, u=None, g=None):
+        """Capture run() on these buffers into a CUDA graph; returns the outputs it writes."""
+        u, g = self._args(pos, q, y, u, g)
+        self._bufs = (pos, q, y, u, g)     # the graph keeps using these addresses
+        w, b = self._w()
+        _check(load().p2p_batch_capture(self._h, self.k, _ptr(pos), _ptr(q), _ptr(y), _ptr(u), _ptr(g), w, b),
+               "p2p_batch_capture")
+        return (u, g) if self.pair else u
+
+    def launch(self, stream=None):
+        _check(load().p2p_batch_launch(self._h, _stream(stream)), "p2p_batch_launch")
+
+    def counters(self, stream=None) -> dict:
+        out = (ctypes.c_int64 * len(COUNTERS))()
+        st = load().p2p_batch_counters(self._h, ctypes.c_void_p(self.ws.data_ptr()), out, _stream(stream))
+        res = {k_: int(v) for k_, v in zip(COUNTERS, out)}
+        res["status"] = int(st)
+        return res

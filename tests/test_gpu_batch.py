@@ -1,0 +1,133 @@
+"""Batched instances in one persistent launch (and one CUDA graph): results
+against the FP64 oracle per instance, and bitwise against per-instance plans
+with the same tuning (each work item does identical arithmetic)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_21535_gb300 import p2p
+from paper_2511_21535_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL_COMPLEX = 2e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def random_instance(n, level, nrhs, seed):
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 3), dtype=np.float32)
+    q = wl.complex_normal((nrhs, n), rng)
+    return wl.Problem("random", pos, q, level, (0.0, 0.0, 0.0), 1.0, "helmholtz", k=float(np.float32(2 * math.pi)))
+
+
+def make_batch(probs, nrhs, pair, layout, dev):
+    k = probs[0].k
+    b = p2p.Batch([(p.n, p.level, p.lo, p.edge) for p in probs], nrhs, k, pair=pair, layout=layout, device=dev)
+    pos = torch.from_numpy(np.concatenate([p.pos for p in probs])).to(dev)
+    q = torch.from_numpy(np.concatenate([p.strength for p in probs], axis=1)).to(dev)
+    rng = np.random.default_rng(99)
+    y = torch.from_numpy(wl.complex_normal((nrhs, b.N), rng)).to(dev) if pair else None
+    return b, pos, q, y
+
+
+def small_set(nrhs):
+    probs = [wl.grid_helmholtz(edge_points=e, nrhs=nrhs, seed=s) for s, e in enumerate((16, 24, 32, 16, 24))]
+    probs.append(random_instance(5000, 3, nrhs, 7))
+    for p in probs:
+        p.k = probs[0].k
+    return probs
+
+
+@pytest.mark.parametrize("layout", ["indirect", "redundant", "auto"])
+@pytest.mark.parametrize("nrhs,pair", [(1, False), (2, True), (3, True)])
+def test_batch_matches_oracle(dev, layout, nrhs, pair):
+    probs = small_set(nrhs)
+    b, pos, q, y = make_batch(probs, nrhs, pair, layout, dev)
+    b.build(pos)
+    out = b.run(pos, q, y)
+    u, g = (out if pair else (out, None))
+    torch.cuda.synchronize()
+    u = u.cpu().numpy()
+    g = g.cpu().numpy() if pair else None
+    yy = y.cpu().numpy() if pair else None
+    for i, p in enumerate(probs):
+        o0, o1 = b.offsets[i], b.offsets[i + 1]
+        ou, _ = oracle.helmholtz(p.pos, p.strength, p.level, p.lo, p.edge, p.k)
+        assert rel_l2(u[:, o0:o1], ou) <= TOL_COMPLEX
+        if pair:
+            og, _ = oracle.helmholtz_adjoint(p.pos, p.strength, yy[:, o0:o1], p.level, p.lo, p.edge, p.k)
+            assert rel_l2(g[:, o0:o1], og) <= TOL_COMPLEX
+    c = b.counters()
+    assert c["status"] == 0
+    assert c["pairs"] == sum(oracle.pair_count(p.pos, p.level, p.lo, p.edge) for p in probs)
+
+
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+def test_batch_bitwise_equals_per_instance_plans(dev, layout):
+    nrhs = 2
+    probs = small_set(nrhs)
+    b, pos, q, y = make_batch(probs, nrhs, False, layout, dev)
+    b.build(pos)
+    b.set_tuning(layout, 1, 64, 4)
+    u = b.run(pos, q).cpu().numpy()
+    for i, p in enumerate(probs):
+        plan = p2p.Plan("helmholtz", p.n, p.level, p.lo, p.edge, nrhs=nrhs, layout=layout, device=dev)
+        plan.set_tuning(1, 64, 0, 4)
+        tp = torch.from_numpy(p.pos).to(dev)
+        plan.tree_build(tp)
+        plan.restructure(tp, torch.from_numpy(p.strength).to(dev))
+        ui = plan.helmholtz(p.k).cpu().numpy()
+        np.testing.assert_array_equal(u[:, b.offsets[i]:b.offsets[i + 1]], ui)
+
+
+def test_batch_autotune_and_graph(dev):
+    nrhs = 2
+    probs = small_set(nrhs)
+    b, pos, q, y = make_batch(probs, nrhs, True, "auto", dev)
+    b.build(pos)
+    best = b.autotune(pos, q, y)
+    assert best["layout"] in ("indirect", "redundant") and best["ms"] > 0
+    u0, g0 = b.run(pos, q, y)
+    u1, g1 = b.capture(pos, q, y)
+    u1.zero_()
+    g1.zero_()
+    b.launch()
+    b.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(u0, u1) and torch.equal(g0, g1)
+
+
+def test_batched_64_instances_sampled(dev):
+    probs = wl.batched_helmholtz()
+    nrhs = 8
+    b, pos, q, y = make_batch(probs, nrhs, True, "indirect", dev)
+    b.build(pos)
+    u, g = b.run(pos, q, y)
+    torch.cuda.synchronize()
+    c = b.counters()
+    assert c["status"] == 0
+    # closed form for full grids of B^3 boxes: t^2 (3B-2)^3 - N per instance
+    expect = sum(64 * 64 * (3 * (p.extra["edge_points"] // 4) - 2) ** 3 - p.n for p in probs)
+    assert c["pairs"] == expect
+    u = u.cpu().numpy()
+    g = g.cpu().numpy()
+    yy = y.cpu().numpy()
+    rng = np.random.default_rng(4)
+    for i in (0, 5, int(np.argmax([p.n for p in probs]))):
+        p = probs[i]
+        o0 = b.offsets[i]
+        tg = rng.choice(p.n, min(p.n, 1500), replace=False)
+        ou, _ = oracle.helmholtz(p.pos, p.strength, p.level, p.lo, p.edge, p.k, targets=tg)
+        assert rel_l2(u[:, o0 + tg], ou) <= TOL_COMPLEX
+    p = probs[0]
+    og, _ = oracle.helmholtz_adjoint(p.pos, p.strength, yy[:, 0:p.n], p.level, p.lo, p.edge, p.k)
+    assert rel_l2(g[:, 0:p.n], og) <= TOL_COMPLEX
