@@ -285,6 +285,18 @@ int p2p_batch_launch(p2p_batch* batch, void* stream);
 /* counters of the combined structure (as p2p_read_counters; pairs are geometric) */
 int p2p_batch_counters(const p2p_batch* batch, const void* ws, int64_t* out, void* stream);
 
+/*
+ * Self-test of the bounded device waits (a library check; the paper has no
+ * counterpart).  Every wait of the P2P kernels on an mbarrier gives up after
+ * ~2 s of global time, records P2P_FLAG_TIMEOUT and lets its copies land
+ * before the warp leaves, so a lost signal can never hang the GPU.  This
+ * call runs one warp waiting on an mbarrier that nothing completes, with a
+ * limit of limit_ns (1 .. 1e10): it returns P2P_ERR_TIMEOUT when the wait
+ * expired as designed (P2P_OK would mean the mechanism is broken).  flags_dev
+ * is a caller-owned device uint32 (overwritten).  Synchronises the stream.
+ */
+int p2p_selftest_bounded_wait(uint64_t limit_ns, uint32_t* flags_dev, void* stream);
+
 /* identifiers of workspace arrays for p2p_plan_array */
 typedef enum {
     P2P_ARR_PERM = 0,        /* int32 [n]               sorted -> original index    */

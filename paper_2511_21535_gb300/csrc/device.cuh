@@ -138,14 +138,25 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-// Warp-uniform bounded wait on an mbarrier phase.  Returns false if the
-// iteration limit expired (the caller records P2P_FLAG_TIMEOUT).
-constexpr uint32_t kWaitLimit = 1u << 24;
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0;; ++it) {
-        bool done = mbar_try_wait(bar, parity);
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Warp-uniform bounded wait on an mbarrier phase: gives up after limit_ns of
+// global time (checked every 64 polls).  Returns false if the limit expired
+// (the caller records P2P_FLAG_TIMEOUT).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        const bool done = mbar_try_wait(bar, parity);
         if (__all_sync(0xffffffffu, done)) return true;
-        if (it >= kWaitLimit) return false;
+        if ((it & 63u) == 0) {
+            const bool late = (global_ns() - t0) > limit_ns;
+            if (__any_sync(0xffffffffu, late)) return false;
+        }
     }
 }
 

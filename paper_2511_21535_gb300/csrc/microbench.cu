@@ -4,6 +4,7 @@
 // lane-operations per SM per clock, independent of the clock frequency, and
 // the CUDA-event time of the launch gives the SM clock during the run.
 #include "common.cuh"
+#include "device.cuh"
 
 namespace p2p {
 
@@ -51,9 +52,36 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_mufu(int iters, float* sink, 
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// One warp initialises an mbarrier that expects one arrival and never gets
+// it, then waits on it with a limit of limit_ns: the wait must run out and
+// the kernel must record P2P_FLAG_TIMEOUT and return.  No copy is in flight.
+__global__ void k_selftest_wait(uint64_t limit_ns, uint32_t* flags) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (!warp_wait(&bar, 0, limit_ns)) {
+        if (threadIdx.x == 0) atomicOr(flags, P2P_FLAG_TIMEOUT);
+    }
+}
+
 }  // namespace p2p
 
 using namespace p2p;
+
+extern "C" int p2p_selftest_bounded_wait(uint64_t limit_ns, uint32_t* flags_dev, void* stream) {
+    if (!flags_dev || limit_ns == 0 || limit_ns > 10000000000ull) return P2P_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    P2P_CUDA_TRY(cudaMemsetAsync(flags_dev, 0, sizeof(uint32_t), s));
+    k_selftest_wait<<<1, 32, 0, s>>>(limit_ns, flags_dev);
+    P2P_LAUNCH_CHECK();
+    uint32_t h = 0;
+    P2P_CUDA_TRY(cudaMemcpyAsync(&h, flags_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    P2P_CUDA_TRY(cudaStreamSynchronize(s));
+    return (h & P2P_FLAG_TIMEOUT) ? P2P_ERR_TIMEOUT : P2P_OK;
+}
 
 extern "C" int p2p_measure_pipes(double* out, void* stream) {
     if (!out) return P2P_ERR_INVALID_ARG;

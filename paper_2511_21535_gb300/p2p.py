@@ -32,7 +32,7 @@ EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_
            "p2p_measure_pipes", "p2p_helmholtz_adjoint", "p2p_gravity_adjoint",
            "p2p_batch_create", "p2p_batch_destroy", "p2p_batch_workspace_bytes", "p2p_batch_build",
            "p2p_batch_set_tuning", "p2p_batch_run", "p2p_batch_autotune", "p2p_batch_capture",
-           "p2p_batch_launch", "p2p_batch_counters")
+           "p2p_batch_launch", "p2p_batch_counters", "p2p_selftest_bounded_wait")
 
 
 class P2PError(RuntimeError):
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_batch_capture": (I, [P, F, P, P, P, P, P, P, SZ]),
         "p2p_batch_launch": (I, [P, P]),
         "p2p_batch_counters": (I, [P, P, ctypes.POINTER(I64), P]),
+        "p2p_selftest_bounded_wait": (I, [ctypes.c_uint64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -117,6 +118,14 @@ def measure_pipes(stream=None) -> dict:
     out = (ctypes.c_double * 4)()
     _check(load().p2p_measure_pipes(out, _stream(stream)), "p2p_measure_pipes")
     return {"fp32": out[0], "mufu_rsqrt": out[1], "mufu_sin": out[2], "sm_mhz": out[3]}
+
+
+def selftest_bounded_wait(limit_ns: int = 2_000_000, device=None, stream=None) -> int:
+    """Run a wait that nothing completes with the given limit; returns the status
+    (P2P_ERR_TIMEOUT = 4 is the expected outcome)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    flags = torch.zeros(1, dtype=torch.int32, device=dev)
+    return int(load().p2p_selftest_bounded_wait(int(limit_ns), _ptr(flags), _stream(stream)))
 
 
 def _check(st: int, what: str):
