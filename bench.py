@@ -64,6 +64,8 @@ def make_problem(name: str):
         return wl.plummer_gravity()
     if name == "grid_helmholtz_128":
         return wl.grid_helmholtz(edge_points=128)
+    if name == "plummer_gravity_1m":
+        return wl.plummer_gravity(n=1 << 20, level=6)
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -43,7 +43,7 @@ struct GravityOp {
 
     template <bool CHECK>
     __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
-#pragma unroll 4
+#pragma unroll 8
         for (int j = 0; j < cnt; ++j) {
             const float4 src = sm[j];
 #pragma unroll

@@ -7,9 +7,12 @@ namespace p2p {
 template <int K, int G>
 static int fast_kg(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                    cudaStream_t s) {
+    const bool w2 = a.words == 2;   // records of one or two right-hand sides
     switch (R) {
-        case 1: return launch_helm<K, G, 1, true, false>(p, a, perm, kk, r0, u, s);
-        case 2: return launch_helm<K, G, 2, true, false>(p, a, perm, kk, r0, u, s);
+        case 1: return w2 ? launch_helm<K, G, 1, true, false, 2>(p, a, perm, kk, r0, u, s)
+                          : launch_helm<K, G, 1, true, false>(p, a, perm, kk, r0, u, s);
+        case 2: return w2 ? launch_helm<K, G, 2, true, false, 2>(p, a, perm, kk, r0, u, s)
+                          : launch_helm<K, G, 2, true, false>(p, a, perm, kk, r0, u, s);
         case 4: return launch_helm<K, G, 4, true, false>(p, a, perm, kk, r0, u, s);
         case 8: return launch_helm<K, G, 8, true, false>(p, a, perm, kk, r0, u, s);
         default: return P2P_ERR_INVALID_ARG;

@@ -15,7 +15,8 @@
 
 namespace p2p {
 
-template <int K, int R, bool COMP, bool PRECISE>
+// W: record stride in 16-byte words when known at compile time (0 = runtime)
+template <int K, int R, bool COMP, bool PRECISE, int W = 0>
 struct HelmOp {
     static constexpr int kOuts = 2 * R * K;
 
@@ -52,9 +53,10 @@ struct HelmOp {
 
     template <bool CHECK>
     __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
+        const int stride = W ? W : words;
         const float4* rj = sm;
-#pragma unroll 2
-        for (int j = 0; j < cnt; ++j, rj += words) {
+#pragma unroll 4
+        for (int j = 0; j < cnt; ++j, rj += stride) {
             const float4 ps = rj[0];
             float qr[R], qi[R];
 #pragma unroll
@@ -167,10 +169,10 @@ struct HelmOp {
     }
 };
 
-template <int K, int G, int R, bool COMP, bool PRECISE>
+template <int K, int G, int R, bool COMP, bool PRECISE, int W = 0>
 __global__ void __launch_bounds__(kLoopThreads, 4)
     k_helmholtz(LoopArgs a, const int32_t* __restrict__ perm, float kk, int qw0, int64_t n, int r0, HelmOut out) {
-    HelmOp<K, R, COMP, PRECISE> op;
+    HelmOp<K, R, COMP, PRECISE, W> op;
     op.rec = a.rec;
     op.perm = perm;
     op.kk = kk;
@@ -182,10 +184,10 @@ __global__ void __launch_bounds__(kLoopThreads, 4)
     warp_item_loop<K, G>(a, op);
 }
 
-template <int K, int G, int R, bool COMP, bool PRECISE>
+template <int K, int G, int R, bool COMP, bool PRECISE, int W = 0>
 int launch_helm(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, HelmOut u, cudaStream_t s) {
-    auto kern = k_helmholtz<K, G, R, COMP, PRECISE>;
-    const size_t smem = loop_smem_bytes(a.tile, a.words, HelmOp<K, R, COMP, PRECISE>::kOuts, G);
+    auto kern = k_helmholtz<K, G, R, COMP, PRECISE, W>;
+    const size_t smem = loop_smem_bytes(a.tile, a.words, HelmOp<K, R, COMP, PRECISE, W>::kOuts, G);
     P2P_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = p->ctas_per_sm;
     if (per_sm <= 0) {
