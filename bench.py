@@ -35,7 +35,7 @@ KERNEL_SOURCES = {"helmholtz": ["common.cuh", "device.cuh", "p2p_loop.cuh", "p2p
                   "gravity": ["common.cuh", "device.cuh", "p2p_loop.cuh", "p2p_gravity.cu"]}
 
 
-def kernel_traffic(kind: str, workload: str, layout: str):
+def kernel_traffic(kind: str, workload: str, layout: str, n: int):
     """DRAM bytes per launch from the committed ncu capture, if the kernel's
     sources are unchanged since that capture (else None)."""
     import hashlib
@@ -45,6 +45,8 @@ def kernel_traffic(kind: str, workload: str, layout: str):
     except (OSError, ValueError):
         return None
     if not rec or rec.get("workload") != workload or rec.get("layout") != layout:
+        return None
+    if rec.get("n") is not None and rec["n"] != n:
         return None
     h = hashlib.sha256()
     for f in rec["source_files"]:
@@ -334,7 +336,7 @@ def run_gpu(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
         "roofline": {"bound": "alu", "pipe": pipe, "kernel": f"k_{prob.kind}", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak,
-                     "traffic": kernel_traffic(prob.kind, prob.name, layout),
+                     "traffic": kernel_traffic(prob.kind, prob.name, layout, prob.n),
                      "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms,
                      "peak_source": "pipe rates measured by p2p_measure_pipes x SMs x sampled SM clock",
                      "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in pipes.items()}},
