@@ -3,7 +3,10 @@
 One step = the whole hot path on one batch of synthetic input already in HBM:
 tree build (Morton keys, radix sort, box CSR, E2 neighbour lists) ->
 restructuring (box-ordered records, redundant per-box streams) -> P2P kernel
-(outputs written in original order).  Default workload: the Helmholtz near
+(outputs written in original order).  The step is captured once in a CUDA
+graph and replayed (--no-graph launches it kernel by kernel); phase times come
+from CUDA events the library records on the launching stream (external event
+nodes inside the graph).  Default workload: the Helmholtz near
 field on a 64^3 grid at lambda/10 spacing, 4^3-point leaf boxes, one complex
 right-hand side, redundant layout.
 
@@ -197,6 +200,7 @@ def run_gpu(args, rank, world, local_rank):
 
     # optionally capture the whole step (tree, restructuring, operator) in one CUDA graph
     run, graph, graph_note, launches_per_replay = step, None, None, None
+    graph_events = False
     if args.graph:
         try:
             side = torch.cuda.Stream(device=dev)
@@ -215,6 +219,12 @@ def run_gpu(args, rank, world, local_rank):
             torch.cuda.synchronize()
             run = graph.replay
             graph_note = "whole step captured in one CUDA graph"
+            try:                       # phase events recorded by the replay itself
+                plan.timing()
+                graph_events = True
+                graph_note += "; phase times from external event nodes of the replay"
+            except Exception:
+                graph_events = False
         except Exception as e:  # report and fall back to stream launches
             graph, run = None, step
             graph_note = f"graph capture failed: {type(e).__name__}: {e}"[:200]
@@ -233,12 +243,12 @@ def run_gpu(args, rank, world, local_rank):
         ev[i][0].record(stream)
         run()
         ev[i][1].record(stream)
-        if graph is None:
-            t = plan.timing()      # waits for this step's events
+        if graph is None or graph_events:
+            t = plan.timing()      # waits for this step's events (external event nodes in a graph)
             for k, v in t.items():
                 phases[k].append(v)
     torch.cuda.synchronize()
-    if graph is not None:
+    if graph is not None and not graph_events:
         # event timing inside a graph replay is not available: phase times
         # come from the same step launched on the stream, right after
         for _ in range(min(args.steps, 50)):
@@ -525,7 +535,8 @@ def main():
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--group", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="launch the step's kernels on the stream instead of replaying one captured CUDA graph")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -62,12 +62,21 @@ int check_ws(const Plan* p, const void* ws, size_t ws_bytes) {
     return P2P_OK;
 }
 
+// Inside a stream capture the events become external event-record nodes, so
+// a replayed graph still records them and their elapsed time can be read.
+static void ev_record(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, s);
+}
 static void ev_begin(Plan* p, int ph, cudaStream_t s) {
-    if (p->timing) cudaEventRecord(p->ev[ph][0], s);
+    if (p->timing) ev_record(p->ev[ph][0], s);
 }
 static void ev_end(Plan* p, int ph, cudaStream_t s) {
     if (p->timing) {
-        cudaEventRecord(p->ev[ph][1], s);
+        ev_record(p->ev[ph][1], s);
         p->ev_valid[ph] = 1;
     }
 }

@@ -55,7 +55,7 @@ struct HelmOp {
     __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
         const int stride = W ? W : words;
         const float4* rj = sm;
-#pragma unroll 4
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j, rj += stride) {
             const float4 ps = rj[0];
             float qr[R], qi[R];
@@ -170,7 +170,7 @@ struct HelmOp {
 };
 
 template <int K, int G, int R, bool COMP, bool PRECISE, int W = 0>
-__global__ void __launch_bounds__(kLoopThreads, 4)
+__global__ void __launch_bounds__(kLoopThreads, 6)
     k_helmholtz(LoopArgs a, const int32_t* __restrict__ perm, float kk, int qw0, int64_t n, int r0, HelmOut out) {
     HelmOp<K, R, COMP, PRECISE, W> op;
     op.rec = a.rec;
