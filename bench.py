@@ -74,8 +74,8 @@ def make_problem(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def workload_config(prob, layout):
-    cfg = {"workload": prob.name, "n": prob.n, "level": prob.level, "kernel": prob.kind, "layout": layout,
+def workload_config(prob, layout, pattern=False):
+    cfg = {"kernel_mode": "pattern table" if pattern else "direct","workload": prob.name, "n": prob.n, "level": prob.level, "kernel": prob.kind, "layout": layout,
            "nrhs": prob.nrhs, "l2": "flushed between steps (512 MiB write)", "inputs": "seeded synthetic"}
     if prob.kind == "gravity":
         cfg["eps"] = prob.eps
@@ -166,6 +166,8 @@ def run_gpu(args, rank, world, local_rank):
                     timing=True, device=dev)
     if args.tpl:
         plan.set_tuning(args.tpl, args.tile, args.ctas, args.group)
+    if args.pattern:
+        plan.set_grid(wl.SPACING, wl.LEAF_EDGE_POINTS)
     pos = torch.from_numpy(prob.pos).to(dev)
     strength = torch.from_numpy(prob.strength).to(dev)
     out_a = torch.empty(prob.n, dtype=torch.float32, device=dev)
@@ -318,7 +320,11 @@ def run_gpu(args, rank, world, local_rank):
     f_mhz = csum["sm_mhz"] or pipes["sm_mhz"] or 2070.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mufu_rate = min(pipes["mufu_rsqrt"], pipes["mufu_sin"])
-    if prob.kind == "helmholtz" and prob.nrhs <= 2:
+    if prob.kind == "helmholtz" and args.pattern:
+        # table lookups: one 8-byte shared load per lane and pair; 128 B/clk/SM of shared bandwidth
+        pipe, per_pair = "smem", 8.0
+        peak = 128.0 * sms * f_mhz * 1e6 / per_pair
+    elif prob.kind == "helmholtz" and prob.nrhs <= 2:
         pipe, per_pair = "mufu", 3.0        # rsqrt, sin, cos per geometric pair
         peak = mufu_rate * sms * f_mhz * 1e6 / per_pair
     elif prob.kind == "helmholtz":
@@ -341,7 +347,7 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": workload_config(prob, layout),
+        "config": workload_config(prob, layout, args.pattern),
         "e2e": {"value": world * pairs / (e2e_mean * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
         "roofline": {"bound": "alu", "pipe": pipe, "kernel": f"k_{prob.kind}", "achieved": achieved / 1e9,
@@ -538,6 +544,7 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the step's kernels on the stream instead of replaying one captured CUDA graph")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--pattern", action="store_true", help="tabulated-G kernel for grid workloads")
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

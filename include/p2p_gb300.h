@@ -90,6 +90,8 @@ typedef enum { P2P_LAYOUT_INDIRECT = 0, P2P_LAYOUT_REDUNDANT = 1, P2P_LAYOUT_AUT
 #define P2P_FLAG_TIMEOUT  0x2u     /* a bounded wait expired in a kernel             */
 #define P2P_FLAG_CAPACITY 0x4u     /* an imported structure overflowed a workspace   */
                                    /* array; the affected step was skipped          */
+#define P2P_FLAG_LATTICE  0x8u     /* pattern mode: a point is off the grid lattice */
+                                   /* or its box; the operator call was skipped     */
 
 /* limits of this build */
 #define P2P_MAX_N      (1LL << 26) /* particles per plan (27 n must fit in int32)   */
@@ -140,6 +142,22 @@ int p2p_plan_workspace_bytes(const p2p_plan* plan, size_t* bytes);
  */
 int p2p_plan_set_tuning(p2p_plan* plan, int targets_per_lane, int tile, int ctas_per_sm,
                         int warps_per_item);
+
+/*
+ * Pattern mode for regular grids (Helmholtz): the precomputed-pattern P2P of
+ * the DBIM solver (Section 5.1).  Every particle must sit on the lattice
+ * lo + (i + 1/2) h (per axis, i integer) and every leaf box must hold
+ * points_per_box lattice points per edge (edge / 2^level = points_per_box * h).
+ * G is then tabulated once per wavenumber for the (4 points_per_box - 1)^3
+ * lattice displacements between neighbouring boxes, in double precision at
+ * the ideal lattice distances, and the kernel reads it from shared memory
+ * instead of evaluating rsqrt/sin/cos per pair.  Particles off the lattice
+ * (by more than 1 % of h) or outside their lattice box set P2P_FLAG_LATTICE
+ * during p2p_restructure and the next operator call computes nothing.
+ * points_per_box in 1..4 (the table must fit in shared memory); 0 disables.
+ * Takes effect at the next p2p_restructure.
+ */
+int p2p_plan_set_grid(p2p_plan* plan, float h, int points_per_box);
 
 /*
  * Collect, part 1 -- build the leaf-box structure from positions:

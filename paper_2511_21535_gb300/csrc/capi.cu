@@ -1,5 +1,6 @@
 // C ABI: plans, workspace layout, argument checks, phase timing.
 #include <atomic>
+#include <cmath>
 #include <new>
 
 #include "common.cuh"
@@ -46,6 +47,7 @@ void compute_layout(Plan* p) {
     L.src = take((size_t)n * p->rec_alloc_words * 16);
     L.box_S = take((bc + 1) * 4);
     L.items = take((size_t)p->items_cap * 8);
+    L.pattern = (p->kind == P2P_HELMHOLTZ) ? take((size_t)kPatternMaxEntries * 8) : 0;
     if (p->layout == P2P_LAYOUT_REDUNDANT) {
         L.red_start = take((bc + 1) * 4);
         L.red_self = take(bc * 4);
@@ -232,6 +234,25 @@ int p2p_plan_set_tuning(p2p_plan* h, int targets_per_lane, int tile, int ctas_pe
     return P2P_OK;
 }
 
+int p2p_plan_set_grid(p2p_plan* h, float grid_h, int points_per_box) {
+    if (!h) return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->p;
+    if (p->kind != P2P_HELMHOLTZ) return P2P_ERR_UNSUPPORTED;
+    if (points_per_box == 0) {
+        p->pattern = 0;
+        p->src_ready = 0;
+        return P2P_OK;
+    }
+    if (!(grid_h > 0.0f) || points_per_box < 1 || points_per_box > 4) return P2P_ERR_INVALID_ARG;
+    // the leaf box must hold points_per_box lattice points per edge
+    const double box = (double)p->edge / (double)(1 << p->level);
+    if (std::fabs(box / ((double)grid_h * points_per_box) - 1.0) > 1e-5) return P2P_ERR_INVALID_ARG;
+    int st = pattern_setup(p, grid_h, points_per_box);
+    if (st) return st;
+    p->src_ready = 0;
+    return P2P_OK;
+}
+
 int p2p_tree_build(p2p_plan* h, const float* pos, void* ws, size_t ws_bytes, void* stream) {
     if (!h || !pos || (reinterpret_cast<uintptr_t>(pos) & 3u)) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
@@ -298,8 +319,18 @@ int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void
     if (!p->tree_ready || !p->src_ready) return P2P_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ev_begin(p, P2P_PHASE_OPERATOR, s);
-    st = build_items(p, ws, 32 * helmholtz_targets_per_lane(p, k), s);
+    st = build_items(p, ws, 32 * (p->pattern ? (p->tpl >= 2 ? 2 : 1) : helmholtz_targets_per_lane(p, k)), s);
     if (st) return st;
+    if (p->pattern) {
+        ev_begin(p, P2P_PHASE_KERNEL, s);
+        st = launch_helmholtz_pattern(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), k,
+                                      at<float2>(ws, p->L.pattern), HelmOut{static_cast<float2*>(u), nullptr, p->nrhs},
+                                      s);
+        if (st) return st;
+        ev_end(p, P2P_PHASE_KERNEL, s);
+        ev_end(p, P2P_PHASE_OPERATOR, s);
+        return P2P_OK;
+    }
     ev_begin(p, P2P_PHASE_KERNEL, s);
     st = launch_helmholtz_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), k,
                                  HelmOut{static_cast<float2*>(u), nullptr, p->nrhs}, s);
@@ -407,7 +438,7 @@ int p2p_read_counters(const p2p_plan* h, const void* ws, int64_t* out, void* str
     out[P2P_CTR_N_ITEMS] = hdr.n_items;
     if (hdr.flags & P2P_FLAG_TIMEOUT) return P2P_ERR_TIMEOUT;
     if (hdr.flags & P2P_FLAG_DOMAIN) return P2P_ERR_DOMAIN;
-    if (hdr.flags & P2P_FLAG_CAPACITY) return P2P_ERR_INVALID_ARG;
+    if (hdr.flags & (P2P_FLAG_CAPACITY | P2P_FLAG_LATTICE)) return P2P_ERR_INVALID_ARG;
     return P2P_OK;
 }
 

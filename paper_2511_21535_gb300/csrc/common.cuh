@@ -44,7 +44,7 @@ static_assert(offsetof(Header, n_items) == kOpSectionOffset, "header layout");
 struct Layout {                        // byte offsets inside the workspace
     size_t header, keys_a, keys_b, vals_a, perm, sorted_key, hist, scan_tmp, flags,
         box_key, box_start, table, nbr_cnt, nbr_start, nbr_idx, src, box_S, red_start,
-        red_self, red_src, gather, items, total;
+        red_self, red_src, gather, items, pattern, total;
 };
 
 struct Plan {
@@ -70,6 +70,11 @@ struct Plan {
     int ctas_per_sm;
     int group;                         // warps cooperating on one work item
     int split;                         // Helmholtz RHS from here on form a conjugated second output
+    // pattern mode (regular grids): lattice spacing, points per box edge, table strides
+    int pattern;
+    float grid_h;
+    int grid_t;
+    int pat_sy, pat_sz, pat_size, pat_bias;
     float rmax;                        // largest distance between points of neighbouring boxes
     Layout L;
     // state
@@ -161,6 +166,11 @@ struct HelmOut {
 };
 int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, HelmOut out,
                             cudaStream_t s);
+// pattern mode: table of 4 pi G(lattice displacement) and the table-lookup kernel
+constexpr int kPatternMaxEntries = 4608;
+int pattern_setup(Plan* p, float h, int t);
+int launch_helmholtz_pattern(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, float2* table,
+                             HelmOut out, cudaStream_t s);
 
 // records
 inline int helmholtz_rec_words(int nrhs) { return 1 + (nrhs + 1) / 2; }

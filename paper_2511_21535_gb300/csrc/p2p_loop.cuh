@@ -104,7 +104,7 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
     }
     __syncwarp();
 
-    if (a.hdr->flags & P2P_FLAG_CAPACITY) return;  // restructuring was skipped (uniform)
+    if (a.hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_LATTICE)) return;  // inputs rejected (uniform)
     const int32_t n_items = a.hdr->n_items;
     const bool redundant = a.red != nullptr;
     const float4* base = redundant ? a.red : a.rec;

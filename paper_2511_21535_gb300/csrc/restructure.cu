@@ -39,14 +39,53 @@ __device__ __forceinline__ float2 rhs_value(const float2* __restrict__ q, const 
     return make_float2(v.x, -v.y);
 }
 
+__global__ void k_clear_flag(Header* hdr, uint32_t bit) { atomicAnd(&hdr->flags, ~bit); }
+
+// Pattern mode: lattice code of a point, ix*1 + iy*sy + iz*sz with
+// ix = rint((x - lo)/h - 1/2); the point must be within 1 % of h of the
+// lattice and in the leaf box (ix div t) the tree put it in.
+struct LatticeArgs {
+    int on;
+    float lo[3];
+    float inv_h;
+    int t, sy, sz;
+    float scale;      // the tree's (float)2^level / edge
+    int cmax;         // 2^level - 1
+};
+
+__device__ __forceinline__ bool lattice_code(const float* x, const LatticeArgs& g, int* code) {
+    int c = 0;
+    const int stride[3] = {1, g.sy, g.sz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float f = (x[a] - g.lo[a]) * g.inv_h - 0.5f;
+        const float r = rintf(f);
+        if (!(fabsf(f - r) <= 0.01f)) return false;
+        const int ix = (int)r;
+        int cell = (int)floorf(__fmul_rn(__fsub_rn(x[a], g.lo[a]), g.scale));
+        cell = cell > g.cmax ? g.cmax : cell;
+        if (ix < 0 || ix / g.t != cell) return false;
+        c += ix * stride[a];
+    }
+    *code = c;
+    return true;
+}
+
 __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2* __restrict__ q,
                                     const float2* __restrict__ q2, int split, const int32_t* __restrict__ perm,
-                                    int64_t n, int nrhs, int words, float4* __restrict__ rec) {
+                                    int64_t n, int nrhs, int words, LatticeArgs lat, Header* hdr,
+                                    float4* __restrict__ rec) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm[s];
     float4* r = rec + s * words;
-    r[0] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], 0.0f);
+    float w = 0.0f;
+    if (lat.on) {
+        int code = 0;
+        if (!lattice_code(pos + 3 * i, lat, &code)) atomicOr(&hdr->flags, P2P_FLAG_LATTICE);
+        w = __int_as_float(code);
+    }
+    r[0] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], w);
     for (int w = 1; w < words; ++w) {
         const int r0 = 2 * (w - 1), r1 = r0 + 1;
         const float2 a = rhs_value(q, q2, split, n, r0, i);
@@ -272,9 +311,24 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
         k_records_gravity<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float*>(strength), perm, n, rec);
     } else {
         const int split = strength2 ? p->split : p->nrhs;
+        LatticeArgs lat{};
+        lat.on = p->pattern;
+        if (p->pattern) {
+            for (int a = 0; a < 3; ++a) lat.lo[a] = p->lo[a];
+            lat.inv_h = 1.0f / p->grid_h;
+            lat.t = p->grid_t;
+            lat.sy = p->pat_sy;
+            lat.sz = p->pat_sz;
+            lat.scale = p->scale;
+            lat.cmax = (1 << p->level) - 1;
+            // the lattice flag belongs to this restructuring
+            k_clear_flag<<<1, 1, 0, s>>>(at<Header>(ws, L.header), P2P_FLAG_LATTICE);
+            P2P_LAUNCH_CHECK();
+        }
         k_records_helmholtz<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float2*>(strength),
                                                               static_cast<const float2*>(strength2), split, perm, n,
-                                                              p->nrhs, p->rec_words, rec);
+                                                              p->nrhs, p->rec_words, lat, at<Header>(ws, L.header),
+                                                              rec);
     }
     P2P_LAUNCH_CHECK();
     int st = restructure_tail(p, ws, p->rec_words, s);

@@ -17,7 +17,7 @@ from . import build as _build
 GRAVITY, HELMHOLTZ = 0, 1
 LAYOUTS = {"indirect": 0, "redundant": 1, "auto": 2}
 PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING, PLAN_ADJOINT = 0x1, 0x2, 0x4, 0x8
-FLAG_DOMAIN, FLAG_TIMEOUT, FLAG_CAPACITY = 0x1, 0x2, 0x4
+FLAG_DOMAIN, FLAG_TIMEOUT, FLAG_CAPACITY, FLAG_LATTICE = 0x1, 0x2, 0x4, 0x8
 
 ARRAYS = {"perm": (0, torch.int32), "box_key": (1, torch.int32), "box_start": (2, torch.int32),
           "nbr_start": (3, torch.int32), "nbr_idx": (4, torch.int32), "red_start": (5, torch.int32),
@@ -32,7 +32,8 @@ EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_
            "p2p_measure_pipes", "p2p_helmholtz_adjoint", "p2p_gravity_adjoint",
            "p2p_batch_create", "p2p_batch_destroy", "p2p_batch_workspace_bytes", "p2p_batch_build",
            "p2p_batch_set_tuning", "p2p_batch_run", "p2p_batch_autotune", "p2p_batch_capture",
-           "p2p_batch_launch", "p2p_batch_counters", "p2p_selftest_bounded_wait")
+           "p2p_batch_launch", "p2p_batch_counters", "p2p_selftest_bounded_wait",
+           "p2p_plan_set_grid")
 
 
 class P2PError(RuntimeError):
@@ -93,6 +94,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_batch_launch": (I, [P, P]),
         "p2p_batch_counters": (I, [P, P, ctypes.POINTER(I64), P]),
         "p2p_selftest_bounded_wait": (I, [ctypes.c_uint64, P, P]),
+        "p2p_plan_set_grid": (I, [P, F, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -187,6 +189,10 @@ class Plan:
     def set_tuning(self, targets_per_lane: int, tile: int, ctas_per_sm: int = 0, warps_per_item: int = 4):
         _check(load().p2p_plan_set_tuning(self._h, targets_per_lane, tile, ctas_per_sm, warps_per_item),
                "p2p_plan_set_tuning")
+
+    def set_grid(self, h: float, points_per_box: int):
+        """Pattern mode for particles on a regular lattice (0 points disables)."""
+        _check(load().p2p_plan_set_grid(self._h, float(h), int(points_per_box)), "p2p_plan_set_grid")
 
     # -- pipeline -----------------------------------------------------------
     def _wsp(self):
