@@ -240,6 +240,7 @@ int p2p_plan_set_grid(p2p_plan* h, float grid_h, int points_per_box) {
     if (p->kind != P2P_HELMHOLTZ) return P2P_ERR_UNSUPPORTED;
     if (points_per_box == 0) {
         p->pattern = 0;
+        p->rec_words = helmholtz_rec_words(p->nrhs);
         p->src_ready = 0;
         return P2P_OK;
     }
@@ -249,6 +250,8 @@ int p2p_plan_set_grid(p2p_plan* h, float grid_h, int points_per_box) {
     if (std::fabs(box / ((double)grid_h * points_per_box) - 1.0) > 1e-5) return P2P_ERR_INVALID_ARG;
     int st = pattern_setup(p, grid_h, points_per_box);
     if (st) return st;
+    // one right-hand side: compact records [code, Re q, Im q, 0] (positions are not read)
+    p->rec_words = (p->nrhs == 1) ? 1 : helmholtz_rec_words(p->nrhs);
     p->src_ready = 0;
     return P2P_OK;
 }
@@ -356,6 +359,15 @@ int p2p_helmholtz_adjoint(p2p_plan* h, float k, const float* pos, const void* q,
         // grad_q = conj(P) gbar = P(-k) gbar: the forward operator on gbar
         st = restructure(p, pos, gbar, ws, s);
         if (st) return st;
+        if (p->pattern) {
+            st = build_items(p, ws, 32 * (p->tpl >= 2 ? 2 : 1), s);
+            if (st) return st;
+            st = launch_helmholtz_pattern(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), -k,
+                                          at<float2>(ws, p->L.pattern),
+                                          HelmOut{static_cast<float2*>(grad_q), nullptr, p->nrhs}, s);
+            p->src_ready = 0;
+            return st;
+        }
         st = build_items(p, ws, 32 * helmholtz_targets_per_lane(p, -k), s);
         if (st) return st;
         st = launch_helmholtz_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), -k,

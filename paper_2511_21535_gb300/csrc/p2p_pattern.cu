@@ -56,7 +56,8 @@ __global__ void k_pattern_table(double h, double k, int t, int sy, int sz, int s
     table[idx] = v;
 }
 
-template <int K, int R>
+// COMPACT: one right-hand side, records [code, Re q, Im q, 0]
+template <int K, int R, bool COMPACT = false>
 struct HelmPatternOp : HelmOp<K, R, true, false, 0> {
     using Base = HelmOp<K, R, true, false, 0>;
     const float2* tab;   // shared-memory table, already offset by the bias
@@ -68,25 +69,31 @@ struct HelmPatternOp : HelmOp<K, R, true, false, 0> {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int l = lane + 32 * k;
-            tcode[k] = __float_as_int(this->rec[(int64_t)(tb + (l < ntg ? l : 0)) * this->words].w);
+            const float4 r = this->rec[(int64_t)(tb + (l < ntg ? l : 0)) * this->words];
+            tcode[k] = __float_as_int(COMPACT ? r.x : r.w);
         }
     }
 
     __device__ __forceinline__ void tile(const float4* sm, int cnt, int, bool) {
         const float4* rj = sm;
 #pragma unroll 4
-        for (int j = 0; j < cnt; ++j, rj += this->words) {
+        for (int j = 0; j < cnt; ++j, rj += (COMPACT ? 1 : this->words)) {
             const float4 ps = rj[0];
-            const int cj = __float_as_int(ps.w);
+            const int cj = __float_as_int(COMPACT ? ps.x : ps.w);
             float qr[R], qi[R];
+            if (COMPACT) {
+                qr[0] = ps.y;
+                qi[0] = ps.z;
+            } else {
 #pragma unroll
-            for (int w = 0; w < (R + 1) / 2; ++w) {
-                const float4 v = rj[this->qw0 + w];
-                qr[2 * w] = v.x;
-                qi[2 * w] = v.y;
-                if (2 * w + 1 < R) {
-                    qr[2 * w + 1] = v.z;
-                    qi[2 * w + 1] = v.w;
+                for (int w = 0; w < (R + 1) / 2; ++w) {
+                    const float4 v = rj[this->qw0 + w];
+                    qr[2 * w] = v.x;
+                    qi[2 * w] = v.y;
+                    if (2 * w + 1 < R) {
+                        qr[2 * w + 1] = v.z;
+                        qi[2 * w + 1] = v.w;
+                    }
                 }
             }
 #pragma unroll
@@ -111,7 +118,7 @@ struct HelmPatternOp : HelmOp<K, R, true, false, 0> {
     }
 };
 
-template <int K, int G, int R>
+template <int K, int G, int R, bool COMPACT>
 __global__ void __launch_bounds__(kLoopThreads, 4)
     k_helmholtz_pattern(LoopArgs a, const int32_t* __restrict__ perm, const float2* __restrict__ table, int size,
                         int bias, size_t table_off, int qw0, int64_t n, int r0, HelmOut out) {
@@ -119,7 +126,7 @@ __global__ void __launch_bounds__(kLoopThreads, 4)
     float2* tab = reinterpret_cast<float2*>(smem_raw + table_off);
     for (int i = threadIdx.x; i < size; i += blockDim.x) tab[i] = table[i];
     __syncthreads();
-    HelmPatternOp<K, R> op;
+    HelmPatternOp<K, R, COMPACT> op;
     op.rec = a.rec;
     op.perm = perm;
     op.kk = 0.f;
@@ -132,11 +139,11 @@ __global__ void __launch_bounds__(kLoopThreads, 4)
     warp_item_loop<K, G>(a, op);
 }
 
-template <int K, int G, int R>
+template <int K, int G, int R, bool COMPACT = false>
 static int launch_pat(const Plan* p, const LoopArgs& a, const int32_t* perm, const float2* table, int r0, HelmOut out,
                       cudaStream_t s) {
-    auto kern = k_helmholtz_pattern<K, G, R>;
-    const size_t loop = loop_smem_bytes(a.tile, a.words, HelmPatternOp<K, R>::kOuts, G);
+    auto kern = k_helmholtz_pattern<K, G, R, COMPACT>;
+    const size_t loop = loop_smem_bytes(a.tile, a.words, HelmPatternOp<K, R, COMPACT>::kOuts, G);
     const size_t table_off = (loop + 15) / 16 * 16;
     const size_t smem = table_off + (size_t)p->pat_size * sizeof(float2);
     P2P_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -155,7 +162,8 @@ template <int K, int G>
 static int pat_r(const Plan* p, const LoopArgs& a, const int32_t* perm, const float2* table, int r0, int R,
                  HelmOut out, cudaStream_t s) {
     switch (R) {
-        case 1: return launch_pat<K, G, 1>(p, a, perm, table, r0, out, s);
+        case 1: return a.words == 1 ? launch_pat<K, G, 1, true>(p, a, perm, table, r0, out, s)
+                                    : launch_pat<K, G, 1>(p, a, perm, table, r0, out, s);
         case 2: return launch_pat<K, G, 2>(p, a, perm, table, r0, out, s);
         case 4: return launch_pat<K, G, 4>(p, a, perm, table, r0, out, s);
         case 8: return launch_pat<K, G, 8>(p, a, perm, table, r0, out, s);

@@ -84,6 +84,11 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
         int code = 0;
         if (!lattice_code(pos + 3 * i, lat, &code)) atomicOr(&hdr->flags, P2P_FLAG_LATTICE);
         w = __int_as_float(code);
+        if (words == 1) {   // compact pattern record [code, Re q, Im q, 0] (one right-hand side)
+            const float2 a = rhs_value(q, q2, split, n, 0, i);
+            r[0] = make_float4(w, a.x, a.y, 0.0f);
+            return;
+        }
     }
     r[0] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], w);
     for (int w = 1; w < words; ++w) {

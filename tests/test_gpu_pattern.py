@@ -73,3 +73,22 @@ def test_pattern_argument_checks(dev):
         plan.set_grid(0.1, 3)           # 3 points of 0.1 do not make the 0.4 leaf box
     plan.set_grid(0.1, 4)
     plan.set_grid(0.0, 0)               # off again
+
+
+def test_pattern_adjoint_q(dev):
+    prob = wl.grid_helmholtz(edge_points=24, nrhs=1, seed=9)
+    rng = np.random.default_rng(10)
+    gbar = wl.complex_normal((1, prob.n), rng)
+    plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, nrhs=1, device=dev)
+    plan.set_grid(wl.SPACING, wl.LEAF_EDGE_POINTS)
+    pos = torch.from_numpy(prob.pos).to(dev)
+    plan.tree_build(pos)
+    gq, _ = plan.helmholtz_adjoint(prob.k, pos, torch.from_numpy(gbar).to(dev), want_q=True, want_pos=False)
+    torch.cuda.synchronize()
+    oq, _ = oracle.helmholtz_adjoint(prob.pos, prob.strength, gbar, prob.level, prob.lo, prob.edge, prob.k)
+    assert rel_l2(gq.cpu().numpy(), oq) <= TOL_COMPLEX
+    # the forward afterwards (records rebuilt) is still right
+    plan.restructure(pos, torch.from_numpy(prob.strength).to(dev))
+    u = plan.helmholtz(prob.k).cpu().numpy()
+    ou, _ = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k)
+    assert rel_l2(u, ou) <= TOL_COMPLEX
