@@ -51,9 +51,13 @@ def load():
         lib.orc_helmholtz.argtypes = [P, P, I, I64, I, P, F, F, P, I64, P, P]
         lib.orc_pair_count.argtypes = [P, I64, I, P, F, P]
         lib.orc_helmholtz_adjoint.argtypes = [P, P, P, I, I64, I, P, F, F, P, P]
+        lib.orc_tree_periodic.argtypes = [P, I64, I, P, F, P, P, P, P, P, P, P, P]
+        lib.orc_gravity_periodic.argtypes = [P, P, I64, I, P, F, F, P, I64, P, P, P]
+        lib.orc_helmholtz_periodic.argtypes = [P, P, I, I64, I, P, F, F, P, I64, P, P]
         lib.orc_gravity_adjoint.argtypes = [P, P, P, P, I64, I, P, F, F, P, P]
         for f in ("orc_cells", "orc_tree", "orc_redundant", "orc_gravity", "orc_helmholtz",
-                  "orc_pair_count", "orc_helmholtz_adjoint", "orc_gravity_adjoint"):
+                  "orc_pair_count", "orc_helmholtz_adjoint", "orc_gravity_adjoint", "orc_tree_periodic",
+                  "orc_gravity_periodic", "orc_helmholtz_periodic"):
             getattr(lib, f).restype = I
         _lib = lib
     return _lib
@@ -96,8 +100,9 @@ def cells(pos, level, lo, edge):
     return cell, key
 
 
-def tree(pos, level, lo, edge):
-    """dict with perm, box_key, box_start, nbr_start, nbr_idx (exact sizes)."""
+def tree(pos, level, lo, edge, periodic: bool = False):
+    """dict with perm, box_key, box_start, nbr_start, nbr_idx (exact sizes); periodic
+    trees also carry nbr_img (image code (ox+1) + 3(oy+1) + 9(oz+1) per entry)."""
     pos = np.ascontiguousarray(pos, np.float32)
     n = pos.shape[0]
     perm = np.zeros(n, np.int32)
@@ -105,16 +110,25 @@ def tree(pos, level, lo, edge):
     box_start = np.zeros(n + 1, np.int32)
     nbr_start = np.zeros(n + 1, np.int32)
     nbr_idx = np.zeros(27 * n, np.int32)
+    nbr_img = np.zeros(27 * n, np.int32)
     nb = ctypes.c_int32()
     ne = ctypes.c_int64()
     lo = _lo(lo)
-    _check(load().orc_tree(_p(pos), n, level, _p(lo), float(edge), _p(perm), _p(box_key),
-                           _p(box_start), ctypes.byref(nb), _p(nbr_start), _p(nbr_idx),
-                           ctypes.byref(ne)), "tree")
+    if periodic:
+        _check(load().orc_tree_periodic(_p(pos), n, level, _p(lo), float(edge), _p(perm), _p(box_key),
+                                        _p(box_start), ctypes.byref(nb), _p(nbr_start), _p(nbr_idx), _p(nbr_img),
+                                        ctypes.byref(ne)), "tree_periodic")
+    else:
+        _check(load().orc_tree(_p(pos), n, level, _p(lo), float(edge), _p(perm), _p(box_key),
+                               _p(box_start), ctypes.byref(nb), _p(nbr_start), _p(nbr_idx),
+                               ctypes.byref(ne)), "tree")
     B, E = nb.value, ne.value
-    return {"perm": perm, "box_key": box_key[:B].copy(), "box_start": box_start[:B + 1].copy(),
-            "nbr_start": nbr_start[:B + 1].copy(), "nbr_idx": nbr_idx[:E].copy(),
-            "n_boxes": B, "n_nbr": E}
+    out = {"perm": perm, "box_key": box_key[:B].copy(), "box_start": box_start[:B + 1].copy(),
+           "nbr_start": nbr_start[:B + 1].copy(), "nbr_idx": nbr_idx[:E].copy(),
+           "n_boxes": B, "n_nbr": E}
+    if periodic:
+        out["nbr_img"] = nbr_img[:E].copy()
+    return out
 
 
 def redundant(t, gather: bool = True):
@@ -138,7 +152,7 @@ def redundant(t, gather: bool = True):
     return out
 
 
-def gravity(pos, mass, level, lo, edge, eps, targets=None):
+def gravity(pos, mass, level, lo, edge, eps, targets=None, periodic: bool = False):
     """(phi[nt], acc[nt,3], pairs) in float64 at `targets` (original indices; None = all)."""
     pos = np.ascontiguousarray(pos, np.float32)
     mass = np.ascontiguousarray(mass, np.float32)
@@ -149,12 +163,13 @@ def gravity(pos, mass, level, lo, edge, eps, targets=None):
     acc = np.zeros((nt, 3), np.float64)
     pairs = ctypes.c_int64()
     lo = _lo(lo)
-    _check(load().orc_gravity(_p(pos), _p(mass), n, level, _p(lo), float(edge), float(eps),
-                              _p(tg), nt, _p(phi), _p(acc), ctypes.byref(pairs)), "gravity")
+    fn = load().orc_gravity_periodic if periodic else load().orc_gravity
+    _check(fn(_p(pos), _p(mass), n, level, _p(lo), float(edge), float(eps),
+              _p(tg), nt, _p(phi), _p(acc), ctypes.byref(pairs)), "gravity")
     return phi, acc, pairs.value
 
 
-def helmholtz(pos, q, level, lo, edge, k, targets=None):
+def helmholtz(pos, q, level, lo, edge, k, targets=None, periodic: bool = False):
     """(u[nrhs, nt] complex128, pairs) at `targets` (original indices; None = all).
 
     q: complex64 [nrhs, n] (or [n] for one right-hand side)."""
@@ -169,8 +184,9 @@ def helmholtz(pos, q, level, lo, edge, k, targets=None):
     u = np.zeros((nrhs, nt, 2), np.float64)
     pairs = ctypes.c_int64()
     lo = _lo(lo)
-    _check(load().orc_helmholtz(_p(pos), _p(q.view(np.float32)), nrhs, n, level, _p(lo),
-                                float(edge), float(k), _p(tg), nt, _p(u), ctypes.byref(pairs)),
+    fn = load().orc_helmholtz_periodic if periodic else load().orc_helmholtz
+    _check(fn(_p(pos), _p(q.view(np.float32)), nrhs, n, level, _p(lo),
+              float(edge), float(k), _p(tg), nt, _p(u), ctypes.byref(pairs)),
            "helmholtz")
     return u[..., 0] + 1j * u[..., 1], pairs.value
 

@@ -151,9 +151,10 @@ static int32_t orc_find_box(const uint32_t* box_key, int32_t nb, uint32_t key) {
  *   nbr_idx[27 n]      neighbour box indices, ascending
  *   *n_nbr             total neighbour entries E
  */
-int orc_tree(const float* pos, int64_t n, int level, const float* lo, float edge,
-             int32_t* perm, uint32_t* box_key, int32_t* box_start, int32_t* n_boxes,
-             int32_t* nbr_start, int32_t* nbr_idx, int64_t* n_nbr) {
+int orc_tree_ex(const float* pos, int64_t n, int level, const float* lo, float edge, int periodic,
+                int32_t* perm, uint32_t* box_key, int32_t* box_start, int32_t* n_boxes,
+                int32_t* nbr_start, int32_t* nbr_idx, int32_t* nbr_img, int64_t* n_nbr) {
+    if (periodic && level < 2) return ORC_ERR_ARG;
     if (n <= 0) return ORC_ERR_ARG;
     uint32_t* key = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
     orc_kv* kv = (orc_kv*)malloc((size_t)n * sizeof(orc_kv));
@@ -180,25 +181,45 @@ int orc_tree(const float* pos, int64_t n, int level, const float* lo, float edge
     for (int32_t b = 0; b < nb; ++b) {
         int32_t cx, cy, cz;
         orc_unmorton(box_key[b], level, &cx, &cy, &cz);
+        /* found[j] = box index * 32 + image code, so sorting by it orders by box */
         int32_t found[27];
         int nf = 0;
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
                     int32_t x = cx + dx, y = cy + dy, z = cz + dz;
-                    if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) continue;
+                    int32_t o[3] = {0, 0, 0};
+                    if (periodic) {
+                        /* toroidal wrap: the source image sits one domain edge away */
+                        if (x < 0) { x += side; o[0] = -1; } else if (x >= side) { x -= side; o[0] = 1; }
+                        if (y < 0) { y += side; o[1] = -1; } else if (y >= side) { y -= side; o[1] = 1; }
+                        if (z < 0) { z += side; o[2] = -1; } else if (z >= side) { z -= side; o[2] = 1; }
+                    } else if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) {
+                        continue;
+                    }
                     int32_t c = orc_find_box(box_key, nb, orc_morton(x, y, z, level));
-                    if (c >= 0) found[nf++] = c;
+                    int32_t code = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+                    if (c >= 0) found[nf++] = c * 32 + code;
                 }
         qsort(found, (size_t)nf, sizeof(int32_t), orc_i32_cmp);
         nbr_start[b] = (int32_t)e;
-        for (int j = 0; j < nf; ++j) nbr_idx[e++] = found[j];
+        for (int j = 0; j < nf; ++j) {
+            if (nbr_img) nbr_img[e] = found[j] % 32;
+            nbr_idx[e++] = found[j] / 32;
+        }
     }
     nbr_start[nb] = (int32_t)e;
     *n_nbr = e;
     free(key);
     free(kv);
     return ORC_OK;
+}
+
+int orc_tree(const float* pos, int64_t n, int level, const float* lo, float edge,
+             int32_t* perm, uint32_t* box_key, int32_t* box_start, int32_t* n_boxes,
+             int32_t* nbr_start, int32_t* nbr_idx, int64_t* n_nbr) {
+    return orc_tree_ex(pos, n, level, lo, edge, 0, perm, box_key, box_start, n_boxes, nbr_start, nbr_idx,
+                       NULL, n_nbr);
 }
 
 /*
@@ -245,17 +266,35 @@ typedef struct {
     int32_t* box_start;
     int32_t* nbr_start;
     int32_t* nbr_idx;
+    int32_t* nbr_img;  /* periodic: image code of each neighbour entry, else NULL */
     int32_t* box_of;   /* original index -> box */
+    double edge;
 } orc_ctx;
+
+/* shift of a neighbour entry's sources: image offset times the domain edge */
+static void orc_img_shift(const orc_ctx* c, int32_t e, double* sh) {
+    if (!c->nbr_img) { sh[0] = sh[1] = sh[2] = 0.0; return; }
+    int32_t code = c->nbr_img[e];
+    sh[0] = (double)(code % 3 - 1) * c->edge;
+    sh[1] = (double)((code / 3) % 3 - 1) * c->edge;
+    sh[2] = (double)(code / 9 - 1) * c->edge;
+}
 
 static void orc_ctx_free(orc_ctx* c) {
     free(c->perm); free(c->box_key); free(c->box_start);
-    free(c->nbr_start); free(c->nbr_idx); free(c->box_of);
+    free(c->nbr_start); free(c->nbr_idx); free(c->nbr_img); free(c->box_of);
 }
+
+static int orc_periodic = 0;   /* set by the *_periodic entry points around a call */
 
 static int orc_ctx_build(orc_ctx* c, const float* pos, int64_t n, int level, const float* lo, float edge) {
     memset(c, 0, sizeof(*c));
     c->n = n;
+    c->edge = (double)edge;
+    if (orc_periodic) {
+        c->nbr_img = (int32_t*)malloc((size_t)n * 27 * sizeof(int32_t));
+        if (!c->nbr_img) return ORC_ERR_NOMEM;
+    }
     c->perm = (int32_t*)malloc((size_t)n * sizeof(int32_t));
     c->box_key = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
     c->box_start = (int32_t*)malloc((size_t)(n + 1) * sizeof(int32_t));
@@ -267,8 +306,8 @@ static int orc_ctx_build(orc_ctx* c, const float* pos, int64_t n, int level, con
         return ORC_ERR_NOMEM;
     }
     int64_t e;
-    int st = orc_tree(pos, n, level, lo, edge, c->perm, c->box_key, c->box_start, &c->nb,
-                      c->nbr_start, c->nbr_idx, &e);
+    int st = orc_tree_ex(pos, n, level, lo, edge, orc_periodic, c->perm, c->box_key, c->box_start, &c->nb,
+                         c->nbr_start, c->nbr_idx, c->nbr_img, &e);
     if (st != ORC_OK) { orc_ctx_free(c); return st; }
     for (int32_t b = 0; b < c->nb; ++b)
         for (int32_t s = c->box_start[b]; s < c->box_start[b + 1]; ++s) c->box_of[c->perm[s]] = b;
@@ -297,12 +336,14 @@ int orc_gravity(const float* pos, const float* mass, int64_t n, int level, const
         double p = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
         for (int32_t e = c.nbr_start[b]; e < c.nbr_start[b + 1]; ++e) {
             int32_t nbox = c.nbr_idx[e];
+            double sh[3];
+            orc_img_shift(&c, e, sh);
             for (int32_t s = c.box_start[nbox]; s < c.box_start[nbox + 1]; ++s) {
                 int64_t j = c.perm[s];
                 if (j == i) continue;
-                double dx = (double)pos[3 * j] - xi;
-                double dy = (double)pos[3 * j + 1] - yi;
-                double dz = (double)pos[3 * j + 2] - zi;
+                double dx = (double)pos[3 * j] + sh[0] - xi;
+                double dy = (double)pos[3 * j + 1] + sh[1] - yi;
+                double dz = (double)pos[3 * j + 2] + sh[2] - zi;
                 double r2 = dx * dx + dy * dy + dz * dz + e2;
                 double inv = 1.0 / sqrt(r2);
                 double m = (double)mass[j];
@@ -344,12 +385,14 @@ int orc_helmholtz(const float* pos, const float* q, int nrhs, int64_t n, int lev
         for (int r = 0; r < nrhs; ++r) { u[2 * (r * nt + t)] = 0.0; u[2 * (r * nt + t) + 1] = 0.0; }
         for (int32_t e = c.nbr_start[b]; e < c.nbr_start[b + 1]; ++e) {
             int32_t nbox = c.nbr_idx[e];
+            double sh[3];
+            orc_img_shift(&c, e, sh);
             for (int32_t s = c.box_start[nbox]; s < c.box_start[nbox + 1]; ++s) {
                 int64_t j = c.perm[s];
                 if (j == i) continue;
-                double dx = (double)pos[3 * j] - xi;
-                double dy = (double)pos[3 * j + 1] - yi;
-                double dz = (double)pos[3 * j + 2] - zi;
+                double dx = (double)pos[3 * j] + sh[0] - xi;
+                double dy = (double)pos[3 * j + 1] + sh[1] - yi;
+                double dz = (double)pos[3 * j + 2] + sh[2] - zi;
                 double r = sqrt(dx * dx + dy * dy + dz * dz);
                 double gre = cos(kk * r) * inv4pi / r;
                 double gim = sin(kk * r) * inv4pi / r;
@@ -497,4 +540,39 @@ int orc_gravity_adjoint(const float* pos, const float* mass, const float* gphi, 
     }
     orc_ctx_free(&c);
     return ORC_OK;
+}
+
+
+/*
+ * Periodic (toroidal) boundaries, the "periodic" interactions of the PhotoNs
+ * case (Section 5.2): neighbour cells wrap around the domain and a wrapped
+ * neighbour's sources interact through their image one domain edge away.
+ * Needs level >= 2 so that a box meets each neighbour through one image.
+ * Same outputs as the non-periodic calls.
+ */
+int orc_tree_periodic(const float* pos, int64_t n, int level, const float* lo, float edge,
+                      int32_t* perm, uint32_t* box_key, int32_t* box_start, int32_t* n_boxes,
+                      int32_t* nbr_start, int32_t* nbr_idx, int32_t* nbr_img, int64_t* n_nbr) {
+    return orc_tree_ex(pos, n, level, lo, edge, 1, perm, box_key, box_start, n_boxes, nbr_start, nbr_idx,
+                       nbr_img, n_nbr);
+}
+
+int orc_gravity_periodic(const float* pos, const float* mass, int64_t n, int level, const float* lo,
+                         float edge, float eps, const int64_t* targets, int64_t nt,
+                         double* phi, double* acc, int64_t* pairs) {
+    if (level < 2) return ORC_ERR_ARG;
+    orc_periodic = 1;
+    int st = orc_gravity(pos, mass, n, level, lo, edge, eps, targets, nt, phi, acc, pairs);
+    orc_periodic = 0;
+    return st;
+}
+
+int orc_helmholtz_periodic(const float* pos, const float* q, int nrhs, int64_t n, int level,
+                           const float* lo, float edge, float k, const int64_t* targets, int64_t nt,
+                           double* u, int64_t* pairs) {
+    if (level < 2) return ORC_ERR_ARG;
+    orc_periodic = 1;
+    int st = orc_helmholtz(pos, q, nrhs, n, level, lo, edge, k, targets, nt, u, pairs);
+    orc_periodic = 0;
+    return st;
 }

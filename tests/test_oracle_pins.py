@@ -386,3 +386,89 @@ def test_gravity_adjoint_finite_differences():
         mm_[i] -= np.float32(0.25)
         fd = (loss(pos, mp) - loss(pos, mm_)) / 0.5
         assert abs(fd - gm[i]) <= 1e-9 * max(1.0, abs(gm[i]))
+
+
+# ---------------------------------------------------------------------------
+# periodic (toroidal) neighbours
+# ---------------------------------------------------------------------------
+
+def brute_periodic(pos, level, edge=1.0):
+    """(mask[i, j], image shift of x_j [i, j, 3]) from wrapped cell offsets."""
+    side = 1 << level
+    cells = brute_cells_unit(pos, level)
+    d = cells[None, :, :] - cells[:, None, :]                 # cell_j - cell_i
+    dw = np.mod(d + 1, side) - 1                              # wrapped offset
+    mask = np.all(np.abs(dw) <= 1, axis=2)
+    shift = (dw - d) * (edge / side)
+    return mask, shift
+
+
+def test_periodic_tree_bruteforce():
+    level, n = 3, 1500
+    pos = np.random.default_rng(41).random((n, 3), dtype=np.float32)
+    t = oracle.tree(pos, level, (0, 0, 0), 1.0, periodic=True)
+    bc = np.array([oracle.unmorton(int(k), level) for k in t["box_key"]])
+    side = 1 << level
+    for b in range(t["n_boxes"]):
+        lst = t["nbr_idx"][t["nbr_start"][b]:t["nbr_start"][b + 1]]
+        img = t["nbr_img"][t["nbr_start"][b]:t["nbr_start"][b + 1]]
+        d = bc - bc[b]
+        dw = np.mod(d + 1, side) - 1
+        near = np.nonzero(np.all(np.abs(dw) <= 1, axis=1))[0]
+        assert lst.tolist() == near.tolist()
+        o = (dw - d)[lst] // side                                # image multiplier per axis
+        np.testing.assert_array_equal(img, (o[:, 0] + 1) + 3 * (o[:, 1] + 1) + 9 * (o[:, 2] + 1))
+
+
+@pytest.mark.parametrize("level", [2, 3])
+def test_periodic_sums_vs_bruteforce(level):
+    n = 1200
+    rng = np.random.default_rng(43 + level)
+    pos = rng.random((n, 3), dtype=np.float32)
+    mass = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    q = wl.complex_normal((2, n), rng)
+    eps = np.float32(1e-3)
+    mask, shift = brute_periodic(pos, level)
+    np.fill_diagonal(mask, False)
+    x = pos.astype(np.float64)
+    d = x[None, :, :] + shift - x[:, None, :]
+    r2 = (d ** 2).sum(axis=2)
+    h = np.where(mask, r2 + float(eps) ** 2, 1.0)
+    m = np.where(mask, mass.astype(np.float64)[None, :], 0.0)
+    bphi = -(m / np.sqrt(h)).sum(axis=1)
+    bacc = ((m / h ** 1.5)[:, :, None] * d).sum(axis=1)
+    phi, acc, pairs = oracle.gravity(pos, mass, level, (0, 0, 0), 1.0, eps, periodic=True)
+    assert rel_l2(phi, bphi) < 1e-13 and rel_l2(acc, bacc) < 1e-13
+    assert pairs == int(mask.sum())
+    k = np.float32(2 * math.pi * 2)
+    r = np.sqrt(np.where(mask, r2, 1.0))
+    g = np.where(mask, np.exp(1j * float(k) * r) / (4 * math.pi * r), 0.0)
+    bu = (g @ q.astype(np.complex128).T).T
+    u, _ = oracle.helmholtz(pos, q, level, (0, 0, 0), 1.0, k, periodic=True)
+    assert rel_l2(u, bu) < 1e-13
+
+
+def test_periodic_pair_across_the_boundary():
+    # x = 1/64 and 63/64 at level 2: neighbours only through the wrap, distance 1/32
+    pos = np.array([[1 / 64, 0.5, 0.5], [63 / 64, 0.5, 0.5]], np.float32)
+    eps = np.float32(0.0)
+    phi, acc, pairs = oracle.gravity(pos, np.ones(2, np.float32), 2, (0, 0, 0), 1.0, eps, periodic=True)
+    assert pairs == 2
+    np.testing.assert_allclose(phi, [-32.0, -32.0], rtol=1e-15)
+    np.testing.assert_allclose(acc[:, 0], [-1024.0, 1024.0], rtol=1e-15)   # attraction through the wrap
+    phi0, _, pairs0 = oracle.gravity(pos, np.ones(2, np.float32), 2, (0, 0, 0), 1.0, eps)
+    assert pairs0 == 0 and np.all(phi0 == 0)
+
+
+def test_periodic_translation_by_a_box():
+    level = 3
+    rng = np.random.default_rng(47)
+    pos = (np.round(rng.random((2000, 3)) * 2 ** 20) / 2 ** 20).astype(np.float32) % np.float32(1.0)
+    mass = rng.uniform(0.5, 1.5, 2000).astype(np.float32)
+    eps = np.float32(1e-3)
+    phi, acc, _ = oracle.gravity(pos, mass, level, (0, 0, 0), 1.0, eps, periodic=True)
+    moved = ((pos.astype(np.float64) + np.array([1 / 8, 3 / 8, 5 / 8])) % 1.0).astype(np.float32)
+    phi2, acc2, _ = oracle.gravity(moved, mass, level, (0, 0, 0), 1.0, eps, periodic=True)
+    assert rel_l2(phi2, phi) < 1e-14 and rel_l2(acc2, acc) < 1e-14
+    f = mass.astype(np.float64)[:, None] * acc
+    assert np.abs(f.sum(axis=0)).max() < 1e-12 * np.abs(f).sum()
