@@ -60,7 +60,13 @@ MUFU_PER_SM_CLK = 16           # nominal XU (MUFU) throughput per SM per clock
 FP32_PER_SM_CLK = 128
 
 
-def make_problem(name: str):
+def make_problem(name: str, periodic: bool = False):
+    prob = _make_problem(name)
+    prob.extra["periodic"] = bool(periodic)
+    return prob
+
+
+def _make_problem(name: str):
     if name == "grid_helmholtz":
         return wl.grid_helmholtz()
     if name == "uniform_gravity":
@@ -75,8 +81,10 @@ def make_problem(name: str):
 
 
 def workload_config(prob, layout, pattern=False):
-    cfg = {"kernel_mode": "pattern table" if pattern else "direct","workload": prob.name, "n": prob.n, "level": prob.level, "kernel": prob.kind, "layout": layout,
-           "nrhs": prob.nrhs, "l2": "flushed between steps (512 MiB write)", "inputs": "seeded synthetic"}
+    cfg = {"workload": prob.name, "n": prob.n, "level": prob.level, "kernel": prob.kind, "layout": layout,
+           "kernel_mode": "pattern table" if pattern else "direct",
+           "boundary": "periodic" if prob.extra.get("periodic") else "open", "nrhs": prob.nrhs,
+           "l2": "flushed between steps (512 MiB write)", "inputs": "seeded synthetic"}
     if prob.kind == "gravity":
         cfg["eps"] = prob.eps
     else:
@@ -160,10 +168,10 @@ def run_gpu(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    prob = make_problem(args.workload)
+    prob = make_problem(args.workload, args.periodic)
     layout = args.layout
     plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
-                    timing=True, device=dev)
+                    timing=True, periodic=args.periodic, device=dev)
     if args.tpl:
         plan.set_tuning(args.tpl, args.tile, args.ctas, args.group)
     if args.pattern:
@@ -352,7 +360,7 @@ def run_gpu(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
         "roofline": {"bound": "alu", "pipe": pipe, "kernel": f"k_{prob.kind}", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak,
-                     "traffic": kernel_traffic(prob.kind, prob.name, layout, prob.n),
+                     "traffic": None if args.periodic else kernel_traffic(prob.kind, prob.name, layout, prob.n),
                      "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms,
                      "peak_source": "pipe rates measured by p2p_measure_pipes x SMs x sampled SM clock",
                      "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in pipes.items()}},
@@ -470,10 +478,13 @@ def oracle_sample(prob, target_seconds: float, seed: int = 0):
 
 
 def _oracle_eval(oracle, prob, tg):
+    per = bool(prob.extra.get("periodic"))
     if prob.kind == "gravity":
-        _, _, pairs = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps, targets=tg)
+        _, _, pairs = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps, targets=tg,
+                                     periodic=per)
         return None, pairs
-    u, pairs = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k, targets=tg)
+    u, pairs = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k, targets=tg,
+                                periodic=per)
     return u, pairs * prob.nrhs
 
 
@@ -499,7 +510,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     import oracle
-    prob = make_problem(args.workload)
+    prob = make_problem(args.workload, args.periodic)
     oracle.build()
     rng = np.random.default_rng(1)
     # size one step to ~2 s of oracle work
@@ -545,6 +556,7 @@ def main():
                     help="launch the step's kernels on the stream instead of replaying one captured CUDA graph")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--pattern", action="store_true", help="tabulated-G kernel for grid workloads")
+    ap.add_argument("--periodic", action="store_true", help="toroidal neighbourhoods (wrapped boxes)")
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -84,6 +84,9 @@ typedef enum { P2P_LAYOUT_INDIRECT = 0, P2P_LAYOUT_REDUNDANT = 1, P2P_LAYOUT_AUT
 #define P2P_PLAN_PLAIN_FP32  0x2u  /* plain FP32 accumulation (default: compensated) */
 #define P2P_PLAN_TIMING      0x4u  /* record CUDA events around each phase           */
 #define P2P_PLAN_ADJOINT     0x8u  /* size the workspace for the adjoint records     */
+#define P2P_PLAN_PERIODIC    0x10u /* toroidal boundaries: neighbour cells wrap and  */
+                                   /* a wrapped neighbour's sources interact through */
+                                   /* their image one domain edge away (level >= 2)  */
 
 /* device flag bits (p2p_read_counters: counters[P2P_CTR_FLAGS]) */
 #define P2P_FLAG_DOMAIN   0x1u     /* a position was outside the domain             */
@@ -326,7 +329,9 @@ typedef enum {
     P2P_ARR_RED_SELF = 6,    /* int32 [n_boxes]         own particles' stream offset */
     P2P_ARR_GATHER_IDX = 7,  /* uint32 [red_start[n_boxes]] sorted source per record */
     P2P_ARR_SORTED_KEY = 8,  /* uint32 [n]              Morton key, sorted order     */
-    P2P_ARR_COUNT = 9
+    P2P_ARR_NBR_IMG = 9,     /* int32 [n_nbr] periodic: image code (ox+1)+3(oy+1)+9(oz+1) */
+                             /* of each neighbour entry, o = image offset in domain edges */
+    P2P_ARR_COUNT = 10
 } p2p_array_id;
 
 /*

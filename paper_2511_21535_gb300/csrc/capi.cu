@@ -44,6 +44,7 @@ void compute_layout(Plan* p) {
     L.nbr_cnt = take(bc * 4);
     L.nbr_start = take((bc + 1) * 4);
     L.nbr_idx = take((size_t)27 * bc * 4);
+    L.nbr_img = p->periodic ? take((size_t)27 * bc * 4) : 0;
     L.src = take((size_t)n * p->rec_alloc_words * 16);
     L.box_S = take((bc + 1) * 4);
     L.items = take((size_t)p->items_cap * 8);
@@ -98,6 +99,10 @@ LoopArgs loop_args(const Plan* p, void* ws, int words) {
     a.red_self = (p->layout == P2P_LAYOUT_REDUNDANT) ? at<int32_t>(ws, L.red_self) : nullptr;
     a.items = at<int2>(ws, L.items);
     a.hdr = at<Header>(ws, L.header);
+    // periodic images: the redundant streams carry shifted sources; the indirect
+    // layout shifts the targets per neighbour range
+    a.nbr_img = (p->periodic && p->layout == P2P_LAYOUT_INDIRECT) ? at<int32_t>(ws, L.nbr_img) : nullptr;
+    a.edge = p->edge;
     return a;
 }
 
@@ -113,9 +118,12 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT) return P2P_ERR_INVALID_ARG;
     if (kind == P2P_GRAVITY && nrhs != 1) return P2P_ERR_INVALID_ARG;
     if (nrhs < 1 || nrhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
-    if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING | P2P_PLAN_ADJOINT))
+    if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING | P2P_PLAN_ADJOINT |
+                  P2P_PLAN_PERIODIC))
         return P2P_ERR_INVALID_ARG;
+    if ((flags & P2P_PLAN_PERIODIC) && level < 2) return P2P_ERR_INVALID_ARG;
     *p = Plan{};
+    p->periodic = (flags & P2P_PLAN_PERIODIC) ? 1 : 0;
     p->kind = kind;
     p->n = n;
     p->level = level;
@@ -245,6 +253,7 @@ int p2p_plan_set_grid(p2p_plan* h, float grid_h, int points_per_box) {
         return P2P_OK;
     }
     if (!(grid_h > 0.0f) || points_per_box < 1 || points_per_box > 4) return P2P_ERR_INVALID_ARG;
+    if (p->periodic) return P2P_ERR_UNSUPPORTED;   // the tabulated lattice displacements are not wrapped
     // the leaf box must hold points_per_box lattice points per edge
     const double box = (double)p->edge / (double)(1 << p->level);
     if (std::fabs(box / ((double)grid_h * points_per_box) - 1.0) > 1e-5) return P2P_ERR_INVALID_ARG;
@@ -276,6 +285,7 @@ int p2p_tree_import(p2p_plan* h, const int32_t* perm, const int32_t* box_start, 
     int st = check_ws(p, ws, ws_bytes);
     if (st) return st;
     if ((int64_t)n_boxes > p->box_cap) return P2P_ERR_INVALID_ARG;
+    if (p->periodic) return P2P_ERR_UNSUPPORTED;   // imported lists carry no image codes
     return tree_import(p, perm, box_start, n_boxes, nbr_start, nbr_idx, n_nbr, ws, static_cast<cudaStream_t>(stream));
 }
 
@@ -429,6 +439,9 @@ int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t*
             if (!red || !(p->flags & P2P_PLAN_GATHER_MAP)) return P2P_ERR_UNSUPPORTED;
             *offset_bytes = L.gather; *capacity = p->red_cap; break;
         case P2P_ARR_SORTED_KEY: *offset_bytes = L.sorted_key; *capacity = p->n; break;
+        case P2P_ARR_NBR_IMG:
+            if (!p->periodic) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.nbr_img; *capacity = 27 * p->box_cap; break;
         default: return P2P_ERR_INVALID_ARG;
     }
     return P2P_OK;

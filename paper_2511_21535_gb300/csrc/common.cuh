@@ -44,7 +44,7 @@ static_assert(offsetof(Header, n_items) == kOpSectionOffset, "header layout");
 struct Layout {                        // byte offsets inside the workspace
     size_t header, keys_a, keys_b, vals_a, perm, sorted_key, hist, scan_tmp, flags,
         box_key, box_start, table, nbr_cnt, nbr_start, nbr_idx, src, box_S, red_start,
-        red_self, red_src, gather, items, pattern, total;
+        red_self, red_src, gather, items, pattern, nbr_img, total;
 };
 
 struct Plan {
@@ -71,6 +71,7 @@ struct Plan {
     int group;                         // warps cooperating on one work item
     int split;                         // Helmholtz RHS from here on form a conjugated second output
     // pattern mode (regular grids): lattice spacing, points per box edge, table strides
+    int periodic;
     int pattern;
     float grid_h;
     int grid_t;

@@ -69,6 +69,8 @@ void noalloc_layout(Plan* p) {
         L.red_start = L.red_self = L.red_src = 0;
     }
     L.gather = 0;
+    L.pattern = 0;
+    L.nbr_img = 0;
     L.total = off;
 }
 
@@ -155,5 +157,7 @@ extern "C" int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t 
     a.red_self = (layout == P2P_LAYOUT_REDUNDANT) ? at<int32_t>(ws, p.L.red_self) : nullptr;
     a.items = at<int2>(ws, p.L.items);
     a.hdr = at<Header>(ws, p.L.header);
+    a.nbr_img = nullptr;
+    a.edge = p.edge;
     return launch_gravity_kernel(&p, a, at<int32_t>(ws, p.L.perm), eps, phi, acc, s);
 }

@@ -73,6 +73,18 @@ struct HelmAdjOp {
         }
     }
 
+    __device__ __forceinline__ void set_shift(float sx, float sy, float sz) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            const float4 r = rec[(int64_t)(tbase + (l < nt ? l : 0)) * words];
+            tx[k] = r.x - sx;
+            ty[k] = r.y - sy;
+            tz[k] = r.z - sz;
+        }
+    }
+
     template <bool CHECK>
     __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
         const float4* rj = sm;
@@ -306,6 +318,18 @@ struct GravAdjOp {
             self[k] = v ? sw_lo + l : -1;
 #pragma unroll
             for (int o = 0; o < NO; ++o) s[k][o] = c[k][o] = p[k][o] = 0.f;
+        }
+    }
+
+    __device__ __forceinline__ void set_shift(float sx, float sy, float sz) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            const float4 r = rec[2 * (int64_t)(tbase + (l < nt ? l : 0))];
+            tx[k] = r.x - sx;
+            ty[k] = r.y - sy;
+            tz[k] = r.z - sz;
         }
     }
 

@@ -41,6 +41,20 @@ struct GravityOp {
         }
     }
 
+    // periodic image of the current neighbour range: targets move by -shift
+    // (reloaded from the records, so no extra registers hold the originals)
+    __device__ __forceinline__ void set_shift(float sx, float sy, float sz) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            const float4 r = rec[tbase + (l < nt ? l : 0)];
+            tx[k] = r.x - sx;
+            ty[k] = r.y - sy;
+            tz[k] = r.z - sz;
+        }
+    }
+
     template <bool CHECK>
     __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
 #pragma unroll 8

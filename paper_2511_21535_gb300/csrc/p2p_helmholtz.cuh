@@ -51,6 +51,19 @@ struct HelmOp {
         }
     }
 
+    // periodic image of the current neighbour range: targets move by -shift
+    __device__ __forceinline__ void set_shift(float sx, float sy, float sz) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            const float4 r = rec[(int64_t)(tbase + (l < nt ? l : 0)) * words];
+            tx[k] = r.x - sx;
+            ty[k] = r.y - sy;
+            tz[k] = r.z - sz;
+        }
+    }
+
     template <bool CHECK>
     __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
         const int stride = W ? W : words;

@@ -45,6 +45,8 @@ struct LoopArgs {
     const int32_t* red_self;
     const int2* items;
     Header* hdr;
+    const int32_t* nbr_img;    // periodic indirect layout: image code per neighbour entry, else nullptr
+    float edge;                // domain edge (periodic image shifts)
 };
 
 // dynamic shared memory: per warp two stages + mbarriers, then (G > 1) the
@@ -127,8 +129,8 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
         const int bs = a.box_start[b];
         const int nt = min(32 * K, a.box_start[b + 1] - bs - t0);
 
-        // source ranges: lane r holds range r
-        int nr, rs = 0, rc = 0, self_base;
+        // source ranges: lane r holds range r (and its image code, periodic indirect)
+        int nr, rs = 0, rc = 0, ri = 13, self_base;
         if (redundant) {
             nr = 1;
             rs = a.red_start[b];
@@ -141,6 +143,7 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
                 const int c = a.nbr_idx[e0 + lane];
                 rs = a.box_start[c];
                 rc = a.box_start[c + 1] - rs;
+                if (a.nbr_img) ri = a.nbr_img[e0 + lane];
             }
             self_base = bs;
         }
@@ -167,9 +170,17 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
         };
 
         bool failed = false;
+        int shift_r = -1;   // range whose image shift the targets carry
         if (pc.r < nr) issue();
         while (cc.r < nr) {
             if (pc.r < nr) issue();
+            if (a.nbr_img && cc.r != shift_r) {
+                // periodic: meet this neighbour's image by moving the targets the other way
+                shift_r = cc.r;
+                const int code = __shfl_sync(FULL, ri, cc.r);
+                op.set_shift((float)(code % 3 - 1) * a.edge, (float)((code / 3) % 3 - 1) * a.edge,
+                             (float)(code / 9 - 1) * a.edge);
+            }
             const int st = cseq & 1;
             if (!warp_wait(&bar[st], (cseq >> 1) & 1)) {
                 failed = true;

@@ -236,11 +236,15 @@ __global__ void __launch_bounds__(256) k_items_fill(const int32_t* __restrict__ 
 
 // Redundant gather: one warp per target box copies the records of each
 // neighbour box, in neighbour order, into the box's stream (16-byte words,
-// coalesced), and optionally the sorted index of every copied record.
+// coalesced), and optionally the sorted index of every copied record.  With
+// periodic boundaries a wrapped neighbour's records are copied with their
+// positions moved to the image the box meets (word 0 holds x, y, z), so the
+// kernel needs no image logic.
 __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ rec, int words,
                                                    const int32_t* __restrict__ box_start,
                                                    const int32_t* __restrict__ nbr_start,
                                                    const int32_t* __restrict__ nbr_idx,
+                                                   const int32_t* __restrict__ nbr_img, float edge,
                                                    const int32_t* __restrict__ red_start, Header* hdr,
                                                    int64_t red_cap, float4* __restrict__ red,
                                                    uint32_t* __restrict__ gather) {
@@ -259,18 +263,33 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
             const int32_t c = nbr_idx[e];
             const int32_t s0 = box_start[c];
             const int32_t cnt = box_start[c + 1] - s0;
-            const int64_t nw = (int64_t)cnt * words;
             const float4* src = rec + (int64_t)s0 * words;
             float4* dst = red + out * words;
-            int64_t w = lane;
-            for (; w + 224 < nw; w += 256) {  // eight independent 16-byte loads in flight per lane
-                float4 v[8];
+            const int32_t code = nbr_img ? nbr_img[e] : 13;
+            if (code != 13) {
+                const float sx = (float)(code % 3 - 1) * edge, sy = (float)((code / 3) % 3 - 1) * edge,
+                            sz = (float)(code / 9 - 1) * edge;
+                for (int32_t l = lane; l < cnt; l += 32) {
+                    float4 v = __ldg(src + (int64_t)l * words);
+                    v.x += sx;
+                    v.y += sy;
+                    v.z += sz;
+                    __stcs(dst + (int64_t)l * words, v);
+                    for (int w = 1; w < words; ++w)
+                        __stcs(dst + (int64_t)l * words + w, __ldg(src + (int64_t)l * words + w));
+                }
+            } else {
+                const int64_t nw = (int64_t)cnt * words;
+                int64_t w = lane;
+                for (; w + 224 < nw; w += 256) {  // eight independent 16-byte loads in flight per lane
+                    float4 v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = __ldg(src + w + 32 * u);
+                    for (int u = 0; u < 8; ++u) v[u] = __ldg(src + w + 32 * u);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) __stcs(dst + w + 32 * u, v[u]);  // streamed: read later by TMA
+                    for (int u = 0; u < 8; ++u) __stcs(dst + w + 32 * u, v[u]);  // streamed: read later by TMA
+                }
+                for (; w < nw; w += 32) __stcs(dst + w, __ldg(src + w));
             }
-            for (; w < nw; w += 32) __stcs(dst + w, __ldg(src + w));
             if (gather)
                 for (int32_t l = lane; l < cnt; l += 32) gather[out + l] = (uint32_t)(s0 + l);
             out += cnt;
@@ -299,7 +318,9 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
         if (st) return st;
         const int sms = num_sms();
         k_red_gather<<<sms * 8, 256, 0, s>>>(rec, words, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
-                                            at<int32_t>(ws, L.nbr_idx), red_start, hdr, p->red_cap,
+                                            at<int32_t>(ws, L.nbr_idx),
+                                            p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr, p->edge, red_start,
+                                            hdr, p->red_cap,
                                             at<float4>(ws, L.red_src),
                                             (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr);
         P2P_LAUNCH_CHECK();

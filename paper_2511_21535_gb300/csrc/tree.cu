@@ -170,18 +170,28 @@ __device__ __forceinline__ int32_t find_box(uint32_t key, const uint32_t* __rest
 // (l % 3 - 1, l / 3 % 3 - 1, l / 9 - 1) and looks it up; the found box
 // indices are ranked across the warp so the list is written ascending.
 // count mode (nbr_start == nullptr): cnt[b] = |N(b)|; write mode: fill nbr_idx.
+// Periodic: cells wrap and the image code (ox+1) + 3(oy+1) + 9(oz+1) records
+// which domain image of the neighbour's sources the box meets.
 __device__ __forceinline__ void neighbours_of(int64_t b, const uint32_t* __restrict__ box_key, int32_t nb, int level,
                                              const int32_t* __restrict__ table, int32_t* __restrict__ cnt,
                                              const int32_t* __restrict__ nbr_start, int32_t* __restrict__ nbr_idx,
-                                             int lane) {
+                                             int32_t* __restrict__ nbr_img, int periodic, int lane) {
     const uint32_t key = box_key[b];
     const int32_t cx = (int32_t)compact3(key), cy = (int32_t)compact3(key >> 1), cz = (int32_t)compact3(key >> 2);
     const int32_t side = 1 << level;
-    int32_t c = -1;
+    int32_t c = -1, code = 13;
     if (lane < 27) {
-        const int32_t x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
-        if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side)
+        int32_t x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+        if (periodic) {
+            int32_t ox = 0, oy = 0, oz = 0;
+            if (x < 0) { x += side; ox = -1; } else if (x >= side) { x -= side; ox = 1; }
+            if (y < 0) { y += side; oy = -1; } else if (y >= side) { y -= side; oy = 1; }
+            if (z < 0) { z += side; oz = -1; } else if (z >= side) { z -= side; oz = 1; }
+            code = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
             c = find_box(morton3(x, y, z), box_key, nb, table);
+        } else if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
+            c = find_box(morton3(x, y, z), box_key, nb, table);
+        }
     }
     const unsigned found = __ballot_sync(FULL, c >= 0);
     if (!nbr_start) {
@@ -194,7 +204,10 @@ __device__ __forceinline__ void neighbours_of(int64_t b, const uint32_t* __restr
         const int32_t v = __shfl_sync(FULL, c, j);
         rank += (v >= 0 && v < c) ? 1 : 0;
     }
-    if (c >= 0) nbr_idx[nbr_start[b] + rank] = c;
+    if (c >= 0) {
+        nbr_idx[nbr_start[b] + rank] = c;
+        if (nbr_img) nbr_img[nbr_start[b] + rank] = code;
+    }
 }
 
 // Grid-stride over the boxes that exist (the count is on the device); the
@@ -202,12 +215,13 @@ __device__ __forceinline__ void neighbours_of(int64_t b, const uint32_t* __restr
 __global__ void __launch_bounds__(256) k_neighbours(const uint32_t* __restrict__ box_key, const Header* hdr,
                                                    int level, const int32_t* __restrict__ table,
                                                    int32_t* __restrict__ cnt, const int32_t* __restrict__ nbr_start,
-                                                   int32_t* __restrict__ nbr_idx) {
+                                                   int32_t* __restrict__ nbr_idx, int32_t* __restrict__ nbr_img,
+                                                   int periodic) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t nb = hdr->n_boxes;
     for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps)
-        neighbours_of(b, box_key, nb, level, table, cnt, nbr_start, nbr_idx, lane);
+        neighbours_of(b, box_key, nb, level, table, cnt, nbr_start, nbr_idx, nbr_img, periodic, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -286,11 +300,12 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     int32_t* nstart = at<int32_t>(ws, L.nbr_start);
     int32_t* nidx = at<int32_t>(ws, L.nbr_idx);
     const unsigned nbl = (unsigned)std::min<int64_t>(blocks_for(bc * 32, 256), (int64_t)num_sms() * 16);
-    k_neighbours<<<nbl, 256, 0, s>>>(box_key, hdr, p->level, table, ncnt, nullptr, nullptr);
+    int32_t* nimg = p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr;
+    k_neighbours<<<nbl, 256, 0, s>>>(box_key, hdr, p->level, table, ncnt, nullptr, nullptr, nullptr, p->periodic);
     P2P_LAUNCH_CHECK();
     st = scan_exclusive(ncnt, nstart, bc, &hdr->n_boxes, &hdr->n_nbr, scratch, s);
     if (st) return st;
-    k_neighbours<<<nbl, 256, 0, s>>>(box_key, hdr, p->level, table, ncnt, nstart, nidx);
+    k_neighbours<<<nbl, 256, 0, s>>>(box_key, hdr, p->level, table, ncnt, nstart, nidx, nimg, p->periodic);
     P2P_LAUNCH_CHECK();
     p->tree_ready = 1;
     p->src_ready = 0;

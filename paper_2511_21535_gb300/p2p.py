@@ -16,12 +16,13 @@ from . import build as _build
 
 GRAVITY, HELMHOLTZ = 0, 1
 LAYOUTS = {"indirect": 0, "redundant": 1, "auto": 2}
-PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING, PLAN_ADJOINT = 0x1, 0x2, 0x4, 0x8
+PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING, PLAN_ADJOINT, PLAN_PERIODIC = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_DOMAIN, FLAG_TIMEOUT, FLAG_CAPACITY, FLAG_LATTICE = 0x1, 0x2, 0x4, 0x8
 
 ARRAYS = {"perm": (0, torch.int32), "box_key": (1, torch.int32), "box_start": (2, torch.int32),
           "nbr_start": (3, torch.int32), "nbr_idx": (4, torch.int32), "red_start": (5, torch.int32),
-          "red_self": (6, torch.int32), "gather_idx": (7, torch.int32), "sorted_key": (8, torch.int32)}
+          "red_self": (6, torch.int32), "gather_idx": (7, torch.int32), "sorted_key": (8, torch.int32),
+          "nbr_img": (9, torch.int32)}
 COUNTERS = ("n_boxes", "n_nbr", "flags", "total_src", "pairs", "n_items")
 PHASES = ("tree", "restructure", "kernel", "operator")
 
@@ -153,7 +154,7 @@ class Plan:
 
     def __init__(self, kind: str, n: int, level: int, lo, edge: float, nrhs: int = 1,
                  layout: str = "redundant", gather_map: bool = False, plain_fp32: bool = False,
-                 timing: bool = False, adjoint: bool = False, device=None,
+                 timing: bool = False, adjoint: bool = False, periodic: bool = False, device=None,
                  workspace: torch.Tensor | None = None):
         lib = load()
         self.kind = kind
@@ -161,9 +162,11 @@ class Plan:
         self.nrhs = int(nrhs)
         self.level = int(level)
         self.layout = layout
+        self.periodic = bool(periodic)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         flags = (PLAN_GATHER_MAP if gather_map else 0) | (PLAN_PLAIN_FP32 if plain_fp32 else 0) | \
-                (PLAN_TIMING if timing else 0) | (PLAN_ADJOINT if adjoint else 0)
+                (PLAN_TIMING if timing else 0) | (PLAN_ADJOINT if adjoint else 0) | \
+                (PLAN_PERIODIC if periodic else 0)
         lo_arr = (ctypes.c_float * 3)(*[float(v) for v in lo])
         h = ctypes.c_void_p()
         kid = {"gravity": GRAVITY, "helmholtz": HELMHOLTZ}[kind]
@@ -312,19 +315,23 @@ def _need(t, dtype, shape, device):
 # one-call conveniences: tree -> restructure -> operator
 # ---------------------------------------------------------------------------
 
-def gravity(pos, mass, level, lo, edge, eps, layout="redundant", plan: Plan | None = None):
+def gravity(pos, mass, level, lo, edge, eps, layout="redundant", plan: Plan | None = None,
+            periodic: bool = False):
     """Softened-gravity near field (phi [n], acc [n,3]) in original particle order."""
-    plan = plan or Plan("gravity", pos.shape[0], level, lo, edge, layout=layout, device=pos.device)
+    plan = plan or Plan("gravity", pos.shape[0], level, lo, edge, layout=layout, periodic=periodic,
+                        device=pos.device)
     plan.tree_build(pos)
     plan.restructure(pos, mass)
     return plan.gravity(eps)
 
 
-def helmholtz(pos, q, level, lo, edge, k, layout="redundant", plan: Plan | None = None):
+def helmholtz(pos, q, level, lo, edge, k, layout="redundant", plan: Plan | None = None,
+              periodic: bool = False):
     """Helmholtz near field u [nrhs, n] (complex64) in original particle order."""
     if q.dim() == 1:
         q = q.unsqueeze(0)
     plan = plan or Plan("helmholtz", pos.shape[0], level, lo, edge, nrhs=q.shape[0], layout=layout,
+                        periodic=periodic,
                         device=pos.device)
     plan.tree_build(pos)
     plan.restructure(pos, q.contiguous())
