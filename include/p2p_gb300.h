@@ -17,7 +17,16 @@
  *                         neighbour sources into one contiguous per-box
  *                         stream (the "Redundant" implementation, data
  *                         duplicated so that each worker reads one
- *                         contiguous block).
+ *                         contiguous block);
+ *   P2P_LAYOUT_PAIRTASK   the thread-level form of the redundant design: one
+ *                         task per (target box, source box) interaction,
+ *                         whose record block holds the target box's
+ *                         particles followed by the source box's (array of
+ *                         structures, both attributes per task, Section
+ *                         5.2.1); every task writes its own partial results
+ *                         and a deterministic reduction in neighbour order
+ *                         adds them per target afterwards (results
+ *                         duplicated, then reduced, Section 1.1).
  *
  * Kernels (the paper names the physics, Sections 5.1 and 5.2, not formulas;
  * these are the library's definitions):
@@ -77,7 +86,12 @@ typedef enum {
 } p2p_status;
 
 typedef enum { P2P_GRAVITY = 0, P2P_HELMHOLTZ = 1 } p2p_kernel_kind;
-typedef enum { P2P_LAYOUT_INDIRECT = 0, P2P_LAYOUT_REDUNDANT = 1, P2P_LAYOUT_AUTO = 2 } p2p_layout;
+typedef enum {
+    P2P_LAYOUT_INDIRECT = 0,
+    P2P_LAYOUT_REDUNDANT = 1,
+    P2P_LAYOUT_AUTO = 2,       /* batches only: the autotuner picks indirect or redundant */
+    P2P_LAYOUT_PAIRTASK = 3    /* single plans only; forward operators only               */
+} p2p_layout;
 
 /* plan flags */
 #define P2P_PLAN_GATHER_MAP  0x1u  /* restructuring also writes the gather map      */
@@ -98,6 +112,7 @@ typedef enum { P2P_LAYOUT_INDIRECT = 0, P2P_LAYOUT_REDUNDANT = 1, P2P_LAYOUT_AUT
 
 /* limits of this build */
 #define P2P_MAX_N      (1LL << 26) /* particles per plan (27 n must fit in int32)   */
+#define P2P_MAX_N_PAIRTASK (1LL << 25) /* pair-task plans (54 n must fit in int32)  */
 #define P2P_MAX_LEVEL  10          /* octree levels (30-bit Morton keys)            */
 #define P2P_MAX_NRHS   16
 
@@ -120,7 +135,8 @@ int p2p_abi_version(void);
  *           evaluated in float32 as written (one subtraction, one product);
  *           points with (x - lo) * s outside [0, 2^level] are out of domain
  *   nrhs    right-hand sides (Helmholtz, 1..P2P_MAX_NRHS; must be 1 for gravity)
- *   layout  P2P_LAYOUT_INDIRECT or P2P_LAYOUT_REDUNDANT
+ *   layout  P2P_LAYOUT_INDIRECT, P2P_LAYOUT_REDUNDANT or P2P_LAYOUT_PAIRTASK
+ *           (pair-task plans: n <= P2P_MAX_N_PAIRTASK, no P2P_PLAN_ADJOINT)
  *   flags   P2P_PLAN_* bits
  * Returns P2P_ERR_INVALID_ARG on a bad shape, P2P_ERR_OOM if the host
  * allocation fails.  *out is NULL on failure.
@@ -191,9 +207,12 @@ int p2p_tree_import(p2p_plan* plan, const int32_t* perm, const int32_t* box_star
 
 /*
  * Collect, part 2 -- restructuring.  Gathers positions and source strengths
- * into box order (both layouts), and for P2P_LAYOUT_REDUNDANT copies each
+ * into box order (every layout), and for P2P_LAYOUT_REDUNDANT copies each
  * box's neighbour sources into one contiguous stream (Section 5.2.1), plus
- * the gather map if P2P_PLAN_GATHER_MAP.
+ * the gather map if P2P_PLAN_GATHER_MAP.  For P2P_LAYOUT_PAIRTASK it lists
+ * the tasks (one per neighbour-list entry e = (b, c)), and copies task e's
+ * block [records of b | records of c] to offset pt_start[e] of the task
+ * stream; the gather map then holds the sorted index of every copied record.
  *   pos        float32 [n][3]
  *   strength   gravity: float32 mass [n]; Helmholtz: complex64 q [nrhs][n]
  */
@@ -204,6 +223,8 @@ int p2p_restructure(p2p_plan* plan, const float* pos, const void* strength, void
  * Compute + update -- softened gravity.  Needs p2p_tree_build (or import) and
  * p2p_restructure on this workspace first.  Writes phi float32 [n] and acc
  * float32 [n][3] in original particle order.  eps >= 0 (float32).
+ * Pair-task plans: the kernel writes one partial result per (task, target)
+ * and a reduction pass adds each target's partials in neighbour-list order.
  */
 int p2p_gravity(p2p_plan* plan, float eps, float* phi, float* acc, void* ws, size_t ws_bytes,
                 void* stream);
@@ -213,7 +234,7 @@ int p2p_gravity(p2p_plan* plan, float eps, float* phi, float* acc, void* ws, siz
  * order.  k is the float32 wavenumber.  When k times the largest in-box
  * distance stays below 100 pi the sine and cosine use the hardware
  * approximation (absolute error below 1e-6 there); otherwise the accurate
- * library routines.
+ * library routines.  Pair-task plans reduce partial results as p2p_gravity.
  */
 int p2p_helmholtz(p2p_plan* plan, float k, void* u, void* ws, size_t ws_bytes, void* stream);
 
@@ -229,6 +250,7 @@ int p2p_helmholtz(p2p_plan* plan, float k, void* u, void* ws, size_t ws_bytes, v
  *   gbar      complex64 [nrhs][n]
  *   grad_q    complex64 [nrhs][n] or NULL;  grad_pos float32 [n][3] or NULL
  * With grad_pos == NULL this is the forward operator with k -> -k on gbar.
+ * Pair-task plans return P2P_ERR_UNSUPPORTED (as does p2p_gravity_adjoint).
  * With grad_pos the plan must have P2P_PLAN_ADJOINT (else
  * P2P_ERR_UNSUPPORTED).  Needs the tree; overwrites the restructured
  * records, so run p2p_restructure again before the next p2p_helmholtz.
@@ -331,7 +353,10 @@ typedef enum {
     P2P_ARR_SORTED_KEY = 8,  /* uint32 [n]              Morton key, sorted order     */
     P2P_ARR_NBR_IMG = 9,     /* int32 [n_nbr] periodic: image code (ox+1)+3(oy+1)+9(oz+1) */
                              /* of each neighbour entry, o = image offset in domain edges */
-    P2P_ARR_COUNT = 10
+    P2P_ARR_ENT_BOX = 10,    /* int32 [n_nbr]   pair tasks: target box of entry e  */
+    P2P_ARR_PT_START = 11,   /* int32 [n_nbr+1] pair tasks: record block bounds     */
+    P2P_ARR_PART_START = 12, /* int32 [n_nbr+1] pair tasks: partial-result bounds   */
+    P2P_ARR_COUNT = 13
 } p2p_array_id;
 
 /*
@@ -339,7 +364,8 @@ typedef enum {
  * *capacity elements reserved (the used length is given by the counters).
  * Returns P2P_ERR_UNSUPPORTED for an array the plan does not keep (the
  * gather map without P2P_PLAN_GATHER_MAP; redundant arrays for the indirect
- * layout).
+ * layout; pair-task arrays for the other layouts).  For pair-task plans
+ * P2P_ARR_GATHER_IDX covers the task stream (pt_start[n_nbr] records).
  */
 int p2p_plan_array(const p2p_plan* plan, int which, int64_t* offset_bytes, int64_t* capacity);
 
@@ -348,7 +374,7 @@ typedef enum {
     P2P_CTR_N_BOXES = 0,     /* non-empty leaf boxes                        */
     P2P_CTR_N_NBR = 1,       /* neighbour-list entries E                    */
     P2P_CTR_FLAGS = 2,       /* P2P_FLAG_* bits                             */
-    P2P_CTR_TOTAL_SRC = 3,   /* redundant records, sum_b S_b                */
+    P2P_CTR_TOTAL_SRC = 3,   /* redundant records sum_b S_b (pair tasks: task-stream records) */
     P2P_CTR_PAIRS = 4,       /* ordered pairs sum_b n_b S_b - n (last op)   */
     P2P_CTR_N_ITEMS = 5,     /* work items of the last operator call        */
     P2P_CTR_COUNT = 6

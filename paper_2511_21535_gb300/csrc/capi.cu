@@ -36,6 +36,8 @@ void compute_layout(Plan* p) {
     L.hist = take(((size_t)256 * p->sort_tiles + 1) * 4);
     int64_t scan_max = (int64_t)256 * p->sort_tiles;
     if (n > scan_max) scan_max = n;
+    const bool pt = p->layout == P2P_LAYOUT_PAIRTASK;
+    if (pt && 27 * bc > scan_max) scan_max = 27 * bc;   // scans over neighbour entries
     L.scan_tmp = take(scan_scratch_bytes(scan_max));
     L.flags = take((n + 1) * 4);
     L.box_key = take(bc * 4);
@@ -49,13 +51,20 @@ void compute_layout(Plan* p) {
     L.box_S = take((bc + 1) * 4);
     L.items = take((size_t)p->items_cap * 8);
     L.pattern = (p->kind == P2P_HELMHOLTZ) ? take((size_t)kPatternMaxEntries * 8) : 0;
+    L.red_start = L.red_self = L.red_src = L.gather = 0;
+    L.ent_box = L.pt_start = L.part_start = L.part = 0;
     if (p->layout == P2P_LAYOUT_REDUNDANT) {
         L.red_start = take((bc + 1) * 4);
         L.red_self = take(bc * 4);
+    } else if (pt) {
+        L.ent_box = take((size_t)27 * bc * 4);
+        L.pt_start = take(((size_t)27 * bc + 1) * 4);
+        L.part_start = take(((size_t)27 * bc + 1) * 4);
+        L.part = take((size_t)p->part_cap * pairtask_part_floats(p->kind, p->nrhs) * 4);
+    }
+    if (p->layout == P2P_LAYOUT_REDUNDANT || pt) {   // the per-box streams, or the task stream
         L.red_src = take((size_t)p->red_cap * p->rec_alloc_words * 16);
         L.gather = (p->flags & P2P_PLAN_GATHER_MAP) ? take((size_t)p->red_cap * 4) : 0;
-    } else {
-        L.red_start = L.red_self = L.red_src = L.gather = 0;
     }
     L.total = off;
 }
@@ -99,10 +108,22 @@ LoopArgs loop_args(const Plan* p, void* ws, int words) {
     a.red_self = (p->layout == P2P_LAYOUT_REDUNDANT) ? at<int32_t>(ws, L.red_self) : nullptr;
     a.items = at<int2>(ws, L.items);
     a.hdr = at<Header>(ws, L.header);
-    // periodic images: the redundant streams carry shifted sources; the indirect
-    // layout shifts the targets per neighbour range
+    // periodic images: the redundant and task streams carry shifted sources;
+    // the indirect layout shifts the targets per neighbour range
     a.nbr_img = (p->periodic && p->layout == P2P_LAYOUT_INDIRECT) ? at<int32_t>(ws, L.nbr_img) : nullptr;
     a.edge = p->edge;
+    a.ent_box = a.pt_start = a.part_start = nullptr;
+    a.part = nullptr;
+    a.part_cap = 0;
+    if (p->layout == P2P_LAYOUT_PAIRTASK) {
+        // targets and sources both come from the task stream
+        a.rec = a.red = at<float4>(ws, L.red_src);
+        a.ent_box = at<int32_t>(ws, L.ent_box);
+        a.pt_start = at<int32_t>(ws, L.pt_start);
+        a.part_start = at<int32_t>(ws, L.part_start);
+        a.part = at<float>(ws, L.part);
+        a.part_cap = p->part_cap;
+    }
     return a;
 }
 
@@ -115,7 +136,10 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     if (!lo || !(edge > 0.0f) || !(edge < 3.0e38f)) return P2P_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
         if (!(lo[a] == lo[a]) || lo[a] > 3.0e38f || lo[a] < -3.0e38f) return P2P_ERR_INVALID_ARG;
-    if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT) return P2P_ERR_INVALID_ARG;
+    if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT && layout != P2P_LAYOUT_PAIRTASK)
+        return P2P_ERR_INVALID_ARG;
+    if (layout == P2P_LAYOUT_PAIRTASK && (n > P2P_MAX_N_PAIRTASK || (flags & P2P_PLAN_ADJOINT)))
+        return P2P_ERR_INVALID_ARG;
     if (kind == P2P_GRAVITY && nrhs != 1) return P2P_ERR_INVALID_ARG;
     if (nrhs < 1 || nrhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
     if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING | P2P_PLAN_ADJOINT |
@@ -135,7 +159,8 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     p->flags = flags;
     const int64_t boxes = (int64_t)1 << (3 * level);
     p->box_cap = n < boxes ? n : boxes;
-    p->red_cap = 27 * n;
+    p->red_cap = (layout == P2P_LAYOUT_PAIRTASK ? 54 : 27) * n;
+    p->part_cap = (layout == P2P_LAYOUT_PAIRTASK) ? 27 * n : 0;
     p->rec_words = (kind == P2P_GRAVITY) ? 1 : helmholtz_rec_words(nrhs);
     p->rec_alloc_words = p->rec_words;
     if (flags & P2P_PLAN_ADJOINT)
@@ -151,10 +176,12 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
         p->tile = nrhs >= 4 ? 32 : 64;
     }
     p->ctas_per_sm = 0;
-    p->group = 4;
+    // a pair task holds one box's sources, usually a single tile: one warp per task
+    p->group = (layout == P2P_LAYOUT_PAIRTASK) ? 1 : 4;
     p->split = nrhs;
     p->rmax = 2.0f * (edge / (float)(1 << level)) * 1.7320508f;
-    p->items_cap = p->box_cap + (n + 31) / 32 + 1;
+    p->items_cap = (layout == P2P_LAYOUT_PAIRTASK) ? 27 * p->box_cap + (27 * n + 31) / 32 + 1
+                                                   : p->box_cap + (n + 31) / 32 + 1;
     compute_layout(p);
     return P2P_OK;
 }
@@ -246,6 +273,7 @@ int p2p_plan_set_grid(p2p_plan* h, float grid_h, int points_per_box) {
     if (!h) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_HELMHOLTZ) return P2P_ERR_UNSUPPORTED;
+    if (p->layout == P2P_LAYOUT_PAIRTASK && points_per_box != 0) return P2P_ERR_UNSUPPORTED;
     if (points_per_box == 0) {
         p->pattern = 0;
         p->rec_words = helmholtz_rec_words(p->nrhs);
@@ -319,6 +347,10 @@ int p2p_gravity(p2p_plan* h, float eps, float* phi, float* acc, void* ws, size_t
     st = launch_gravity_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), eps, phi, acc, s);
     if (st) return st;
     ev_end(p, P2P_PHASE_KERNEL, s);
+    if (p->layout == P2P_LAYOUT_PAIRTASK) {
+        st = pairtask_reduce_gravity(p, ws, phi, acc, s);
+        if (st) return st;
+    }
     ev_end(p, P2P_PHASE_OPERATOR, s);
     return P2P_OK;
 }
@@ -349,6 +381,10 @@ int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void
                                  HelmOut{static_cast<float2*>(u), nullptr, p->nrhs}, s);
     if (st) return st;
     ev_end(p, P2P_PHASE_KERNEL, s);
+    if (p->layout == P2P_LAYOUT_PAIRTASK) {
+        st = pairtask_reduce_helmholtz(p, ws, static_cast<float2*>(u), s);
+        if (st) return st;
+    }
     ev_end(p, P2P_PHASE_OPERATOR, s);
     return P2P_OK;
 }
@@ -361,6 +397,7 @@ int p2p_helmholtz_adjoint(p2p_plan* h, float k, const float* pos, const void* q,
         return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_HELMHOLTZ || !(k == k) || !(fabsf(k) < 1.0e30f)) return P2P_ERR_INVALID_ARG;
+    if (p->layout == P2P_LAYOUT_PAIRTASK) return P2P_ERR_UNSUPPORTED;
     int st = check_ws(p, ws, ws_bytes);
     if (st) return st;
     if (!p->tree_ready) return P2P_ERR_STATE;
@@ -405,6 +442,7 @@ int p2p_gravity_adjoint(p2p_plan* h, float eps, const float* pos, const float* m
         return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_GRAVITY || !(eps >= 0.0f) || !(eps < 1.0e19f)) return P2P_ERR_INVALID_ARG;
+    if (p->layout == P2P_LAYOUT_PAIRTASK) return P2P_ERR_UNSUPPORTED;
     int st = check_ws(p, ws, ws_bytes);
     if (st) return st;
     if (!p->tree_ready) return P2P_ERR_STATE;
@@ -423,6 +461,7 @@ int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t*
     const Plan* p = &h->p;
     const Layout& L = p->L;
     const bool red = p->layout == P2P_LAYOUT_REDUNDANT;
+    const bool pt = p->layout == P2P_LAYOUT_PAIRTASK;
     switch (which) {
         case P2P_ARR_PERM: *offset_bytes = L.perm; *capacity = p->n; break;
         case P2P_ARR_BOX_KEY: *offset_bytes = L.box_key; *capacity = p->box_cap; break;
@@ -436,12 +475,21 @@ int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t*
             if (!red) return P2P_ERR_UNSUPPORTED;
             *offset_bytes = L.red_self; *capacity = p->box_cap; break;
         case P2P_ARR_GATHER_IDX:
-            if (!red || !(p->flags & P2P_PLAN_GATHER_MAP)) return P2P_ERR_UNSUPPORTED;
+            if (!(red || pt) || !(p->flags & P2P_PLAN_GATHER_MAP)) return P2P_ERR_UNSUPPORTED;
             *offset_bytes = L.gather; *capacity = p->red_cap; break;
         case P2P_ARR_SORTED_KEY: *offset_bytes = L.sorted_key; *capacity = p->n; break;
         case P2P_ARR_NBR_IMG:
             if (!p->periodic) return P2P_ERR_UNSUPPORTED;
             *offset_bytes = L.nbr_img; *capacity = 27 * p->box_cap; break;
+        case P2P_ARR_ENT_BOX:
+            if (!pt) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.ent_box; *capacity = 27 * p->box_cap; break;
+        case P2P_ARR_PT_START:
+            if (!pt) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.pt_start; *capacity = 27 * p->box_cap + 1; break;
+        case P2P_ARR_PART_START:
+            if (!pt) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.part_start; *capacity = 27 * p->box_cap + 1; break;
         default: return P2P_ERR_INVALID_ARG;
     }
     return P2P_OK;

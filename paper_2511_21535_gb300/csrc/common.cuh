@@ -23,8 +23,9 @@ struct Header {
     int32_t tree_pad[13];
     // restructuring section (zeroed at the start of each restructuring), offset 64
     unsigned long long pairs_nS;       // sum_b n_b S_b
-    int32_t total_src;                 // sum_b S_b (redundant records)
-    int32_t restr_pad[13];
+    int32_t total_src;                 // sum_b S_b (redundant records; pair tasks: task-stream records)
+    int32_t part_total;                // pair tasks: partial-result slots, sum_e n_b(e)
+    int32_t restr_pad[12];
     // operator section (zeroed at the start of each operator call), offset 128
     int32_t n_items;
     uint32_t work_ctr;
@@ -44,7 +45,9 @@ static_assert(offsetof(Header, n_items) == kOpSectionOffset, "header layout");
 struct Layout {                        // byte offsets inside the workspace
     size_t header, keys_a, keys_b, vals_a, perm, sorted_key, hist, scan_tmp, flags,
         box_key, box_start, table, nbr_cnt, nbr_start, nbr_idx, src, box_S, red_start,
-        red_self, red_src, gather, items, pattern, nbr_img, total;
+        red_self, red_src, gather, items, pattern, nbr_img,
+        ent_box, pt_start, part_start, part,   // pair tasks (red_src/gather hold the task stream)
+        total;
 };
 
 struct Plan {
@@ -59,7 +62,8 @@ struct Plan {
     unsigned flags;
     int64_t box_cap;                   // min(n, 8^level)
     int64_t items_cap;
-    int64_t red_cap;                   // 27 n records
+    int64_t red_cap;                   // 27 n records (pair tasks: 54 n)
+    int64_t part_cap;                  // pair tasks: 27 n partial-result slots
     int rec_words;                     // 16-byte words per source record (forward)
     int rec_alloc_words;               // words per record the workspace holds (>= adjoint records)
     int sort_tiles;
@@ -156,6 +160,12 @@ inline int helmholtz_adjoint_words(int nrhs) { return 1 + 2 * ((nrhs + 1) / 2); 
 constexpr int kGravityAdjointWords = 2;
 // work items of up to tt targets (tt = 32 * the kernel's targets per lane)
 int build_items(Plan* p, void* ws, int tt, cudaStream_t s);
+// pair tasks: task list, task stream and the reductions of the partial results
+int pairtask_restructure(Plan* p, void* ws, int words, cudaStream_t s);
+int pairtask_reduce_gravity(const Plan* p, void* ws, float* phi, float* acc, cudaStream_t s);
+int pairtask_reduce_helmholtz(const Plan* p, void* ws, float2* u, cudaStream_t s);
+// floats of partial result per (task, target)
+inline int pairtask_part_floats(int kind, int nrhs) { return kind == P2P_GRAVITY ? 4 : 2 * nrhs; }
 int helmholtz_targets_per_lane(const Plan* p, float k);
 int launch_gravity_kernel(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps, float* phi, float* acc,
                           cudaStream_t s);

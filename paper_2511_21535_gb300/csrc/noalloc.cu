@@ -71,6 +71,7 @@ void noalloc_layout(Plan* p) {
     L.gather = 0;
     L.pattern = 0;
     L.nbr_img = 0;
+    L.ent_box = L.pt_start = L.part_start = L.part = 0;
     L.total = off;
 }
 
@@ -159,5 +160,8 @@ extern "C" int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t 
     a.hdr = at<Header>(ws, p.L.header);
     a.nbr_img = nullptr;
     a.edge = p.edge;
+    a.ent_box = a.pt_start = a.part_start = nullptr;
+    a.part = nullptr;
+    a.part_cap = 0;
     return launch_gravity_kernel(&p, a, at<int32_t>(ws, p.L.perm), eps, phi, acc, s);
 }

@@ -12,6 +12,7 @@ namespace p2p {
 template <int K, bool COMP>
 struct GravityOp {
     static constexpr int kOuts = 4 * K;   // floats per lane exchanged between cooperating warps
+    static constexpr bool kPartial = true; // can write pair-task partial results
 
     const float4* __restrict__ rec;
     const int32_t* __restrict__ perm;
@@ -119,6 +120,17 @@ struct GravityOp {
         for (int k = 0; k < K; ++k)
 #pragma unroll
             for (int o = 0; o < 4; ++o) s[k][o] += src[(k * 4 + o) * 32 + lane];
+    }
+
+    // pair task: raw sums (phi not yet negated) to the task's slots
+    __device__ __forceinline__ void end_partial(int lane, void* part, int64_t, int64_t slot) {
+        float4* o = static_cast<float4*>(part) + slot;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            if (l < nt)
+                o[l] = make_float4(s[k][0] - c[k][0], s[k][1] - c[k][1], s[k][2] - c[k][2], s[k][3] - c[k][3]);
+        }
     }
 
     __device__ __forceinline__ void end(int lane) {

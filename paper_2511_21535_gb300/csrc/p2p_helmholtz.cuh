@@ -19,6 +19,7 @@ namespace p2p {
 template <int K, int R, bool COMP, bool PRECISE, int W = 0>
 struct HelmOp {
     static constexpr int kOuts = 2 * R * K;
+    static constexpr bool kPartial = true;    // can write pair-task partial results
 
     const float4* __restrict__ rec;
     const int32_t* __restrict__ perm;
@@ -161,6 +162,22 @@ struct HelmOp {
                 sr[k][q] += src[((k * R + q) * 2 + 0) * 32 + lane];
                 si[k][q] += src[((k * R + q) * 2 + 1) * 32 + lane];
             }
+    }
+
+    // pair task: this task's contribution, scaled, to slot `slot` of each RHS row
+    __device__ __forceinline__ void end_partial(int lane, void* part, int64_t cap, int64_t slot) {
+        const float inv4pi = 0.0795774715459476678844418816862571882f;  // 1 / (4 pi)
+        float2* o = static_cast<float2*>(part) + slot;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            if (l < nt) {
+#pragma unroll
+                for (int q = 0; q < R; ++q)
+                    o[(int64_t)(r0 + q) * cap + l] =
+                        make_float2((sr[k][q] - cr[k][q]) * inv4pi, (si[k][q] - ci[k][q]) * inv4pi);
+            }
+        }
     }
 
     __device__ __forceinline__ void end(int lane) {

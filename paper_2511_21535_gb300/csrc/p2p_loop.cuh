@@ -13,7 +13,11 @@
 // lane issues while the warp computes the previous stage; an mbarrier per
 // stage signals arrival.  Sources are read as ranges of 16-byte records:
 //   redundant layout: one range, the box's contiguous stream (Section 5.2.1);
-//   indirect layout:  one range per neighbour box in the box-ordered array.
+//   indirect layout:  one range per neighbour box in the box-ordered array;
+//   pair tasks:       an item is (task e = (b, c), targets); its targets and
+//                     its one source range both come from the task's block
+//                     [records of b | records of c], and its results go to
+//                     the task's own partial-result slots (reduced later).
 // Items are taken from a global counter (persistent grid, longest-first
 // order prepared by the restructuring pass).  Outputs are owned by exactly
 // one group, so no atomics touch results and the result does not depend on
@@ -47,6 +51,11 @@ struct LoopArgs {
     Header* hdr;
     const int32_t* nbr_img;    // periodic indirect layout: image code per neighbour entry, else nullptr
     float edge;                // domain edge (periodic image shifts)
+    const int32_t* ent_box;    // pair tasks: target box of each task (entry), else nullptr
+    const int32_t* pt_start;   // pair tasks: record block of each task in the task stream (red)
+    const int32_t* part_start; // pair tasks: first partial-result slot of each task
+    void* part;                // pair tasks: partial results
+    int64_t part_cap;          // pair tasks: slots per right-hand side
 };
 
 // dynamic shared memory: per warp two stages + mbarriers, then (G > 1) the
@@ -108,7 +117,8 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
 
     if (a.hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_LATTICE)) return;  // inputs rejected (uniform)
     const int32_t n_items = a.hdr->n_items;
-    const bool redundant = a.red != nullptr;
+    const bool pairtask = a.ent_box != nullptr;
+    const bool redundant = a.red != nullptr;   // also the pair-task stream
     const float4* base = redundant ? a.red : a.rec;
     uint32_t pseq = 0, cseq = 0;       // tiles issued / consumed by this warp
 
@@ -125,13 +135,25 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
         }
         if (item >= n_items) break;
         const int2 it = a.items[item];
-        const int b = it.x, t0 = it.y;
+        const int t0 = it.y;
+        const int b = pairtask ? a.ent_box[it.x] : it.x;
         const int bs = a.box_start[b];
-        const int nt = min(32 * K, a.box_start[b + 1] - bs - t0);
+        const int nbox = a.box_start[b + 1] - bs;
+        const int nt = min(32 * K, nbox - t0);
 
         // source ranges: lane r holds range r (and its image code, periodic indirect)
-        int nr, rs = 0, rc = 0, ri = 13, self_base;
-        if (redundant) {
+        int nr, rs = 0, rc = 0, ri = 13, self_base, tgt = bs + t0;
+        int64_t slot = 0;
+        if (pairtask) {
+            const int e = it.x, tb = a.pt_start[e];
+            nr = 1;
+            rs = tb + nbox;
+            rc = a.pt_start[e + 1] - rs;
+            // only the task of the box with itself holds the targets' own copies
+            self_base = (a.nbr_idx[e] == b) ? rs : -(1 << 30);
+            tgt = tb + t0;
+            slot = (int64_t)a.part_start[e] + t0;
+        } else if (redundant) {
             nr = 1;
             rs = a.red_start[b];
             rc = a.red_start[b + 1] - rs;
@@ -148,7 +170,7 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
             self_base = bs;
         }
         const int sw_lo = self_base + t0, sw_hi = sw_lo + nt;
-        op.begin(bs + t0, nt, sw_lo, lane);
+        op.begin(tgt, nt, sw_lo, lane);
 
         // this warp's tiles: gw, gw + G, gw + 2G, ... of the item's tile sequence
         TileCursor pc{0, 0, 0, 0};
@@ -201,8 +223,17 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
             if (G == 1) return;
             if (lane == 0) abort_flag[group] = 1;
         }
-        if (G == 1) {
+        auto finish = [&]() {
+            if constexpr (Op::kPartial) {
+                if (pairtask) {
+                    op.end_partial(lane, a.part, a.part_cap, slot);
+                    return;
+                }
+            }
             op.end(lane);
+        };
+        if (G == 1) {
+            finish();
         } else {
             float* mine = partial + (size_t)warp * Op::kOuts * 32;
             if (gw != 0) op.store_partial(mine, lane);
@@ -210,7 +241,7 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
             if (gw == 0) {
                 op.fold();
                 for (int w = 1; w < G; ++w) op.add_partial(mine + (size_t)w * Op::kOuts * 32, lane);
-                op.end(lane);
+                finish();
             }
             group_sync<G>(group);
             if (abort_flag[group]) return;

@@ -60,6 +60,7 @@ __global__ void k_pattern_table(double h, double k, int t, int sy, int sz, int s
 template <int K, int R, bool COMPACT = false>
 struct HelmPatternOp : HelmOp<K, R, true, false, 0> {
     using Base = HelmOp<K, R, true, false, 0>;
+    static constexpr bool kPartial = false;   // pattern plans are target-owned
     const float2* tab;   // shared-memory table, already offset by the bias
     int tcode[K];
 

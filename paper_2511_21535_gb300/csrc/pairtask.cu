@@ -1,0 +1,194 @@
+// Pair-task layout: the thread-level form of the redundant design
+// (Section 5.2.1) with results duplicated and reduced afterwards (Section
+// 1.1).
+//
+// One task per neighbour-list entry e = (b, c), target box b, source box c.
+// The task stream holds, per task, the block [records of b | records of c]
+// (both attributes of the interaction in one contiguous block: array of
+// structures); pt_start[e] is the block's first record.  The P2P kernel
+// computes task e's sums for b's targets over c's sources only and writes
+// them to the task's partial-result slots part_start[e] + t (t = target in
+// b).  The update step then adds, per target, the partials of b's tasks in
+// neighbour-list order: a fixed order, so the result is deterministic and
+// no two workers ever write the same output.
+#include <algorithm>
+
+#include "common.cuh"
+#include "device.cuh"
+
+namespace p2p {
+
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// per entry: its target box, the block length n_b + n_c and the slot count n_b
+__global__ void __launch_bounds__(256) k_pt_entries(const int32_t* __restrict__ box_start,
+                                                   const int32_t* __restrict__ nbr_start,
+                                                   const int32_t* __restrict__ nbr_idx, const Header* hdr,
+                                                   int32_t* __restrict__ ent_box, int32_t* __restrict__ blk_len,
+                                                   int32_t* __restrict__ slot_len) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nb = hdr->n_boxes;
+    for (int64_t b = warp; b < nb; b += nwarps) {
+        const int32_t occ = box_start[b + 1] - box_start[b];
+        for (int32_t e = nbr_start[b] + lane; e < nbr_start[b + 1]; e += 32) {
+            const int32_t c = nbr_idx[e];
+            ent_box[e] = (int32_t)b;
+            blk_len[e] = occ + (box_start[c + 1] - box_start[c]);
+            slot_len[e] = occ;
+        }
+    }
+}
+
+// one warp per task copies [records of b | records of c (at its periodic image)]
+__global__ void __launch_bounds__(256) k_pt_gather(const float4* __restrict__ rec, int words,
+                                                  const int32_t* __restrict__ box_start,
+                                                  const int32_t* __restrict__ nbr_idx,
+                                                  const int32_t* __restrict__ ent_box,
+                                                  const int32_t* __restrict__ nbr_img, float edge,
+                                                  const int32_t* __restrict__ pt_start, Header* hdr, int64_t cap,
+                                                  int64_t part_cap, float4* __restrict__ pt,
+                                                  uint32_t* __restrict__ gather) {
+    const int lane = threadIdx.x & 31;
+    // an imported, inconsistent neighbour relation can exceed the capacities
+    if (hdr->total_src < 0 || (int64_t)hdr->total_src > cap || hdr->part_total < 0 ||
+        (int64_t)hdr->part_total > part_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);
+        return;
+    }
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t ne = hdr->n_nbr;
+    for (int64_t e = warp; e < ne; e += nwarps) {
+        const int32_t b = ent_box[e], c = nbr_idx[e];
+        const int32_t sb = box_start[b], nb = box_start[b + 1] - sb;
+        const int32_t sc = box_start[c], nc = box_start[c + 1] - sc;
+        const int64_t out = pt_start[e];
+        warp_copy_records(rec + (int64_t)sb * words, pt + out * words, nb, words, lane, 13, edge);
+        warp_copy_records(rec + (int64_t)sc * words, pt + (out + nb) * words, nc, words, lane,
+                          nbr_img ? nbr_img[e] : 13, edge);
+        if (gather) {
+            for (int32_t l = lane; l < nb; l += 32) gather[out + l] = (uint32_t)(sb + l);
+            for (int32_t l = lane; l < nc; l += 32) gather[out + nb + l] = (uint32_t)(sc + l);
+        }
+    }
+}
+
+int pairtask_restructure(Plan* p, void* ws, int words, cudaStream_t s) {
+    const Layout& L = p->L;
+    Header* hdr = at<Header>(ws, L.header);
+    const int64_t ecap = 27 * p->box_cap;
+    int32_t* ent_box = at<int32_t>(ws, L.ent_box);
+    int32_t* pt_start = at<int32_t>(ws, L.pt_start);
+    int32_t* part_start = at<int32_t>(ws, L.part_start);
+    const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
+    k_pt_entries<<<wb, 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+                                    at<int32_t>(ws, L.nbr_idx), hdr, ent_box, pt_start, part_start);
+    P2P_LAUNCH_CHECK();
+    int st = scan_exclusive(pt_start, pt_start, ecap, &hdr->n_nbr, &hdr->total_src, at<int32_t>(ws, L.scan_tmp), s);
+    if (st) return st;
+    st = scan_exclusive(part_start, part_start, ecap, &hdr->n_nbr, &hdr->part_total, at<int32_t>(ws, L.scan_tmp), s);
+    if (st) return st;
+    k_pt_gather<<<num_sms() * 8, 256, 0, s>>>(at<float4>(ws, L.src), words, at<int32_t>(ws, L.box_start),
+                                            at<int32_t>(ws, L.nbr_idx), ent_box,
+                                            p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr, p->edge, pt_start,
+                                            hdr, p->red_cap, p->part_cap, at<float4>(ws, L.red_src),
+                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr);
+    P2P_LAUNCH_CHECK();
+    return P2P_OK;
+}
+
+// Update: per target, the partials of its box's tasks in neighbour order,
+// compensated, then scattered to original order.  One warp per box.
+__global__ void __launch_bounds__(256) k_pt_reduce_gravity(const int32_t* __restrict__ box_start,
+                                                          const int32_t* __restrict__ nbr_start,
+                                                          const int32_t* __restrict__ part_start,
+                                                          const int32_t* __restrict__ perm, const Header* hdr,
+                                                          const float4* __restrict__ part, float* __restrict__ phi,
+                                                          float* __restrict__ acc) {
+    if (hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_TIMEOUT)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nb = hdr->n_boxes;
+    for (int64_t b = warp; b < nb; b += nwarps) {
+        const int32_t bs = box_start[b], occ = box_start[b + 1] - bs;
+        const int32_t e0 = nbr_start[b], e1 = nbr_start[b + 1];
+        for (int32_t l = lane; l < occ; l += 32) {
+            float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int32_t e = e0; e < e1; ++e) {
+                const float4 v = part[(int64_t)part_start[e] + l];
+                const float in[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const float y = in[o] - c[o];
+                    const float t = s[o] + y;
+                    c[o] = (t - s[o]) - y;
+                    s[o] = t;
+                }
+            }
+            const int64_t o = perm[bs + l];
+            phi[o] = -(s[0] - c[0]);
+            acc[3 * o + 0] = s[1] - c[1];
+            acc[3 * o + 1] = s[2] - c[2];
+            acc[3 * o + 2] = s[3] - c[3];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pt_reduce_helmholtz(const int32_t* __restrict__ box_start,
+                                                            const int32_t* __restrict__ nbr_start,
+                                                            const int32_t* __restrict__ part_start,
+                                                            const int32_t* __restrict__ perm, const Header* hdr,
+                                                            const float2* __restrict__ part, int64_t cap, int nrhs,
+                                                            int64_t n, float2* __restrict__ u) {
+    if (hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_TIMEOUT)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nb = hdr->n_boxes;
+    for (int64_t b = warp; b < nb; b += nwarps) {
+        const int32_t bs = box_start[b], occ = box_start[b + 1] - bs;
+        const int32_t e0 = nbr_start[b], e1 = nbr_start[b + 1];
+        for (int r = 0; r < nrhs; ++r) {
+            const float2* pr = part + (int64_t)r * cap;
+            for (int32_t l = lane; l < occ; l += 32) {
+                float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
+                for (int32_t e = e0; e < e1; ++e) {
+                    const float2 v = pr[(int64_t)part_start[e] + l];
+                    const float yr = v.x - cr, tr = sr + yr;
+                    cr = (tr - sr) - yr;
+                    sr = tr;
+                    const float yi = v.y - ci, ti = si + yi;
+                    ci = (ti - si) - yi;
+                    si = ti;
+                }
+                u[(int64_t)r * n + perm[bs + l]] = make_float2(sr - cr, si - ci);
+            }
+        }
+    }
+}
+
+int pairtask_reduce_gravity(const Plan* p, void* ws, float* phi, float* acc, cudaStream_t s) {
+    const Layout& L = p->L;
+    const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
+    k_pt_reduce_gravity<<<wb, 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+                                           at<int32_t>(ws, L.part_start), at<int32_t>(ws, L.perm),
+                                           at<Header>(ws, L.header), at<float4>(ws, L.part), phi, acc);
+    P2P_LAUNCH_CHECK();
+    return P2P_OK;
+}
+
+int pairtask_reduce_helmholtz(const Plan* p, void* ws, float2* u, cudaStream_t s) {
+    const Layout& L = p->L;
+    const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
+    k_pt_reduce_helmholtz<<<wb, 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+                                             at<int32_t>(ws, L.part_start), at<int32_t>(ws, L.perm),
+                                             at<Header>(ws, L.header), at<float2>(ws, L.part), p->part_cap, p->nrhs,
+                                             p->n, u);
+    P2P_LAUNCH_CHECK();
+    return P2P_OK;
+}
+
+}  // namespace p2p

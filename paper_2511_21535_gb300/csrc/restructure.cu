@@ -173,19 +173,41 @@ __device__ __forceinline__ int cost_class(int32_t nt, int32_t sb) {
     return 63 - __clzll(cost);
 }
 
+// Work units: target boxes (unit u = box b: occupancy n_b, sources S_b), or
+// for pair tasks neighbour entries (u = e = (b, c): n_b targets, n_c sources).
+struct Units {
+    const int32_t* box_start;
+    const int32_t* S;          // per box S_b (box units)
+    const int32_t* ent_box;    // pair tasks: target box per entry, else nullptr
+    const int32_t* nbr_idx;    // pair tasks: source box per entry
+    int64_t cap;               // units the grid covers
+};
+
+__device__ __forceinline__ int32_t unit_count(const Units& U, const Header* hdr) {
+    return U.ent_box ? hdr->n_nbr : hdr->n_boxes;
+}
+__device__ __forceinline__ void unit_shape(const Units& U, int64_t u, int32_t& occ, int32_t& sb) {
+    if (U.ent_box) {
+        const int32_t b = U.ent_box[u], c = U.nbr_idx[u];
+        occ = U.box_start[b + 1] - U.box_start[b];
+        sb = U.box_start[c + 1] - U.box_start[c];
+    } else {
+        occ = U.box_start[u + 1] - U.box_start[u];
+        sb = U.S[u];
+    }
+}
+
 // Cost-class histogram of the work items (items of up to tt targets).
-__global__ void __launch_bounds__(256) k_items_count(const int32_t* __restrict__ box_start,
-                                                    const int32_t* __restrict__ S, Header* hdr, int64_t box_cap,
-                                                    int tt) {
+__global__ void __launch_bounds__(256) k_items_count(Units U, Header* hdr, int tt) {
     __shared__ int32_t cls[kCostClasses];
     __shared__ int32_t items_s;
     for (int c = threadIdx.x; c < kCostClasses; c += blockDim.x) cls[c] = 0;
     if (threadIdx.x == 0) items_s = 0;
     __syncthreads();
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < box_cap && b < hdr->n_boxes) {
-        const int32_t occ = box_start[b + 1] - box_start[b];
-        const int32_t sb = S[b];
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < U.cap && u < unit_count(U, hdr)) {
+        int32_t occ, sb;
+        unit_shape(U, u, occ, sb);
         int32_t ni = 0;
         for (int32_t t0 = 0; t0 < occ; t0 += tt, ++ni) atomicAdd(&cls[cost_class(min(tt, occ - t0), sb)], 1);
         atomicAdd(&items_s, ni);
@@ -198,9 +220,7 @@ __global__ void __launch_bounds__(256) k_items_count(const int32_t* __restrict__
 
 // Place each item in its cost class, heaviest class first.  Blocks reserve a
 // range per class with one atomic, then fill it through shared counters.
-__global__ void __launch_bounds__(256) k_items_fill(const int32_t* __restrict__ box_start,
-                                                   const int32_t* __restrict__ S, Header* hdr, int64_t box_cap,
-                                                   int tt, int2* __restrict__ items) {
+__global__ void __launch_bounds__(256) k_items_fill(Units U, Header* hdr, int tt, int2* __restrict__ items) {
     __shared__ int32_t cls_base[kCostClasses];
     __shared__ int32_t local_cnt[kCostClasses];
     __shared__ int32_t local_cur[kCostClasses];
@@ -213,12 +233,11 @@ __global__ void __launch_bounds__(256) k_items_fill(const int32_t* __restrict__ 
         local_cur[threadIdx.x] = 0;
     }
     __syncthreads();
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = b < box_cap && b < hdr->n_boxes;
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = u < U.cap && u < unit_count(U, hdr);
     int32_t occ = 0, sb = 0;
     if (active) {
-        occ = box_start[b + 1] - box_start[b];
-        sb = S[b];
+        unit_shape(U, u, occ, sb);
         for (int32_t t0 = 0; t0 < occ; t0 += tt) atomicAdd(&local_cnt[cost_class(min(tt, occ - t0), sb)], 1);
     }
     __syncthreads();
@@ -229,7 +248,7 @@ __global__ void __launch_bounds__(256) k_items_fill(const int32_t* __restrict__ 
         for (int32_t t0 = 0; t0 < occ; t0 += tt) {
             const int c = cost_class(min(tt, occ - t0), sb);
             const int32_t pos = cls_base[c] + atomicAdd(&local_cur[c], 1);
-            items[pos] = make_int2((int32_t)b, t0);
+            items[pos] = make_int2((int32_t)u, t0);
         }
     }
 }
@@ -265,31 +284,7 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
             const int32_t cnt = box_start[c + 1] - s0;
             const float4* src = rec + (int64_t)s0 * words;
             float4* dst = red + out * words;
-            const int32_t code = nbr_img ? nbr_img[e] : 13;
-            if (code != 13) {
-                const float sx = (float)(code % 3 - 1) * edge, sy = (float)((code / 3) % 3 - 1) * edge,
-                            sz = (float)(code / 9 - 1) * edge;
-                for (int32_t l = lane; l < cnt; l += 32) {
-                    float4 v = __ldg(src + (int64_t)l * words);
-                    v.x += sx;
-                    v.y += sy;
-                    v.z += sz;
-                    __stcs(dst + (int64_t)l * words, v);
-                    for (int w = 1; w < words; ++w)
-                        __stcs(dst + (int64_t)l * words + w, __ldg(src + (int64_t)l * words + w));
-                }
-            } else {
-                const int64_t nw = (int64_t)cnt * words;
-                int64_t w = lane;
-                for (; w + 224 < nw; w += 256) {  // eight independent 16-byte loads in flight per lane
-                    float4 v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = __ldg(src + w + 32 * u);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) __stcs(dst + w + 32 * u, v[u]);  // streamed: read later by TMA
-                }
-                for (; w < nw; w += 32) __stcs(dst + w, __ldg(src + w));
-            }
+            warp_copy_records(src, dst, cnt, words, lane, nbr_img ? nbr_img[e] : 13, edge);
             if (gather)
                 for (int32_t l = lane; l < cnt; l += 32) gather[out + l] = (uint32_t)(s0 + l);
             out += cnt;
@@ -324,6 +319,8 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
                                             at<float4>(ws, L.red_src),
                                             (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr);
         P2P_LAUNCH_CHECK();
+    } else if (p->layout == P2P_LAYOUT_PAIRTASK) {
+        return pairtask_restructure(p, ws, words, s);
     }
     return P2P_OK;
 }
@@ -396,10 +393,15 @@ int build_items(Plan* p, void* ws, int tt, cudaStream_t s) {
     const int32_t* S = at<int32_t>(ws, L.box_S);
     P2P_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(hdr) + kOpSectionOffset, 0,
                                  sizeof(Header) - kOpSectionOffset, s));
-    k_items_count<<<blocks_for(bc, 256), 256, 0, s>>>(at<int32_t>(ws, L.box_start), S, hdr, bc, tt);
+    Units U{at<int32_t>(ws, L.box_start), S, nullptr, nullptr, bc};
+    if (p->layout == P2P_LAYOUT_PAIRTASK) {
+        U.ent_box = at<int32_t>(ws, L.ent_box);
+        U.nbr_idx = at<int32_t>(ws, L.nbr_idx);
+        U.cap = 27 * bc;
+    }
+    k_items_count<<<blocks_for(U.cap, 256), 256, 0, s>>>(U, hdr, tt);
     P2P_LAUNCH_CHECK();
-    k_items_fill<<<blocks_for(bc, 256), 256, 0, s>>>(at<int32_t>(ws, L.box_start), S, hdr, bc, tt,
-                                                    at<int2>(ws, L.items));
+    k_items_fill<<<blocks_for(U.cap, 256), 256, 0, s>>>(U, hdr, tt, at<int2>(ws, L.items));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }

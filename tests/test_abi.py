@@ -57,7 +57,8 @@ def _create(lib, kind=0, n=1000, level=3, lo=(0.0, 0.0, 0.0), edge=1.0, nrhs=1, 
 
 def test_plan_argument_checks(lib):
     bad = [dict(n=0), dict(n=(1 << 26) + 1), dict(level=0), dict(level=11), dict(edge=0.0), dict(edge=-1.0),
-           dict(kind=2), dict(layout=3), dict(nrhs=2), dict(kind=1, nrhs=0), dict(kind=1, nrhs=17),
+           dict(kind=2), dict(layout=4), dict(layout=2), dict(nrhs=2), dict(kind=1, nrhs=0), dict(kind=1, nrhs=17),
+           dict(layout=3, n=(1 << 25) + 1), dict(layout=3, flags=0x8), dict(flags=0x10, level=1),
            dict(flags=0x100), dict(lo=(float("nan"), 0.0, 0.0))]
     for kw in bad:
         st, h = _create(lib, **kw)
@@ -69,6 +70,11 @@ def test_plan_argument_checks(lib):
     nb = ctypes.c_size_t()
     assert lib.p2p_plan_workspace_bytes(h, ctypes.byref(nb)) == 0
     assert nb.value > 27 * 1000 * 16          # holds the redundant streams
+    st, hp = _create(lib, layout=3)
+    assert st == 0 and hp.value
+    nbp = ctypes.c_size_t()
+    assert lib.p2p_plan_workspace_bytes(hp, ctypes.byref(nbp)) == 0
+    assert nbp.value > nb.value + 27 * 1000 * 16   # task stream (54 n records) and partial results
     lib.p2p_plan_set_tuning.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
     assert lib.p2p_plan_set_tuning(h, 3, 64, 0, 1) == 1
     assert lib.p2p_plan_set_tuning(h, 2, 48, 0, 1) == 1
@@ -80,6 +86,7 @@ def test_plan_argument_checks(lib):
     assert lib.p2p_gravity(h, 1e-3, 256, 256, 0, 0, None) == 7      # no workspace
     lib.p2p_plan_destroy.argtypes = [ctypes.c_void_p]
     assert lib.p2p_plan_destroy(h) == 0
+    assert lib.p2p_plan_destroy(hp) == 0
     assert lib.p2p_plan_destroy(None) == 0
 
 
