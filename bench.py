@@ -60,6 +60,23 @@ MUFU_PER_SM_CLK = 16           # nominal XU (MUFU) throughput per SM per clock
 FP32_PER_SM_CLK = 128
 
 
+def replica_throughput(units: float, ms: float, dist: bool, device=None):
+    """Whole-job throughput of independent replicas (one per GPU): the units
+    of all ranks over the slowest rank's time per step.  Returns (units/s,
+    max ms, total units); every rank gets the same values."""
+    if not dist:
+        return units / (ms * 1e-3), ms, units
+    import torch
+    import torch.distributed as td
+    t_ms = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    t_units = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    td.all_reduce(t_ms, op=td.ReduceOp.MAX)
+    td.all_reduce(t_units, op=td.ReduceOp.SUM)
+    td.barrier()
+    ms_max, total = float(t_ms.item()), float(t_units.item())
+    return total / (ms_max * 1e-3), ms_max, total
+
+
 def make_problem(name: str, periodic: bool = False):
     prob = _make_problem(name)
     prob.extra["periodic"] = bool(periodic)
@@ -275,12 +292,7 @@ def run_gpu(args, rank, world, local_rank):
         launches = launches_per_replay * args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
-    if dist:
-        import torch.distributed as td
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        td.all_reduce(tt, op=td.ReduceOp.MAX)
-        ms = float(tt.item())
-        td.barrier()
+    value, ms, _ = replica_throughput(pairs, ms, dist, dev)
 
     # end to end through the API from pinned host buffers: H2D, full step, D2H
     hpos = torch.from_numpy(prob.pos).pin_memory()
@@ -322,6 +334,7 @@ def run_gpu(args, rank, world, local_rank):
     h2d = prob.pos.nbytes + prob.strength.nbytes
     d2h = sum(t.numel() * t.element_size() for t in hout)
     e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    e2e_value, e2e_mean, _ = replica_throughput(pairs, e2e_mean, dist, dev)
 
     kern_ms = sum(phases["kernel"]) / len(phases["kernel"])
     csum = clk.summary(t_start, t_end)
@@ -344,7 +357,7 @@ def run_gpu(args, rank, world, local_rank):
     achieved = geo_pairs / (kern_ms * 1e-3)
     result = {
         "metric": METRIC,
-        "value": world * pairs / (ms * 1e-3),
+        "value": value,
         "unit": "pairs/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -356,7 +369,7 @@ def run_gpu(args, rank, world, local_rank):
         "dtype": "f32",
         "data": "synthetic",
         "config": workload_config(prob, layout, args.pattern),
-        "e2e": {"value": world * pairs / (e2e_mean * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
         "roofline": {"bound": "alu", "pipe": pipe, "kernel": f"k_{prob.kind}", "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak,
