@@ -50,6 +50,8 @@ __global__ void k_batch_merge(const int32_t* __restrict__ perm_i, const int32_t*
                               int32_t B_i, int32_t E_i, int32_t P, int32_t Boff, int32_t Eoff,
                               int32_t* __restrict__ perm, int32_t* __restrict__ bs, int32_t* __restrict__ ns,
                               int32_t* __restrict__ ni) {
+    pdl_wait();
+    pdl_release();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t m = std::max<int64_t>(n_i, std::max<int64_t>(B_i, E_i));
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += stride) {
@@ -63,6 +65,8 @@ __global__ void k_batch_merge(const int32_t* __restrict__ perm_i, const int32_t*
 }
 
 __global__ void k_batch_finish(Header* hdr, int32_t* bs, int32_t* ns, int32_t B, int32_t E, int32_t N) {
+    pdl_wait();
+    pdl_release();
     bs[B] = N;
     ns[B] = E;
     hdr->n_boxes = B;
@@ -213,18 +217,21 @@ int p2p_batch_build(p2p_batch* h, const float* pos, void* ws, size_t ws_bytes, v
         P2P_CUDA_TRY(cudaStreamSynchronize(s));
         if (hdr.flags & P2P_FLAG_DOMAIN) return P2P_ERR_DOMAIN;
         const int64_t m = std::max<int64_t>(pi.n, std::max<int64_t>(hdr.n_boxes, hdr.n_nbr));
-        k_batch_merge<<<std::min<unsigned>(blocks_for(m, 256), (unsigned)num_sms() * 8), 256, 0, s>>>(
+        P2P_CUDA_TRY(launch_pdl(k_batch_merge, std::min<unsigned>(blocks_for(m, 256), (unsigned)num_sms() * 8), 256, 0, s, 
             at<int32_t>(tws, pi.L.perm), at<int32_t>(tws, pi.L.box_start), at<int32_t>(tws, pi.L.nbr_start),
             at<int32_t>(tws, pi.L.nbr_idx), pi.n, hdr.n_boxes, hdr.n_nbr, (int32_t)b.off[i], Boff, Eoff,
             at<int32_t>(cws, b.comb.L.perm), at<int32_t>(cws, b.comb.L.box_start), at<int32_t>(cws, b.comb.L.nbr_start),
-            at<int32_t>(cws, b.comb.L.nbr_idx));
+            at<int32_t>(cws, b.comb.L.nbr_idx)));
         P2P_LAUNCH_CHECK();
         Boff += hdr.n_boxes;
         Eoff += hdr.n_nbr;
     }
-    P2P_CUDA_TRY(cudaMemsetAsync(at<Header>(cws, b.comb.L.header), 0, kOpSectionOffset, s));
-    k_batch_finish<<<1, 1, 0, s>>>(at<Header>(cws, b.comb.L.header), at<int32_t>(cws, b.comb.L.box_start),
-                                   at<int32_t>(cws, b.comb.L.nbr_start), Boff, Eoff, (int32_t)b.N);
+    {
+        int st0 = fill32(at<Header>(cws, b.comb.L.header), 0u, kOpSectionOffset / 4, s);
+        if (st0) return st0;
+    }
+    P2P_CUDA_TRY(launch_pdl(k_batch_finish, 1, 1, 0, s, at<Header>(cws, b.comb.L.header), at<int32_t>(cws, b.comb.L.box_start),
+                                   at<int32_t>(cws, b.comb.L.nbr_start), Boff, Eoff, (int32_t)b.N));
     P2P_LAUNCH_CHECK();
     P2P_CUDA_TRY(cudaStreamSynchronize(s));
     b.comb.tree_ready = 1;

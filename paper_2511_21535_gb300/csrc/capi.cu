@@ -1,6 +1,7 @@
 // C ABI: plans, workspace layout, argument checks, phase timing.
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <new>
 
 #include "common.cuh"
@@ -14,6 +15,14 @@ namespace p2p {
 
 static std::atomic<long long> g_launches{0};
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("P2P_NO_PDL");
+        return !(v && v[0] == '1');
+    }();
+    return on;
+}
 
 static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -176,8 +185,15 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
         p->tile = nrhs >= 4 ? 32 : 64;
     }
     p->ctas_per_sm = 0;
-    // a pair task holds one box's sources, usually a single tile: one warp per task
-    p->group = (layout == P2P_LAYOUT_PAIRTASK) ? 1 : 4;
+    // Warps per work item.  A pair task holds one box's sources, usually a
+    // single tile: one warp per task.  Otherwise, when the work items far
+    // outnumber the resident warps (upper bound: every box non-empty) one warp
+    // per item balances well and saves the group's exchange; few, heavy items
+    // need cooperating warps.  Crossover measured on GB300 between the 2^20-point
+    // (level 6) and 2^22-point (level 7) Plummer spheres.
+    const double items_est = (double)p->box_cap + (double)n / (32.0 * p->tpl);
+    const double resident_warps = (double)num_sms() * 16.0;
+    p->group = (layout == P2P_LAYOUT_PAIRTASK || items_est > 256.0 * resident_warps) ? 1 : 4;
     p->split = nrhs;
     p->rmax = 2.0f * (edge / (float)(1 << level)) * 1.7320508f;
     p->items_cap = (layout == P2P_LAYOUT_PAIRTASK) ? 27 * p->box_cap + (27 * n + 31) / 32 + 1

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "p2p_gb300.h"
 
 namespace p2p {
@@ -110,6 +112,31 @@ void count_launch(int k = 1);
 
 template <typename T>
 inline T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+// Launches with programmatic stream serialisation, so that a kernel's launch
+// overlaps the end of its predecessor in the stream (the kernels wait on the
+// predecessor's completion themselves, see pdl_wait); disabled when the
+// environment sets P2P_NO_PDL=1.
+bool pdl_enabled();
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// 32-bit fill of a device range as a kernel (a memset node would break the
+// chain of programmatic launches)
+int fill32(void* dst, uint32_t value, int64_t count, cudaStream_t s);
 
 inline int num_sms() {
     static int sms = 0;

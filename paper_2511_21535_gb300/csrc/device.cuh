@@ -160,6 +160,14 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64
     }
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor in the stream drains.
+// pdl_wait() blocks until the predecessor grid has completed and its memory
+// is visible (a no-op for an ordinary launch), so every kernel calls it before
+// touching memory; pdl_release() lets the successor be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // One warp copies cnt records of `words` 16-byte words from src to dst
 // (coalesced; streamed stores, the data is read later by the bulk copies).
 // A periodic image code other than 13 moves the positions (word 0: x, y, z)

@@ -213,6 +213,7 @@ template <int K, int G, int R, bool PRECISE>
 __global__ void __launch_bounds__(kLoopThreads, 2)
     k_helmholtz_adjoint(LoopArgs a, const int32_t* __restrict__ perm, float kk, int qw0, int gw0, int64_t n, int r0,
                         int accumulate_x, float2* __restrict__ grad_q, float* __restrict__ grad_x) {
+    pdl_wait();
     HelmAdjOp<K, R, PRECISE> op;
     op.rec = a.rec;
     op.perm = perm;
@@ -241,8 +242,8 @@ static int launch_hadj(const Plan* p, const LoopArgs& a, const int32_t* perm, fl
     }
     const int qw0 = 1 + r0 / 2;
     const int gw0 = 1 + (p->nrhs + 1) / 2 + r0 / 2;
-    kern<<<num_sms() * per_sm, kLoopThreads, smem, s>>>(a, perm, kk, qw0, gw0, p->n, r0, accumulate ? 1 : 0, grad_q,
-                                                        grad_x);
+    P2P_CUDA_TRY(launch_pdl(kern, num_sms() * per_sm, kLoopThreads, smem, s, a, perm, kk, qw0, gw0, p->n, r0, accumulate ? 1 : 0, grad_q,
+                                                        grad_x));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }
@@ -265,7 +266,8 @@ int launch_helmholtz_adjoint_kernel(const Plan* p, const LoopArgs& a, const int3
     while (r0 < p->nrhs) {
         const int left = p->nrhs - r0;
         const int R = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-        P2P_CUDA_TRY(cudaMemsetAsync(&a.hdr->work_ctr, 0, sizeof(uint32_t), s));
+        int st0 = fill32(&a.hdr->work_ctr, 0u, 1, s);
+        if (st0) return st0;
         const bool acc = r0 > 0;
         int st;
         if (p->group >= 2)
@@ -425,6 +427,7 @@ template <int K, int G>
 __global__ void __launch_bounds__(kLoopThreads, 4)
     k_gravity_adjoint(LoopArgs a, const int32_t* __restrict__ perm, float eps2, float* __restrict__ grad_m,
                       float* __restrict__ grad_x) {
+    pdl_wait();
     GravAdjOp<K> op;
     op.rec = a.rec;
     op.perm = perm;
@@ -445,7 +448,7 @@ static int launch_gadj(const Plan* p, const LoopArgs& a, const int32_t* perm, fl
         P2P_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem));
         if (per_sm < 1) per_sm = 1;
     }
-    kern<<<num_sms() * per_sm, kLoopThreads, smem, s>>>(a, perm, eps2, gm, gx);
+    P2P_CUDA_TRY(launch_pdl(kern, num_sms() * per_sm, kLoopThreads, smem, s, a, perm, eps2, gm, gx));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }

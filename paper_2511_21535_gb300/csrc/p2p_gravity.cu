@@ -152,6 +152,7 @@ template <int K, int G, bool COMP>
 __global__ void __launch_bounds__(kLoopThreads, 4)
     k_gravity(LoopArgs a, const int32_t* __restrict__ perm, float eps2, float* __restrict__ phi,
               float* __restrict__ acc) {
+    pdl_wait();
     GravityOp<K, COMP> op;
     op.rec = a.rec;
     op.perm = perm;
@@ -172,7 +173,7 @@ static int launch_gravity(const Plan* p, const LoopArgs& a, const int32_t* perm,
         P2P_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem));
         if (per_sm < 1) per_sm = 1;
     }
-    kern<<<num_sms() * per_sm, kLoopThreads, smem, s>>>(a, perm, eps2, phi, acc);
+    P2P_CUDA_TRY(launch_pdl(kern, num_sms() * per_sm, kLoopThreads, smem, s, a, perm, eps2, phi, acc));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }

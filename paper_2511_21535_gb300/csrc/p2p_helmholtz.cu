@@ -52,7 +52,8 @@ int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* per
     while (r0 < p->nrhs) {
         const int left = p->nrhs - r0;
         const int R = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-        P2P_CUDA_TRY(cudaMemsetAsync(&a.hdr->work_ctr, 0, sizeof(uint32_t), s));
+        int st0 = fill32(&a.hdr->work_ctr, 0u, 1, s);
+        if (st0) return st0;
         int st = precise ? launch_helm_precise(p, a, perm, k, r0, R, u, s)
                  : comp  ? launch_helm_fast(p, a, perm, k, r0, R, u, s)
                          : launch_helm_plain(p, a, perm, k, r0, R, u, s);

@@ -202,6 +202,7 @@ struct HelmOp {
 template <int K, int G, int R, bool COMP, bool PRECISE, int W = 0>
 __global__ void __launch_bounds__(kLoopThreads, 6)
     k_helmholtz(LoopArgs a, const int32_t* __restrict__ perm, float kk, int qw0, int64_t n, int r0, HelmOut out) {
+    pdl_wait();
     HelmOp<K, R, COMP, PRECISE, W> op;
     op.rec = a.rec;
     op.perm = perm;
@@ -225,7 +226,7 @@ int launch_helm(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk,
         if (per_sm < 1) per_sm = 1;
     }
     const int qw0 = 1 + r0 / 2;
-    kern<<<num_sms() * per_sm, kLoopThreads, smem, s>>>(a, perm, kk, qw0, p->n, r0, u);
+    P2P_CUDA_TRY(launch_pdl(kern, num_sms() * per_sm, kLoopThreads, smem, s, a, perm, kk, qw0, p->n, r0, u));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }

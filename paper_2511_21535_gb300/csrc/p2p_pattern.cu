@@ -38,6 +38,8 @@ int pattern_setup(Plan* p, float h, int t) {
 }
 
 __global__ void k_pattern_table(double h, double k, int t, int sy, int sz, int size, float2* __restrict__ table) {
+    pdl_wait();
+    pdl_release();
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= size) return;
     const int D = 4 * t - 1, m = 2 * t - 1;
@@ -123,6 +125,7 @@ template <int K, int G, int R, bool COMPACT>
 __global__ void __launch_bounds__(kLoopThreads, 4)
     k_helmholtz_pattern(LoopArgs a, const int32_t* __restrict__ perm, const float2* __restrict__ table, int size,
                         int bias, size_t table_off, int qw0, int64_t n, int r0, HelmOut out) {
+    pdl_wait();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* tab = reinterpret_cast<float2*>(smem_raw + table_off);
     for (int i = threadIdx.x; i < size; i += blockDim.x) tab[i] = table[i];
@@ -153,8 +156,8 @@ static int launch_pat(const Plan* p, const LoopArgs& a, const int32_t* perm, con
         P2P_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem));
         if (per_sm < 1) per_sm = 1;
     }
-    kern<<<num_sms() * per_sm, kLoopThreads, smem, s>>>(a, perm, table, p->pat_size, p->pat_bias, table_off,
-                                                        1 + r0 / 2, p->n, r0, out);
+    P2P_CUDA_TRY(launch_pdl(kern, num_sms() * per_sm, kLoopThreads, smem, s, a, perm, table, p->pat_size, p->pat_bias, table_off,
+                                                        1 + r0 / 2, p->n, r0, out));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }
@@ -174,15 +177,16 @@ static int pat_r(const Plan* p, const LoopArgs& a, const int32_t* perm, const fl
 
 int launch_helmholtz_pattern(const Plan* p, const LoopArgs& a, const int32_t* perm, float k, float2* table,
                              HelmOut out, cudaStream_t s) {
-    k_pattern_table<<<(p->pat_size + 255) / 256, 256, 0, s>>>((double)p->grid_h, (double)k, p->grid_t, p->pat_sy,
-                                                              p->pat_sz, p->pat_size, table);
+    P2P_CUDA_TRY(launch_pdl(k_pattern_table, (p->pat_size + 255) / 256, 256, 0, s, (double)p->grid_h, (double)k, p->grid_t, p->pat_sy,
+                                                              p->pat_sz, p->pat_size, table));
     P2P_LAUNCH_CHECK();
     const int K = p->tpl >= 2 ? 2 : 1;
     int r0 = 0;
     while (r0 < p->nrhs) {
         const int left = p->nrhs - r0;
         const int R = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-        P2P_CUDA_TRY(cudaMemsetAsync(&a.hdr->work_ctr, 0, sizeof(uint32_t), s));
+        int st0 = fill32(&a.hdr->work_ctr, 0u, 1, s);
+        if (st0) return st0;
         int st;
         if (p->group >= 2)
             st = K == 2 ? pat_r<2, 4>(p, a, perm, table, r0, R, out, s) : pat_r<1, 4>(p, a, perm, table, r0, R, out, s);

@@ -26,6 +26,8 @@ __global__ void __launch_bounds__(256) k_pt_entries(const int32_t* __restrict__ 
                                                    const int32_t* __restrict__ nbr_idx, const Header* hdr,
                                                    int32_t* __restrict__ ent_box, int32_t* __restrict__ blk_len,
                                                    int32_t* __restrict__ slot_len) {
+    pdl_wait();
+    pdl_release();
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -50,6 +52,8 @@ __global__ void __launch_bounds__(256) k_pt_gather(const float4* __restrict__ re
                                                   const int32_t* __restrict__ pt_start, Header* hdr, int64_t cap,
                                                   int64_t part_cap, float4* __restrict__ pt,
                                                   uint32_t* __restrict__ gather) {
+    pdl_wait();
+    pdl_release();
     const int lane = threadIdx.x & 31;
     // an imported, inconsistent neighbour relation can exceed the capacities
     if (hdr->total_src < 0 || (int64_t)hdr->total_src > cap || hdr->part_total < 0 ||
@@ -83,18 +87,18 @@ int pairtask_restructure(Plan* p, void* ws, int words, cudaStream_t s) {
     int32_t* pt_start = at<int32_t>(ws, L.pt_start);
     int32_t* part_start = at<int32_t>(ws, L.part_start);
     const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
-    k_pt_entries<<<wb, 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
-                                    at<int32_t>(ws, L.nbr_idx), hdr, ent_box, pt_start, part_start);
+    P2P_CUDA_TRY(launch_pdl(k_pt_entries, wb, 256, 0, s, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+                                    at<int32_t>(ws, L.nbr_idx), hdr, ent_box, pt_start, part_start));
     P2P_LAUNCH_CHECK();
     int st = scan_exclusive(pt_start, pt_start, ecap, &hdr->n_nbr, &hdr->total_src, at<int32_t>(ws, L.scan_tmp), s);
     if (st) return st;
     st = scan_exclusive(part_start, part_start, ecap, &hdr->n_nbr, &hdr->part_total, at<int32_t>(ws, L.scan_tmp), s);
     if (st) return st;
-    k_pt_gather<<<num_sms() * 8, 256, 0, s>>>(at<float4>(ws, L.src), words, at<int32_t>(ws, L.box_start),
+    P2P_CUDA_TRY(launch_pdl(k_pt_gather, num_sms() * 8, 256, 0, s, at<float4>(ws, L.src), words, at<int32_t>(ws, L.box_start),
                                             at<int32_t>(ws, L.nbr_idx), ent_box,
                                             p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr, p->edge, pt_start,
                                             hdr, p->red_cap, p->part_cap, at<float4>(ws, L.red_src),
-                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr);
+                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }
@@ -107,6 +111,8 @@ __global__ void __launch_bounds__(256) k_pt_reduce_gravity(const int32_t* __rest
                                                           const int32_t* __restrict__ perm, const Header* hdr,
                                                           const float4* __restrict__ part, float* __restrict__ phi,
                                                           float* __restrict__ acc) {
+    pdl_wait();
+    pdl_release();
     if (hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_TIMEOUT)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -143,6 +149,8 @@ __global__ void __launch_bounds__(256) k_pt_reduce_helmholtz(const int32_t* __re
                                                             const int32_t* __restrict__ perm, const Header* hdr,
                                                             const float2* __restrict__ part, int64_t cap, int nrhs,
                                                             int64_t n, float2* __restrict__ u) {
+    pdl_wait();
+    pdl_release();
     if (hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_TIMEOUT)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -173,9 +181,9 @@ __global__ void __launch_bounds__(256) k_pt_reduce_helmholtz(const int32_t* __re
 int pairtask_reduce_gravity(const Plan* p, void* ws, float* phi, float* acc, cudaStream_t s) {
     const Layout& L = p->L;
     const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
-    k_pt_reduce_gravity<<<wb, 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+    P2P_CUDA_TRY(launch_pdl(k_pt_reduce_gravity, wb, 256, 0, s, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
                                            at<int32_t>(ws, L.part_start), at<int32_t>(ws, L.perm),
-                                           at<Header>(ws, L.header), at<float4>(ws, L.part), phi, acc);
+                                           at<Header>(ws, L.header), at<float4>(ws, L.part), phi, acc));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }
@@ -183,10 +191,10 @@ int pairtask_reduce_gravity(const Plan* p, void* ws, float* phi, float* acc, cud
 int pairtask_reduce_helmholtz(const Plan* p, void* ws, float2* u, cudaStream_t s) {
     const Layout& L = p->L;
     const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
-    k_pt_reduce_helmholtz<<<wb, 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+    P2P_CUDA_TRY(launch_pdl(k_pt_reduce_helmholtz, wb, 256, 0, s, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
                                              at<int32_t>(ws, L.part_start), at<int32_t>(ws, L.perm),
                                              at<Header>(ws, L.header), at<float2>(ws, L.part), p->part_cap, p->nrhs,
-                                             p->n, u);
+                                             p->n, u));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }

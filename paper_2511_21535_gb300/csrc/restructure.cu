@@ -24,6 +24,8 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 
 __global__ void k_records_gravity(const float* __restrict__ pos, const float* __restrict__ mass,
                                   const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec) {
+    pdl_wait();
+    pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm[s];
@@ -39,7 +41,11 @@ __device__ __forceinline__ float2 rhs_value(const float2* __restrict__ q, const 
     return make_float2(v.x, -v.y);
 }
 
-__global__ void k_clear_flag(Header* hdr, uint32_t bit) { atomicAnd(&hdr->flags, ~bit); }
+__global__ void k_clear_flag(Header* hdr, uint32_t bit) {
+    pdl_wait();
+    pdl_release();
+    atomicAnd(&hdr->flags, ~bit);
+}
 
 // Pattern mode: lattice code of a point, ix*1 + iy*sy + iz*sz with
 // ix = rint((x - lo)/h - 1/2); the point must be within 1 % of h of the
@@ -75,6 +81,8 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
                                     const float2* __restrict__ q2, int split, const int32_t* __restrict__ perm,
                                     int64_t n, int nrhs, int words, LatticeArgs lat, Header* hdr,
                                     float4* __restrict__ rec) {
+    pdl_wait();
+    pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm[s];
@@ -102,6 +110,8 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
 __global__ void k_records_helm_adjoint(const float* __restrict__ pos, const float2* __restrict__ q,
                                        const float2* __restrict__ gbar, const int32_t* __restrict__ perm, int64_t n,
                                        int nrhs, int words, float4* __restrict__ rec) {
+    pdl_wait();
+    pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm[s];
@@ -122,6 +132,8 @@ __global__ void k_records_helm_adjoint(const float* __restrict__ pos, const floa
 __global__ void k_records_grav_adjoint(const float* __restrict__ pos, const float* __restrict__ mass,
                                        const float* __restrict__ gphi, const float* __restrict__ gacc,
                                        const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec) {
+    pdl_wait();
+    pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm[s];
@@ -137,6 +149,8 @@ __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ b
                                                   const int32_t* __restrict__ nbr_start,
                                                   const int32_t* __restrict__ nbr_idx, Header* hdr,
                                                   int32_t* __restrict__ S, int32_t* __restrict__ self_off) {
+    pdl_wait();
+    pdl_release();
     __shared__ unsigned long long pairs_s;
     if (threadIdx.x == 0) pairs_s = 0ull;
     __syncthreads();
@@ -199,6 +213,8 @@ __device__ __forceinline__ void unit_shape(const Units& U, int64_t u, int32_t& o
 
 // Cost-class histogram of the work items (items of up to tt targets).
 __global__ void __launch_bounds__(256) k_items_count(Units U, Header* hdr, int tt) {
+    pdl_wait();
+    pdl_release();
     __shared__ int32_t cls[kCostClasses];
     __shared__ int32_t items_s;
     for (int c = threadIdx.x; c < kCostClasses; c += blockDim.x) cls[c] = 0;
@@ -221,6 +237,8 @@ __global__ void __launch_bounds__(256) k_items_count(Units U, Header* hdr, int t
 // Place each item in its cost class, heaviest class first.  Blocks reserve a
 // range per class with one atomic, then fill it through shared counters.
 __global__ void __launch_bounds__(256) k_items_fill(Units U, Header* hdr, int tt, int2* __restrict__ items) {
+    pdl_wait();
+    pdl_release();
     __shared__ int32_t cls_base[kCostClasses];
     __shared__ int32_t local_cnt[kCostClasses];
     __shared__ int32_t local_cur[kCostClasses];
@@ -267,6 +285,8 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
                                                    const int32_t* __restrict__ red_start, Header* hdr,
                                                    int64_t red_cap, float4* __restrict__ red,
                                                    uint32_t* __restrict__ gather) {
+    pdl_wait();
+    pdl_release();
     const int lane = threadIdx.x & 31;
     // an imported, inconsistent neighbour relation can exceed the stream capacity
     if (hdr->total_src < 0 || (int64_t)hdr->total_src > red_cap) {
@@ -301,23 +321,24 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
     float4* rec = at<float4>(ws, L.src);
     const bool red = p->layout == P2P_LAYOUT_REDUNDANT;
     int32_t* S = at<int32_t>(ws, L.box_S);
-    P2P_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(hdr) + kRestrSectionOffset, 0,
-                                 kOpSectionOffset - kRestrSectionOffset, s));
+    int st0 = fill32(reinterpret_cast<char*>(hdr) + kRestrSectionOffset, 0u,
+                     (kOpSectionOffset - kRestrSectionOffset) / 4, s);
+    if (st0) return st0;
     const unsigned sbl = (unsigned)std::min<int64_t>(blocks_for(bc * 32, 256), (int64_t)num_sms() * 16);
-    k_box_stats<<<sbl, 256, 0, s>>>(at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
-                                    at<int32_t>(ws, L.nbr_idx), hdr, S, red ? at<int32_t>(ws, L.red_self) : nullptr);
+    P2P_CUDA_TRY(launch_pdl(k_box_stats, sbl, 256, 0, s, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+                                    at<int32_t>(ws, L.nbr_idx), hdr, S, red ? at<int32_t>(ws, L.red_self) : nullptr));
     P2P_LAUNCH_CHECK();
     if (red) {
         int32_t* red_start = at<int32_t>(ws, L.red_start);
         int st = scan_exclusive(S, red_start, bc, &hdr->n_boxes, &hdr->total_src, at<int32_t>(ws, L.scan_tmp), s);
         if (st) return st;
         const int sms = num_sms();
-        k_red_gather<<<sms * 8, 256, 0, s>>>(rec, words, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+        P2P_CUDA_TRY(launch_pdl(k_red_gather, sms * 8, 256, 0, s, rec, words, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
                                             at<int32_t>(ws, L.nbr_idx),
                                             p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr, p->edge, red_start,
                                             hdr, p->red_cap,
                                             at<float4>(ws, L.red_src),
-                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr);
+                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr));
         P2P_LAUNCH_CHECK();
     } else if (p->layout == P2P_LAYOUT_PAIRTASK) {
         return pairtask_restructure(p, ws, words, s);
@@ -331,7 +352,7 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
     const int32_t* perm = at<int32_t>(ws, L.perm);
     float4* rec = at<float4>(ws, L.src);
     if (p->kind == P2P_GRAVITY) {
-        k_records_gravity<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float*>(strength), perm, n, rec);
+        P2P_CUDA_TRY(launch_pdl(k_records_gravity, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float*>(strength), perm, n, rec));
     } else {
         const int split = strength2 ? p->split : p->nrhs;
         LatticeArgs lat{};
@@ -345,13 +366,13 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
             lat.scale = p->scale;
             lat.cmax = (1 << p->level) - 1;
             // the lattice flag belongs to this restructuring
-            k_clear_flag<<<1, 1, 0, s>>>(at<Header>(ws, L.header), P2P_FLAG_LATTICE);
+            P2P_CUDA_TRY(launch_pdl(k_clear_flag, 1, 1, 0, s, at<Header>(ws, L.header), P2P_FLAG_LATTICE));
             P2P_LAUNCH_CHECK();
         }
-        k_records_helmholtz<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float2*>(strength),
+        P2P_CUDA_TRY(launch_pdl(k_records_helmholtz, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float2*>(strength),
                                                               static_cast<const float2*>(strength2), split, perm, n,
                                                               p->nrhs, p->rec_words, lat, at<Header>(ws, L.header),
-                                                              rec);
+                                                              rec));
     }
     P2P_LAUNCH_CHECK();
     int st = restructure_tail(p, ws, p->rec_words, s);
@@ -370,15 +391,15 @@ int restructure_adjoint(Plan* p, const float* pos, const void* a, const void* b,
     if (p->kind == P2P_GRAVITY) {
         w = kGravityAdjointWords;
         if (w > p->rec_alloc_words) return P2P_ERR_UNSUPPORTED;
-        k_records_grav_adjoint<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float*>(a),
+        P2P_CUDA_TRY(launch_pdl(k_records_grav_adjoint, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float*>(a),
                                                                  static_cast<const float*>(b),
-                                                                 static_cast<const float*>(c), perm, n, rec);
+                                                                 static_cast<const float*>(c), perm, n, rec));
     } else {
         w = helmholtz_adjoint_words(p->nrhs);
         if (w > p->rec_alloc_words) return P2P_ERR_UNSUPPORTED;
-        k_records_helm_adjoint<<<blocks_for(n, 256), 256, 0, s>>>(pos, static_cast<const float2*>(a),
+        P2P_CUDA_TRY(launch_pdl(k_records_helm_adjoint, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float2*>(a),
                                                                  static_cast<const float2*>(b), perm, n, p->nrhs, w,
-                                                                 rec);
+                                                                 rec));
     }
     P2P_LAUNCH_CHECK();
     p->src_ready = 0;   // the forward records are overwritten
@@ -391,17 +412,17 @@ int build_items(Plan* p, void* ws, int tt, cudaStream_t s) {
     Header* hdr = at<Header>(ws, L.header);
     const int64_t bc = p->box_cap;
     const int32_t* S = at<int32_t>(ws, L.box_S);
-    P2P_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(hdr) + kOpSectionOffset, 0,
-                                 sizeof(Header) - kOpSectionOffset, s));
+    int st0 = fill32(reinterpret_cast<char*>(hdr) + kOpSectionOffset, 0u, (sizeof(Header) - kOpSectionOffset) / 4, s);
+    if (st0) return st0;
     Units U{at<int32_t>(ws, L.box_start), S, nullptr, nullptr, bc};
     if (p->layout == P2P_LAYOUT_PAIRTASK) {
         U.ent_box = at<int32_t>(ws, L.ent_box);
         U.nbr_idx = at<int32_t>(ws, L.nbr_idx);
         U.cap = 27 * bc;
     }
-    k_items_count<<<blocks_for(U.cap, 256), 256, 0, s>>>(U, hdr, tt);
+    P2P_CUDA_TRY(launch_pdl(k_items_count, blocks_for(U.cap, 256), 256, 0, s, U, hdr, tt));
     P2P_LAUNCH_CHECK();
-    k_items_fill<<<blocks_for(U.cap, 256), 256, 0, s>>>(U, hdr, tt, at<int2>(ws, L.items));
+    P2P_CUDA_TRY(launch_pdl(k_items_fill, blocks_for(U.cap, 256), 256, 0, s, U, hdr, tt, at<int2>(ws, L.items)));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }

@@ -4,6 +4,8 @@
 // Three phases (block reduce -> scan of block sums -> block scan + offset),
 // no inter-block waiting.  Lengths may be given on the device so that the
 // whole tree build runs without a host round trip.
+#include <algorithm>
+
 #include "common.cuh"
 #include "device.cuh"
 
@@ -23,6 +25,8 @@ __device__ __forceinline__ int64_t eff_len(int64_t n_cap, const int32_t* d_len) 
 // one block scans everything, chunk by chunk, carrying the running total
 __global__ void __launch_bounds__(kScanThreads) k_scan_single(const int32_t* in, int32_t* out, int64_t n_cap,
                                                              const int32_t* d_len, int32_t* d_total) {
+    pdl_wait();
+    pdl_release();
     const int64_t len = eff_len(n_cap, d_len);
     int32_t carry = 0;
     for (int64_t base = 0; base < n_cap; base += kScanChunk) {
@@ -52,6 +56,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(const int32_t* in,
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* in, int64_t n_cap,
                                                              const int32_t* d_len, int32_t* block_sums) {
+    pdl_wait();
+    pdl_release();
     const int64_t len = eff_len(n_cap, d_len);
     const int64_t base = (int64_t)blockIdx.x * kScanChunk;
     int32_t s = 0;
@@ -70,6 +76,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* in,
 __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int32_t* in, int32_t* out, int64_t n_cap,
                                                             const int32_t* d_len, const int32_t* block_off,
                                                             int32_t* d_total, int nblocks) {
+    pdl_wait();
+    pdl_release();
     const int64_t len = eff_len(n_cap, d_len);
     const int64_t base = (int64_t)blockIdx.x * kScanChunk;
     int32_t v[kScanItems];
@@ -95,6 +103,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int32_t* in, 
     }
 }
 
+__global__ void __launch_bounds__(256) k_fill32(uint32_t* __restrict__ dst, uint32_t value, int64_t count) {
+    pdl_wait();
+    pdl_release();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) dst[i] = value;
+}
+
+int fill32(void* dst, uint32_t value, int64_t count, cudaStream_t s) {
+    if (count <= 0) return P2P_OK;
+    const int64_t blocks = std::min<int64_t>((count + 255) / 256, (int64_t)num_sms() * 8);
+    P2P_CUDA_TRY(launch_pdl(k_fill32, (unsigned)blocks, 256, 0, s, static_cast<uint32_t*>(dst), value, count));
+    P2P_LAUNCH_CHECK();
+    return P2P_OK;
+}
+
 size_t scan_scratch_bytes(int64_t n_cap) {
     int64_t nb = (n_cap + kScanChunk - 1) / kScanChunk;
     return (size_t)(nb + 1) * 2 * sizeof(int32_t) + 256;
@@ -104,18 +127,18 @@ int scan_exclusive(const int32_t* in, int32_t* out, int64_t n_cap, const int32_t
                    int32_t* d_total, int32_t* scratch, cudaStream_t s) {
     if (n_cap <= 0) return P2P_ERR_INVALID_ARG;
     if (n_cap <= kSingleBlockMax) {
-        k_scan_single<<<1, kScanThreads, 0, s>>>(in, out, n_cap, d_len, d_total);
+        P2P_CUDA_TRY(launch_pdl(k_scan_single, 1, kScanThreads, 0, s, in, out, n_cap, d_len, d_total));
         P2P_LAUNCH_CHECK();
         return P2P_OK;
     }
     int nblocks = (int)((n_cap + kScanChunk - 1) / kScanChunk);
     int32_t* sums = scratch;
     int32_t* offs = scratch + (nblocks + 1);
-    k_scan_reduce<<<nblocks, kScanThreads, 0, s>>>(in, n_cap, d_len, sums);
+    P2P_CUDA_TRY(launch_pdl(k_scan_reduce, nblocks, kScanThreads, 0, s, in, n_cap, d_len, sums));
     P2P_LAUNCH_CHECK();
-    k_scan_single<<<1, kScanThreads, 0, s>>>(sums, offs, nblocks, nullptr, nullptr);
+    P2P_CUDA_TRY(launch_pdl(k_scan_single, 1, kScanThreads, 0, s, sums, offs, nblocks, nullptr, nullptr));
     P2P_LAUNCH_CHECK();
-    k_scan_final<<<nblocks, kScanThreads, 0, s>>>(in, out, n_cap, d_len, offs, d_total, nblocks);
+    P2P_CUDA_TRY(launch_pdl(k_scan_final, nblocks, kScanThreads, 0, s, in, out, n_cap, d_len, offs, d_total, nblocks));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }

@@ -24,6 +24,8 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // ---------------------------------------------------------------------------
 __global__ void k_keys(const float* __restrict__ pos, int64_t n, float lo0, float lo1, float lo2,
                        float scale, int level, uint32_t* __restrict__ keys, Header* hdr) {
+    pdl_wait();
+    pdl_release();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float side = (float)(1 << level);
@@ -51,6 +53,8 @@ __global__ void k_keys(const float* __restrict__ pos, int64_t n, float lo0, floa
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n,
                                                             int shift, uint32_t mask, int32_t* hist, int tiles) {
+    pdl_wait();
+    pdl_release();
     __shared__ int32_t cnt[256];
     const int radix = (int)mask + 1;
     for (int d = threadIdx.x; d < radix; d += kSortThreads) cnt[d] = 0;
@@ -75,6 +79,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
                                                                const int32_t* __restrict__ hist, int tiles,
                                                                uint32_t* __restrict__ kout,
                                                                int32_t* __restrict__ vout) {
+    pdl_wait();
+    pdl_release();
     constexpr int W = kSortThreads / 32;
     __shared__ int32_t base[256];
     __shared__ int32_t wcnt[W][256];
@@ -127,6 +133,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
 // 3. box CSR
 // ---------------------------------------------------------------------------
 __global__ void k_box_flags(const uint32_t* __restrict__ skey, int64_t n, int32_t* __restrict__ flag) {
+    pdl_wait();
+    pdl_release();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     flag[i] = (i == 0 || skey[i] != skey[i - 1]) ? 1 : 0;
@@ -135,6 +143,8 @@ __global__ void k_box_flags(const uint32_t* __restrict__ skey, int64_t n, int32_
 // flag_scan[i] = number of boxes starting before i; n_boxes already in hdr
 __global__ void k_box_emit(const uint32_t* __restrict__ skey, int64_t n, const int32_t* __restrict__ flag_scan,
                            uint32_t* __restrict__ box_key, int32_t* __restrict__ box_start) {
+    pdl_wait();
+    pdl_release();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (i == 0 || skey[i] != skey[i - 1]) {
@@ -149,6 +159,8 @@ __global__ void k_box_emit(const uint32_t* __restrict__ skey, int64_t n, const i
 // 4. neighbour lists
 // ---------------------------------------------------------------------------
 __global__ void k_table_fill(const uint32_t* __restrict__ box_key, const Header* hdr, int32_t* __restrict__ table) {
+    pdl_wait();
+    pdl_release();
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= hdr->n_boxes) return;
     table[box_key[b]] = (int32_t)b;
@@ -217,6 +229,8 @@ __global__ void __launch_bounds__(256) k_neighbours(const uint32_t* __restrict__
                                                    int32_t* __restrict__ cnt, const int32_t* __restrict__ nbr_start,
                                                    int32_t* __restrict__ nbr_idx, int32_t* __restrict__ nbr_img,
                                                    int periodic) {
+    pdl_wait();
+    pdl_release();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t nb = hdr->n_boxes;
@@ -234,7 +248,8 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     Header* hdr = at<Header>(ws, L.header);
     const int64_t n = p->n;
     // clear the tree and restructuring sections of the header (counts and flags)
-    P2P_CUDA_TRY(cudaMemsetAsync(hdr, 0, kOpSectionOffset, s));
+    int st0 = fill32(hdr, 0u, kOpSectionOffset / 4, s);
+    if (st0) return st0;
 
     uint32_t* ka = at<uint32_t>(ws, L.keys_a);
     uint32_t* kb = at<uint32_t>(ws, L.keys_b);
@@ -244,7 +259,7 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     int32_t* hist = at<int32_t>(ws, L.hist);
     int32_t* scratch = at<int32_t>(ws, L.scan_tmp);
 
-    k_keys<<<blocks_for(n, 256), 256, 0, s>>>(pos, n, p->lo[0], p->lo[1], p->lo[2], p->scale, p->level, ka, hdr);
+    P2P_CUDA_TRY(launch_pdl(k_keys, blocks_for(n, 256), 256, 0, s, pos, n, p->lo[0], p->lo[1], p->lo[2], p->scale, p->level, ka, hdr));
     P2P_LAUNCH_CHECK();
 
     // radix passes over 3*level key bits, equal digit widths <= 8 bits
@@ -262,11 +277,11 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
         int32_t* vout = (remaining % 2 == 0) ? perm : va;
         if (kout == kin) kout = (kout == skey) ? kb : skey;  // never in place
         const int shift = ps * dbits;
-        k_radix_hist<<<tiles, kSortThreads, 0, s>>>(kin, n, shift, mask, hist, tiles);
+        P2P_CUDA_TRY(launch_pdl(k_radix_hist, tiles, kSortThreads, 0, s, kin, n, shift, mask, hist, tiles));
         P2P_LAUNCH_CHECK();
         int st = scan_exclusive(hist, hist, (int64_t)(mask + 1) * tiles, nullptr, nullptr, scratch, s);
         if (st) return st;
-        k_radix_scatter<<<tiles, kSortThreads, 0, s>>>(kin, vin, n, shift, mask, hist, tiles, kout, vout);
+        P2P_CUDA_TRY(launch_pdl(k_radix_scatter, tiles, kSortThreads, 0, s, kin, vin, n, shift, mask, hist, tiles, kout, vout));
         P2P_LAUNCH_CHECK();
         kin = kout;
         vin = vout;
@@ -280,11 +295,11 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     int32_t* flag = at<int32_t>(ws, L.flags);
     uint32_t* box_key = at<uint32_t>(ws, L.box_key);
     int32_t* box_start = at<int32_t>(ws, L.box_start);
-    k_box_flags<<<blocks_for(n, 256), 256, 0, s>>>(skey, n, flag);
+    P2P_CUDA_TRY(launch_pdl(k_box_flags, blocks_for(n, 256), 256, 0, s, skey, n, flag));
     P2P_LAUNCH_CHECK();
     int st = scan_exclusive(flag, flag, n, nullptr, &hdr->n_boxes, scratch, s);
     if (st) return st;
-    k_box_emit<<<blocks_for(n, 256), 256, 0, s>>>(skey, n, flag, box_key, box_start);
+    P2P_CUDA_TRY(launch_pdl(k_box_emit, blocks_for(n, 256), 256, 0, s, skey, n, flag, box_key, box_start));
     P2P_LAUNCH_CHECK();
 
     // neighbour lists
@@ -292,8 +307,9 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     int32_t* table = nullptr;
     if (p->use_table) {
         table = at<int32_t>(ws, L.table);
-        P2P_CUDA_TRY(cudaMemsetAsync(table, 0xff, ((size_t)1 << (3 * p->level)) * sizeof(int32_t), s));
-        k_table_fill<<<blocks_for(bc, 256), 256, 0, s>>>(box_key, hdr, table);
+        st = fill32(table, 0xffffffffu, (int64_t)1 << (3 * p->level), s);
+        if (st) return st;
+        P2P_CUDA_TRY(launch_pdl(k_table_fill, blocks_for(bc, 256), 256, 0, s, box_key, hdr, table));
         P2P_LAUNCH_CHECK();
     }
     int32_t* ncnt = at<int32_t>(ws, L.nbr_cnt);
@@ -301,11 +317,11 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     int32_t* nidx = at<int32_t>(ws, L.nbr_idx);
     const unsigned nbl = (unsigned)std::min<int64_t>(blocks_for(bc * 32, 256), (int64_t)num_sms() * 16);
     int32_t* nimg = p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr;
-    k_neighbours<<<nbl, 256, 0, s>>>(box_key, hdr, p->level, table, ncnt, nullptr, nullptr, nullptr, p->periodic);
+    P2P_CUDA_TRY(launch_pdl(k_neighbours, nbl, 256, 0, s, box_key, hdr, p->level, table, ncnt, nullptr, nullptr, nullptr, p->periodic));
     P2P_LAUNCH_CHECK();
     st = scan_exclusive(ncnt, nstart, bc, &hdr->n_boxes, &hdr->n_nbr, scratch, s);
     if (st) return st;
-    k_neighbours<<<nbl, 256, 0, s>>>(box_key, hdr, p->level, table, ncnt, nstart, nidx, nimg, p->periodic);
+    P2P_CUDA_TRY(launch_pdl(k_neighbours, nbl, 256, 0, s, box_key, hdr, p->level, table, ncnt, nstart, nidx, nimg, p->periodic));
     P2P_LAUNCH_CHECK();
     p->tree_ready = 1;
     p->src_ready = 0;
@@ -316,6 +332,8 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
 // import of a caller-built structure
 // ---------------------------------------------------------------------------
 __global__ void k_set_counts(Header* hdr, int32_t n_boxes, int32_t n_nbr) {
+    pdl_wait();
+    pdl_release();
     hdr->n_boxes = n_boxes;
     hdr->n_nbr = n_nbr;
 }
@@ -334,7 +352,7 @@ int tree_import(Plan* p, const int32_t* perm, const int32_t* box_start, int32_t 
                                  cudaMemcpyDeviceToDevice, s));
     P2P_CUDA_TRY(cudaMemcpyAsync(at<int32_t>(ws, L.nbr_idx), nbr_idx, (size_t)n_nbr * sizeof(int32_t),
                                  cudaMemcpyDeviceToDevice, s));
-    k_set_counts<<<1, 1, 0, s>>>(hdr, n_boxes, n_nbr);
+    P2P_CUDA_TRY(launch_pdl(k_set_counts, 1, 1, 0, s, hdr, n_boxes, n_nbr));
     P2P_LAUNCH_CHECK();
     p->tree_ready = 1;
     p->src_ready = 0;
