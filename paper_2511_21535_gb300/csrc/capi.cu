@@ -48,11 +48,10 @@ void compute_layout(Plan* p) {
     const bool pt = p->layout == P2P_LAYOUT_PAIRTASK;
     if (pt && 27 * bc > scan_max) scan_max = 27 * bc;   // scans over neighbour entries
     L.scan_tmp = take(scan_scratch_bytes(scan_max));
-    L.flags = take((n + 1) * 4);
+    L.lookback = take((size_t)lb_regions(n, bc).words * 8);
     L.box_key = take(bc * 4);
     L.box_start = take((bc + 1) * 4);
     L.table = p->use_table ? take(((size_t)1 << (3 * p->level)) * 4) : 0;
-    L.nbr_cnt = take(bc * 4);
     L.nbr_start = take((bc + 1) * 4);
     L.nbr_idx = take((size_t)27 * bc * 4);
     L.nbr_img = p->periodic ? take((size_t)27 * bc * 4) : 0;

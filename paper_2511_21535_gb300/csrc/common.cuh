@@ -45,8 +45,8 @@ static_assert(offsetof(Header, n_items) == kOpSectionOffset, "header layout");
 // plan
 // ---------------------------------------------------------------------------
 struct Layout {                        // byte offsets inside the workspace
-    size_t header, keys_a, keys_b, vals_a, perm, sorted_key, hist, scan_tmp, flags,
-        box_key, box_start, table, nbr_cnt, nbr_start, nbr_idx, src, box_S, red_start,
+    size_t header, keys_a, keys_b, vals_a, perm, sorted_key, hist, scan_tmp, lookback,
+        box_key, box_start, table, nbr_start, nbr_idx, src, box_S, red_start,
         red_self, red_src, gather, items, pattern, nbr_img,
         ent_box, pt_start, part_start, part,   // pair tasks (red_src/gather hold the task stream)
         total;
@@ -132,6 +132,27 @@ inline cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, si
     cfg.attrs = attr;
     cfg.numAttrs = pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// Chained-scan scratch (lookback.cuh), three regions of 1 + tiles words:
+// the box CSR (tiles of kCsrTileElems sorted particles), the neighbour CSR
+// and the box statistics (tiles of kBoxTile boxes).  The key kernel clears
+// the first two, the record kernels of the restructuring the third.
+constexpr int kCsrTileElems = 2048;
+constexpr int kBoxTile = 32;
+struct LbRegions {
+    int64_t csr, nbr, stats, tree_words, words;   // offsets and sizes in 8-byte words
+};
+inline LbRegions lb_regions(int64_t n, int64_t box_cap) {
+    LbRegions r;
+    const int64_t a = 1 + (n + kCsrTileElems - 1) / kCsrTileElems;
+    const int64_t b = 1 + (box_cap + kBoxTile - 1) / kBoxTile;
+    r.csr = 0;
+    r.nbr = a;
+    r.stats = a + b;
+    r.tree_words = a + b;
+    r.words = a + 2 * b;
+    return r;
 }
 
 // 32-bit fill of a device range as a kernel (a memset node would break the

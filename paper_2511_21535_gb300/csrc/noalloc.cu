@@ -51,11 +51,10 @@ void noalloc_layout(Plan* p) {
     int64_t scan_max = (int64_t)256 * p->sort_tiles;
     if (n > scan_max) scan_max = n;
     L.scan_tmp = take(scan_scratch_bytes(scan_max));
-    L.flags = take((n + 1) * 4);
+    L.lookback = take((size_t)lb_regions(n, bc).words * 8);
     L.box_key = take(bc * 4);
     L.box_start = take((bc + 1) * 4);
     L.table = take(((size_t)1 << (3 * p->level)) * 4);
-    L.nbr_cnt = take(bc * 4);
     L.nbr_start = take((bc + 1) * 4);
     L.nbr_idx = take((size_t)27 * bc * 4);
     L.src = take((size_t)n * 16);

@@ -17,16 +17,19 @@
 
 #include "common.cuh"
 #include "device.cuh"
+#include "lookback.cuh"
 
 namespace p2p {
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 __global__ void k_records_gravity(const float* __restrict__ pos, const float* __restrict__ mass,
-                                  const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec) {
+                                  const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec,
+                                  unsigned long long* __restrict__ lb, int64_t lb_words) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
     if (s >= n) return;
     const int64_t i = perm[s];
     rec[s] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass[i]);
@@ -80,10 +83,12 @@ __device__ __forceinline__ bool lattice_code(const float* x, const LatticeArgs& 
 __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2* __restrict__ q,
                                     const float2* __restrict__ q2, int split, const int32_t* __restrict__ perm,
                                     int64_t n, int nrhs, int words, LatticeArgs lat, Header* hdr,
-                                    float4* __restrict__ rec) {
+                                    float4* __restrict__ rec,
+                                  unsigned long long* __restrict__ lb, int64_t lb_words) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
     if (s >= n) return;
     const int64_t i = perm[s];
     float4* r = rec + s * words;
@@ -109,10 +114,12 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
 
 __global__ void k_records_helm_adjoint(const float* __restrict__ pos, const float2* __restrict__ q,
                                        const float2* __restrict__ gbar, const int32_t* __restrict__ perm, int64_t n,
-                                       int nrhs, int words, float4* __restrict__ rec) {
+                                       int nrhs, int words, float4* __restrict__ rec,
+                                  unsigned long long* __restrict__ lb, int64_t lb_words) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
     if (s >= n) return;
     const int64_t i = perm[s];
     float4* r = rec + s * words;
@@ -131,40 +138,60 @@ __global__ void k_records_helm_adjoint(const float* __restrict__ pos, const floa
 
 __global__ void k_records_grav_adjoint(const float* __restrict__ pos, const float* __restrict__ mass,
                                        const float* __restrict__ gphi, const float* __restrict__ gacc,
-                                       const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec) {
+                                       const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec,
+                                  unsigned long long* __restrict__ lb, int64_t lb_words) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
     if (s >= n) return;
     const int64_t i = perm[s];
     rec[2 * s] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass[i]);
     rec[2 * s + 1] = make_float4(gphi[i], gacc[3 * i], gacc[3 * i + 1], gacc[3 * i + 2]);
 }
 
-// Per-box statistics, one warp per box (lane e reads neighbour e):
-// S[b] = sum of the occupancies of b's neighbours; self[b] = offset of b's own
-// particles in its stream (neighbours are ascending, so it is the sum over
-// neighbours with a smaller index); the pair count sum_b n_b S_b.
+// Per-box statistics, a tile of kBoxTile boxes per block, four per warp
+// (lane e reads neighbour e): S[b] = sum of the occupancies of b's
+// neighbours; self[b] = offset of b's own particles in its stream (neighbours
+// are ascending, so it is the sum over neighbours with a smaller index); the
+// pair count sum_b n_b S_b.  For the redundant layout the stream bounds
+// red_start = exclusive scan of S are chained across tiles in the same pass
+// (lookback.cuh), and the tile holding the last box closes them.
+constexpr int kStatsPerWarp = kBoxTile / 8;
+
 __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ box_start,
                                                   const int32_t* __restrict__ nbr_start,
                                                   const int32_t* __restrict__ nbr_idx, Header* hdr,
-                                                  int32_t* __restrict__ S, int32_t* __restrict__ self_off) {
+                                                  int32_t* __restrict__ S, int32_t* __restrict__ self_off,
+                                                  int32_t* __restrict__ red_start, unsigned long long* lb) {
     pdl_wait();
     pdl_release();
+    __shared__ int tile_s;
+    __shared__ int32_t s_s[kBoxTile];
+    __shared__ int32_t pre_s[kBoxTile + 1];
     __shared__ unsigned long long pairs_s;
-    if (threadIdx.x == 0) pairs_s = 0ull;
+    if (threadIdx.x == 0) {
+        tile_s = lb_ticket(lb);
+        pairs_s = 0ull;
+    }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int tile = tile_s;
     const int32_t nb = hdr->n_boxes;
+    const int64_t b0 = (int64_t)tile * kBoxTile;
+    if (b0 >= nb) return;   // past the last box (whole block): no later tile waits on it
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long pairs = 0ull;
-    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
-        const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+#pragma unroll
+    for (int q = 0; q < kStatsPerWarp; ++q) {
+        const int64_t b = b0 + warp * kStatsPerWarp + q;
         int32_t cnt = 0, lower = 0;
-        if (lane < ne) {
-            const int32_t c = nbr_idx[e0 + lane];
-            cnt = box_start[c + 1] - box_start[c];
-            lower = c < b ? cnt : 0;
+        if (b < nb) {
+            const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+            if (lane < ne) {
+                const int32_t c = nbr_idx[e0 + lane];
+                cnt = box_start[c + 1] - box_start[c];
+                lower = c < b ? cnt : 0;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -172,14 +199,32 @@ __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ b
             lower += __shfl_xor_sync(FULL, lower, o);
         }
         if (lane == 0) {
-            S[b] = cnt;
-            if (self_off) self_off[b] = lower;
-            pairs += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)cnt;
+            s_s[warp * kStatsPerWarp + q] = cnt;
+            if (b < nb) {
+                S[b] = cnt;
+                if (self_off) self_off[b] = lower;
+                pairs += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)cnt;
+            }
         }
     }
     if (lane == 0 && pairs) atomicAdd(&pairs_s, pairs);
     __syncthreads();
     if (threadIdx.x == 0 && pairs_s) atomicAdd(&hdr->pairs_nS, pairs_s);
+    if (!red_start) return;
+    if (warp == 0) {
+        const int32_t v = s_s[lane];
+        const int32_t inc = warp_incl_scan(v);
+        const int32_t agg = __shfl_sync(FULL, inc, 31);
+        const int32_t ex = lb_exclusive(lb, tile, agg, hdr);
+        pre_s[lane] = ex + inc - v;
+        if (lane == 31) pre_s[kBoxTile] = ex + inc;
+    }
+    __syncthreads();
+    if (threadIdx.x < kBoxTile && b0 + threadIdx.x < nb) red_start[b0 + threadIdx.x] = pre_s[threadIdx.x];
+    if (threadIdx.x == 0 && nb - 1 >= b0 && nb - 1 < b0 + kBoxTile) {
+        red_start[nb] = pre_s[kBoxTile];
+        hdr->total_src = pre_s[kBoxTile];
+    }
 }
 
 __device__ __forceinline__ int cost_class(int32_t nt, int32_t sb) {
@@ -324,14 +369,13 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
     int st0 = fill32(reinterpret_cast<char*>(hdr) + kRestrSectionOffset, 0u,
                      (kOpSectionOffset - kRestrSectionOffset) / 4, s);
     if (st0) return st0;
-    const unsigned sbl = (unsigned)std::min<int64_t>(blocks_for(bc * 32, 256), (int64_t)num_sms() * 16);
-    P2P_CUDA_TRY(launch_pdl(k_box_stats, sbl, 256, 0, s, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
-                                    at<int32_t>(ws, L.nbr_idx), hdr, S, red ? at<int32_t>(ws, L.red_self) : nullptr));
+    int32_t* red_start = red ? at<int32_t>(ws, L.red_start) : nullptr;
+    unsigned long long* lb = at<unsigned long long>(ws, L.lookback) + lb_regions(p->n, bc).stats;
+    P2P_CUDA_TRY(launch_pdl(k_box_stats, blocks_for(bc, kBoxTile), 256, 0, s, at<int32_t>(ws, L.box_start),
+                            at<int32_t>(ws, L.nbr_start), at<int32_t>(ws, L.nbr_idx), hdr, S,
+                            red ? at<int32_t>(ws, L.red_self) : nullptr, red_start, lb));
     P2P_LAUNCH_CHECK();
     if (red) {
-        int32_t* red_start = at<int32_t>(ws, L.red_start);
-        int st = scan_exclusive(S, red_start, bc, &hdr->n_boxes, &hdr->total_src, at<int32_t>(ws, L.scan_tmp), s);
-        if (st) return st;
         const int sms = num_sms();
         P2P_CUDA_TRY(launch_pdl(k_red_gather, sms * 8, 256, 0, s, rec, words, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
                                             at<int32_t>(ws, L.nbr_idx),
@@ -351,8 +395,12 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
     const int64_t n = p->n;
     const int32_t* perm = at<int32_t>(ws, L.perm);
     float4* rec = at<float4>(ws, L.src);
+    const LbRegions lr = lb_regions(n, p->box_cap);
+    unsigned long long* lbc = at<unsigned long long>(ws, L.lookback) + lr.stats;
+    const int64_t lbc_words = lr.words - lr.stats;
     if (p->kind == P2P_GRAVITY) {
-        P2P_CUDA_TRY(launch_pdl(k_records_gravity, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float*>(strength), perm, n, rec));
+        P2P_CUDA_TRY(launch_pdl(k_records_gravity, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float*>(strength),
+                                perm, n, rec, lbc, lbc_words));
     } else {
         const int split = strength2 ? p->split : p->nrhs;
         LatticeArgs lat{};
@@ -372,7 +420,7 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
         P2P_CUDA_TRY(launch_pdl(k_records_helmholtz, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float2*>(strength),
                                                               static_cast<const float2*>(strength2), split, perm, n,
                                                               p->nrhs, p->rec_words, lat, at<Header>(ws, L.header),
-                                                              rec));
+                                                              rec, lbc, lbc_words));
     }
     P2P_LAUNCH_CHECK();
     int st = restructure_tail(p, ws, p->rec_words, s);
@@ -387,19 +435,23 @@ int restructure_adjoint(Plan* p, const float* pos, const void* a, const void* b,
     const int64_t n = p->n;
     const int32_t* perm = at<int32_t>(ws, L.perm);
     float4* rec = at<float4>(ws, L.src);
+    const LbRegions lr = lb_regions(n, p->box_cap);
+    unsigned long long* lbc = at<unsigned long long>(ws, L.lookback) + lr.stats;
+    const int64_t lbc_words = lr.words - lr.stats;
     int w;
     if (p->kind == P2P_GRAVITY) {
         w = kGravityAdjointWords;
         if (w > p->rec_alloc_words) return P2P_ERR_UNSUPPORTED;
         P2P_CUDA_TRY(launch_pdl(k_records_grav_adjoint, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float*>(a),
                                                                  static_cast<const float*>(b),
-                                                                 static_cast<const float*>(c), perm, n, rec));
+                                                                 static_cast<const float*>(c), perm, n, rec, lbc,
+                                                                 lbc_words));
     } else {
         w = helmholtz_adjoint_words(p->nrhs);
         if (w > p->rec_alloc_words) return P2P_ERR_UNSUPPORTED;
         P2P_CUDA_TRY(launch_pdl(k_records_helm_adjoint, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float2*>(a),
                                                                  static_cast<const float2*>(b), perm, n, p->nrhs, w,
-                                                                 rec));
+                                                                 rec, lbc, lbc_words));
     }
     P2P_LAUNCH_CHECK();
     p->src_ready = 0;   // the forward records are overwritten

@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "device.cuh"
+#include "lookback.cuh"
 
 namespace p2p {
 
@@ -22,11 +23,15 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // ---------------------------------------------------------------------------
 // 1. keys
 // ---------------------------------------------------------------------------
+// Also clears the chained-scan scratch of the box and neighbour CSR kernels
+// that follow (lb_words words; the grid always covers them).
 __global__ void k_keys(const float* __restrict__ pos, int64_t n, float lo0, float lo1, float lo2,
-                       float scale, int level, uint32_t* __restrict__ keys, Header* hdr) {
+                       float scale, int level, uint32_t* __restrict__ keys, Header* hdr,
+                       unsigned long long* __restrict__ lb, int64_t lb_words) {
     pdl_wait();
     pdl_release();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < lb_words) lb[i] = 0ull;
     if (i >= n) return;
     const float side = (float)(1 << level);
     const int32_t cmax = (1 << level) - 1;
@@ -130,42 +135,72 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
 }
 
 // ---------------------------------------------------------------------------
-// 3. box CSR
+// 3. box CSR: one pass over the sorted keys.  A box starts where the key
+// changes; box indices are a chained scan of those starts across tiles
+// (lookback.cuh).  The kernel also fills the dense key -> box table and
+// closes the CSR (box_start[n_boxes] = n, the box count in the header).
 // ---------------------------------------------------------------------------
-__global__ void k_box_flags(const uint32_t* __restrict__ skey, int64_t n, int32_t* __restrict__ flag) {
-    pdl_wait();
-    pdl_release();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    flag[i] = (i == 0 || skey[i] != skey[i - 1]) ? 1 : 0;
-}
+constexpr int kCsrThreads = 256;
+constexpr int kCsrItems = 8;
+constexpr int kCsrTile = kCsrThreads * kCsrItems;
+static_assert(kCsrTile == kCsrTileElems, "box CSR tile");
 
-// flag_scan[i] = number of boxes starting before i; n_boxes already in hdr
-__global__ void k_box_emit(const uint32_t* __restrict__ skey, int64_t n, const int32_t* __restrict__ flag_scan,
-                           uint32_t* __restrict__ box_key, int32_t* __restrict__ box_start) {
+__global__ void __launch_bounds__(kCsrThreads) k_box_csr(const uint32_t* __restrict__ skey, int64_t n,
+                                                        uint32_t* __restrict__ box_key,
+                                                        int32_t* __restrict__ box_start,
+                                                        int32_t* __restrict__ table, unsigned long long* lb,
+                                                        Header* hdr) {
     pdl_wait();
     pdl_release();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (i == 0 || skey[i] != skey[i - 1]) {
-        const int32_t b = flag_scan[i];
-        box_key[b] = skey[i];
-        box_start[b] = (int32_t)i;
+    __shared__ int tile_s;
+    __shared__ int32_t prefix_s;
+    if (threadIdx.x == 0) tile_s = lb_ticket(lb);
+    __syncthreads();
+    const int tile = tile_s;
+    const int64_t base = (int64_t)tile * kCsrTile + (int64_t)threadIdx.x * kCsrItems;
+    uint32_t k[kCsrItems];
+    int32_t cnt = 0;
+    unsigned starts = 0;
+    uint32_t prev = (base > 0 && base <= n) ? skey[base - 1] : 0xffffffffu;   // keys have <= 30 bits
+#pragma unroll
+    for (int j = 0; j < kCsrItems; ++j) {
+        const int64_t i = base + j;
+        k[j] = 0;
+        if (i < n) {
+            k[j] = skey[i];
+            if (k[j] != prev) {
+                starts |= 1u << j;
+                ++cnt;
+            }
+            prev = k[j];
+        }
     }
-    if (i == n - 1) box_start[flag_scan[n]] = (int32_t)n;
+    int32_t agg;
+    const int32_t off = block_excl_scan<kCsrThreads>(cnt, &agg);
+    if (threadIdx.x < 32) {
+        const int32_t ex = lb_exclusive(lb, tile, agg, hdr);
+        if (threadIdx.x == 0) prefix_s = ex;
+    }
+    __syncthreads();
+    int32_t b = prefix_s + off;
+#pragma unroll
+    for (int j = 0; j < kCsrItems; ++j) {
+        if (starts & (1u << j)) {
+            box_key[b] = k[j];
+            box_start[b] = (int32_t)(base + j);
+            if (table) table[k[j]] = b;
+            ++b;
+        }
+    }
+    if (n - 1 >= base && n - 1 < base + kCsrItems) {   // the thread holding the last particle
+        box_start[b] = (int32_t)n;
+        hdr->n_boxes = b;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // 4. neighbour lists
 // ---------------------------------------------------------------------------
-__global__ void k_table_fill(const uint32_t* __restrict__ box_key, const Header* hdr, int32_t* __restrict__ table) {
-    pdl_wait();
-    pdl_release();
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= hdr->n_boxes) return;
-    table[box_key[b]] = (int32_t)b;
-}
-
 __device__ __forceinline__ int32_t find_box(uint32_t key, const uint32_t* __restrict__ box_key, int32_t nb,
                                             const int32_t* __restrict__ table) {
     if (table) return table[key];
@@ -178,20 +213,18 @@ __device__ __forceinline__ int32_t find_box(uint32_t key, const uint32_t* __rest
     return (lo < nb && box_key[lo] == key) ? lo : -1;
 }
 
-// One warp per box: lane l < 27 examines the neighbour cell at offset
-// (l % 3 - 1, l / 3 % 3 - 1, l / 9 - 1) and looks it up; the found box
-// indices are ranked across the warp so the list is written ascending.
-// count mode (nbr_start == nullptr): cnt[b] = |N(b)|; write mode: fill nbr_idx.
-// Periodic: cells wrap and the image code (ox+1) + 3(oy+1) + 9(oz+1) records
-// which domain image of the neighbour's sources the box meets.
-__device__ __forceinline__ void neighbours_of(int64_t b, const uint32_t* __restrict__ box_key, int32_t nb, int level,
-                                             const int32_t* __restrict__ table, int32_t* __restrict__ cnt,
-                                             const int32_t* __restrict__ nbr_start, int32_t* __restrict__ nbr_idx,
-                                             int32_t* __restrict__ nbr_img, int periodic, int lane) {
+// Lane l < 27 of a warp examines the neighbour cell of box b at offset
+// (l % 3 - 1, l / 3 % 3 - 1, l / 9 - 1) and returns the box found there (or
+// -1).  Periodic: cells wrap and *code receives the image code
+// (ox+1) + 3(oy+1) + 9(oz+1) of the domain copy of that box which b meets.
+__device__ __forceinline__ int32_t neighbour_cell(int64_t b, const uint32_t* __restrict__ box_key, int32_t nb,
+                                                  int level, const int32_t* __restrict__ table, int periodic,
+                                                  int lane, int32_t* code) {
     const uint32_t key = box_key[b];
     const int32_t cx = (int32_t)compact3(key), cy = (int32_t)compact3(key >> 1), cz = (int32_t)compact3(key >> 2);
     const int32_t side = 1 << level;
-    int32_t c = -1, code = 13;
+    int32_t c = -1;
+    *code = 13;
     if (lane < 27) {
         int32_t x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
         if (periodic) {
@@ -199,43 +232,80 @@ __device__ __forceinline__ void neighbours_of(int64_t b, const uint32_t* __restr
             if (x < 0) { x += side; ox = -1; } else if (x >= side) { x -= side; ox = 1; }
             if (y < 0) { y += side; oy = -1; } else if (y >= side) { y -= side; oy = 1; }
             if (z < 0) { z += side; oz = -1; } else if (z >= side) { z -= side; oz = 1; }
-            code = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+            *code = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
             c = find_box(morton3(x, y, z), box_key, nb, table);
         } else if (x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side) {
             c = find_box(morton3(x, y, z), box_key, nb, table);
         }
     }
-    const unsigned found = __ballot_sync(FULL, c >= 0);
-    if (!nbr_start) {
-        if (lane == 0) cnt[b] = __popc(found);
-        return;
-    }
-    int rank = 0;  // found indices are distinct: rank = how many are smaller
-#pragma unroll
-    for (int j = 0; j < 27; ++j) {
-        const int32_t v = __shfl_sync(FULL, c, j);
-        rank += (v >= 0 && v < c) ? 1 : 0;
-    }
-    if (c >= 0) {
-        nbr_idx[nbr_start[b] + rank] = c;
-        if (nbr_img) nbr_img[nbr_start[b] + rank] = code;
-    }
+    return c;
 }
 
-// Grid-stride over the boxes that exist (the count is on the device); the
-// count array needs no zeros beyond it because its scan reads only n_boxes.
-__global__ void __launch_bounds__(256) k_neighbours(const uint32_t* __restrict__ box_key, const Header* hdr,
-                                                   int level, const int32_t* __restrict__ table,
-                                                   int32_t* __restrict__ cnt, const int32_t* __restrict__ nbr_start,
-                                                   int32_t* __restrict__ nbr_idx, int32_t* __restrict__ nbr_img,
-                                                   int periodic) {
+// Neighbour CSR in one pass: a block holds a tile of kNbrTile boxes, four per
+// warp; the list lengths are scanned across tiles (lookback.cuh) and each
+// list is written ascending (a found box's rank = how many found indices are
+// smaller; they are distinct).  The tile holding the last box closes the CSR.
+constexpr int kNbrPerWarp = 4;
+constexpr int kNbrTile = 8 * kNbrPerWarp;
+static_assert(kNbrTile == kBoxTile, "neighbour CSR tile");
+
+__global__ void __launch_bounds__(256) k_nbr_csr(const uint32_t* __restrict__ box_key, Header* hdr, int level,
+                                                const int32_t* __restrict__ table, int32_t* __restrict__ nbr_start,
+                                                int32_t* __restrict__ nbr_idx, int32_t* __restrict__ nbr_img,
+                                                int periodic, unsigned long long* lb) {
     pdl_wait();
     pdl_release();
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    __shared__ int tile_s;
+    __shared__ int32_t cnt_s[kNbrTile];
+    __shared__ int32_t pre_s[kNbrTile + 1];
+    if (threadIdx.x == 0) tile_s = lb_ticket(lb);
+    __syncthreads();
+    const int tile = tile_s;
     const int32_t nb = hdr->n_boxes;
-    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps)
-        neighbours_of(b, box_key, nb, level, table, cnt, nbr_start, nbr_idx, nbr_img, periodic, lane);
+    const int64_t b0 = (int64_t)tile * kNbrTile;
+    if (b0 >= nb) return;   // past the last box (whole block): no later tile waits on it
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t c[kNbrPerWarp], code[kNbrPerWarp];
+#pragma unroll
+    for (int q = 0; q < kNbrPerWarp; ++q) {
+        const int64_t b = b0 + warp * kNbrPerWarp + q;
+        c[q] = -1;
+        code[q] = 13;
+        if (b < nb) c[q] = neighbour_cell(b, box_key, nb, level, table, periodic, lane, &code[q]);
+        const int32_t found = __popc(__ballot_sync(FULL, c[q] >= 0));
+        if (lane == 0) cnt_s[warp * kNbrPerWarp + q] = found;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int32_t v = cnt_s[lane];
+        const int32_t inc = warp_incl_scan(v);
+        const int32_t agg = __shfl_sync(FULL, inc, 31);
+        const int32_t ex = lb_exclusive(lb, tile, agg, hdr);
+        pre_s[lane] = ex + inc - v;
+        if (lane == 31) pre_s[kNbrTile] = ex + inc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kNbrPerWarp; ++q) {
+        const int64_t b = b0 + warp * kNbrPerWarp + q;
+        if (b >= nb) break;
+        const int32_t start = pre_s[warp * kNbrPerWarp + q];
+        if (lane == 0) nbr_start[b] = start;
+        int rank = 0;
+#pragma unroll
+        for (int j = 0; j < 27; ++j) {
+            const int32_t v = __shfl_sync(FULL, c[q], j);
+            rank += (v >= 0 && v < c[q]) ? 1 : 0;
+        }
+        if (c[q] >= 0) {
+            nbr_idx[start + rank] = c[q];
+            if (nbr_img) nbr_img[start + rank] = code[q];
+        }
+    }
+    if (threadIdx.x == 0 && nb - 1 >= b0 && nb - 1 < b0 + kNbrTile) {
+        nbr_start[nb] = pre_s[kNbrTile];
+        hdr->n_nbr = pre_s[kNbrTile];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -259,7 +329,10 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     int32_t* hist = at<int32_t>(ws, L.hist);
     int32_t* scratch = at<int32_t>(ws, L.scan_tmp);
 
-    P2P_CUDA_TRY(launch_pdl(k_keys, blocks_for(n, 256), 256, 0, s, pos, n, p->lo[0], p->lo[1], p->lo[2], p->scale, p->level, ka, hdr));
+    const LbRegions lr = lb_regions(n, p->box_cap);
+    unsigned long long* lb = at<unsigned long long>(ws, L.lookback);
+    P2P_CUDA_TRY(launch_pdl(k_keys, blocks_for(n, 256), 256, 0, s, pos, n, p->lo[0], p->lo[1], p->lo[2], p->scale,
+                            p->level, ka, hdr, lb, lr.tree_words));
     P2P_LAUNCH_CHECK();
 
     // radix passes over 3*level key bits, equal digit widths <= 8 bits
@@ -291,37 +364,25 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
         P2P_CUDA_TRY(cudaMemcpyAsync(perm, vin, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
 
-    // box CSR
-    int32_t* flag = at<int32_t>(ws, L.flags);
+    // box CSR (and the dense key -> box table, cleared first)
     uint32_t* box_key = at<uint32_t>(ws, L.box_key);
     int32_t* box_start = at<int32_t>(ws, L.box_start);
-    P2P_CUDA_TRY(launch_pdl(k_box_flags, blocks_for(n, 256), 256, 0, s, skey, n, flag));
-    P2P_LAUNCH_CHECK();
-    int st = scan_exclusive(flag, flag, n, nullptr, &hdr->n_boxes, scratch, s);
-    if (st) return st;
-    P2P_CUDA_TRY(launch_pdl(k_box_emit, blocks_for(n, 256), 256, 0, s, skey, n, flag, box_key, box_start));
+    int32_t* table = nullptr;
+    if (p->use_table) {
+        table = at<int32_t>(ws, L.table);
+        const int st = fill32(table, 0xffffffffu, (int64_t)1 << (3 * p->level), s);
+        if (st) return st;
+    }
+    P2P_CUDA_TRY(launch_pdl(k_box_csr, blocks_for(n, kCsrTile), kCsrThreads, 0, s, skey, n, box_key, box_start,
+                            table, lb + lr.csr, hdr));
     P2P_LAUNCH_CHECK();
 
     // neighbour lists
     const int64_t bc = p->box_cap;
-    int32_t* table = nullptr;
-    if (p->use_table) {
-        table = at<int32_t>(ws, L.table);
-        st = fill32(table, 0xffffffffu, (int64_t)1 << (3 * p->level), s);
-        if (st) return st;
-        P2P_CUDA_TRY(launch_pdl(k_table_fill, blocks_for(bc, 256), 256, 0, s, box_key, hdr, table));
-        P2P_LAUNCH_CHECK();
-    }
-    int32_t* ncnt = at<int32_t>(ws, L.nbr_cnt);
-    int32_t* nstart = at<int32_t>(ws, L.nbr_start);
-    int32_t* nidx = at<int32_t>(ws, L.nbr_idx);
-    const unsigned nbl = (unsigned)std::min<int64_t>(blocks_for(bc * 32, 256), (int64_t)num_sms() * 16);
     int32_t* nimg = p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr;
-    P2P_CUDA_TRY(launch_pdl(k_neighbours, nbl, 256, 0, s, box_key, hdr, p->level, table, ncnt, nullptr, nullptr, nullptr, p->periodic));
-    P2P_LAUNCH_CHECK();
-    st = scan_exclusive(ncnt, nstart, bc, &hdr->n_boxes, &hdr->n_nbr, scratch, s);
-    if (st) return st;
-    P2P_CUDA_TRY(launch_pdl(k_neighbours, nbl, 256, 0, s, box_key, hdr, p->level, table, ncnt, nstart, nidx, nimg, p->periodic));
+    P2P_CUDA_TRY(launch_pdl(k_nbr_csr, blocks_for(bc, kNbrTile), 256, 0, s, box_key, hdr, p->level, table,
+                            at<int32_t>(ws, L.nbr_start), at<int32_t>(ws, L.nbr_idx), nimg, p->periodic,
+                            lb + lr.nbr));
     P2P_LAUNCH_CHECK();
     p->tree_ready = 1;
     p->src_ready = 0;
