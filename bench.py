@@ -559,7 +559,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="grid_helmholtz")
-    ap.add_argument("--layout", default="redundant", choices=["redundant", "indirect", "pairtask"])
+    ap.add_argument("--layout", default="redundant", choices=["redundant", "indirect", "pairtask", "symmetric"])
     ap.add_argument("--tpl", type=int, default=0)
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--ctas", type=int, default=0)

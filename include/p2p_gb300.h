@@ -26,7 +26,15 @@
  *                         5.2.1); every task writes its own partial results
  *                         and a deterministic reduction in neighbour order
  *                         adds them per target afterwards (results
- *                         duplicated, then reduced, Section 1.1).
+ *                         duplicated, then reduced, Section 1.1);
+ *   P2P_LAYOUT_SYMMETRIC  pair tasks over unordered box pairs: where one box
+ *                         of a pair fits one work item (<= 64 particles), a
+ *                         single "mutual" task evaluates each of its pairs
+ *                         once and credits both particles (the kernel is
+ *                         symmetric in the two particles), writing the
+ *                         partials of both boxes; other pairs get one
+ *                         one-sided task per direction, each box one self
+ *                         task; the same ordered reduction follows.
  *
  * Kernels (the paper names the physics, Sections 5.1 and 5.2, not formulas;
  * these are the library's definitions):
@@ -90,7 +98,9 @@ typedef enum {
     P2P_LAYOUT_INDIRECT = 0,
     P2P_LAYOUT_REDUNDANT = 1,
     P2P_LAYOUT_AUTO = 2,       /* batches only: the autotuner picks indirect or redundant */
-    P2P_LAYOUT_PAIRTASK = 3    /* single plans only; forward operators only               */
+    P2P_LAYOUT_PAIRTASK = 3,   /* single plans only; forward operators only               */
+    P2P_LAYOUT_SYMMETRIC = 4   /* as pair tasks; Helmholtz: nrhs <= 2, hardware sin/cos,
+                                  compensated; 2 targets per lane                         */
 } p2p_layout;
 
 /* plan flags */
@@ -112,7 +122,7 @@ typedef enum {
 
 /* limits of this build */
 #define P2P_MAX_N      (1LL << 26) /* particles per plan (27 n must fit in int32)   */
-#define P2P_MAX_N_PAIRTASK (1LL << 25) /* pair-task plans (54 n must fit in int32)  */
+#define P2P_MAX_N_PAIRTASK (1LL << 25) /* pair-task and symmetric plans (54 n must fit in int32) */
 #define P2P_MAX_LEVEL  10          /* octree levels (30-bit Morton keys)            */
 #define P2P_MAX_NRHS   16
 
@@ -135,8 +145,10 @@ int p2p_abi_version(void);
  *           evaluated in float32 as written (one subtraction, one product);
  *           points with (x - lo) * s outside [0, 2^level] are out of domain
  *   nrhs    right-hand sides (Helmholtz, 1..P2P_MAX_NRHS; must be 1 for gravity)
- *   layout  P2P_LAYOUT_INDIRECT, P2P_LAYOUT_REDUNDANT or P2P_LAYOUT_PAIRTASK
- *           (pair-task plans: n <= P2P_MAX_N_PAIRTASK, no P2P_PLAN_ADJOINT)
+ *   layout  P2P_LAYOUT_INDIRECT, P2P_LAYOUT_REDUNDANT, P2P_LAYOUT_PAIRTASK or
+ *           P2P_LAYOUT_SYMMETRIC (pair-task and symmetric plans: n <=
+ *           P2P_MAX_N_PAIRTASK, no P2P_PLAN_ADJOINT; symmetric Helmholtz
+ *           plans: nrhs <= 2)
  *   flags   P2P_PLAN_* bits
  * Returns P2P_ERR_INVALID_ARG on a bad shape, P2P_ERR_OOM if the host
  * allocation fails.  *out is NULL on failure.
@@ -213,6 +225,9 @@ int p2p_tree_import(p2p_plan* plan, const int32_t* perm, const int32_t* box_star
  * the tasks (one per neighbour-list entry e = (b, c)), and copies task e's
  * block [records of b | records of c] to offset pt_start[e] of the task
  * stream; the gather map then holds the sorted index of every copied record.
+ * P2P_LAYOUT_SYMMETRIC lists its tasks the same way, one per entry that holds
+ * a task (P2P_ARR_TASK_KIND: 0 = none, the mirror entry's mutual task covers
+ * the pair; 1 = self, block [records of b]; 2 = mutual; 3 = one-sided).
  *   pos        float32 [n][3]
  *   strength   gravity: float32 mass [n]; Helmholtz: complex64 q [nrhs][n]
  */
@@ -224,7 +239,8 @@ int p2p_restructure(p2p_plan* plan, const float* pos, const void* strength, void
  * p2p_restructure on this workspace first.  Writes phi float32 [n] and acc
  * float32 [n][3] in original particle order.  eps >= 0 (float32).
  * Pair-task plans: the kernel writes one partial result per (task, target)
- * and a reduction pass adds each target's partials in neighbour-list order.
+ * and a reduction pass adds each target's partials in neighbour-list order
+ * (symmetric plans: the same, with mutual tasks writing both boxes' partials).
  */
 int p2p_gravity(p2p_plan* plan, float eps, float* phi, float* acc, void* ws, size_t ws_bytes,
                 void* stream);
@@ -235,6 +251,8 @@ int p2p_gravity(p2p_plan* plan, float eps, float* phi, float* acc, void* ws, siz
  * distance stays below 100 pi the sine and cosine use the hardware
  * approximation (absolute error below 1e-6 there); otherwise the accurate
  * library routines.  Pair-task plans reduce partial results as p2p_gravity.
+ * Symmetric plans need the hardware sine/cosine range and compensated
+ * accumulation (otherwise P2P_ERR_UNSUPPORTED).
  */
 int p2p_helmholtz(p2p_plan* plan, float k, void* u, void* ws, size_t ws_bytes, void* stream);
 
@@ -250,7 +268,8 @@ int p2p_helmholtz(p2p_plan* plan, float k, void* u, void* ws, size_t ws_bytes, v
  *   gbar      complex64 [nrhs][n]
  *   grad_q    complex64 [nrhs][n] or NULL;  grad_pos float32 [n][3] or NULL
  * With grad_pos == NULL this is the forward operator with k -> -k on gbar.
- * Pair-task plans return P2P_ERR_UNSUPPORTED (as does p2p_gravity_adjoint).
+ * Pair-task and symmetric plans return P2P_ERR_UNSUPPORTED (as does
+ * p2p_gravity_adjoint).
  * With grad_pos the plan must have P2P_PLAN_ADJOINT (else
  * P2P_ERR_UNSUPPORTED).  Needs the tree; overwrites the restructured
  * records, so run p2p_restructure again before the next p2p_helmholtz.
@@ -356,7 +375,9 @@ typedef enum {
     P2P_ARR_ENT_BOX = 10,    /* int32 [n_nbr]   pair tasks: target box of entry e  */
     P2P_ARR_PT_START = 11,   /* int32 [n_nbr+1] pair tasks: record block bounds     */
     P2P_ARR_PART_START = 12, /* int32 [n_nbr+1] pair tasks: partial-result bounds   */
-    P2P_ARR_COUNT = 13
+    P2P_ARR_TASK_KIND = 13,  /* int32 [n_nbr]   symmetric tasks: task kind of entry e */
+    P2P_ARR_MIRROR = 14,     /* int32 [n_nbr]   symmetric tasks: entry (c -> b) of (b -> c) */
+    P2P_ARR_COUNT = 15
 } p2p_array_id;
 
 /*

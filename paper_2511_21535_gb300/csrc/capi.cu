@@ -45,7 +45,7 @@ void compute_layout(Plan* p) {
     L.hist = take(((size_t)256 * p->sort_tiles + 1) * 4);
     int64_t scan_max = (int64_t)256 * p->sort_tiles;
     if (n > scan_max) scan_max = n;
-    const bool pt = p->layout == P2P_LAYOUT_PAIRTASK;
+    const bool pt = is_pairtask(p->layout);
     if (pt && 27 * bc > scan_max) scan_max = 27 * bc;   // scans over neighbour entries
     L.scan_tmp = take(scan_scratch_bytes(scan_max));
     L.lookback = take((size_t)lb_regions(n, bc).words * 8);
@@ -61,6 +61,7 @@ void compute_layout(Plan* p) {
     L.pattern = (p->kind == P2P_HELMHOLTZ) ? take((size_t)kPatternMaxEntries * 8) : 0;
     L.red_start = L.red_self = L.red_src = L.gather = 0;
     L.ent_box = L.pt_start = L.part_start = L.part = 0;
+    L.task_kind = L.mirror = 0;
     if (p->layout == P2P_LAYOUT_REDUNDANT) {
         L.red_start = take((bc + 1) * 4);
         L.red_self = take(bc * 4);
@@ -69,6 +70,10 @@ void compute_layout(Plan* p) {
         L.pt_start = take(((size_t)27 * bc + 1) * 4);
         L.part_start = take(((size_t)27 * bc + 1) * 4);
         L.part = take((size_t)p->part_cap * pairtask_part_floats(p->kind, p->nrhs) * 4);
+        if (p->layout == P2P_LAYOUT_SYMMETRIC) {
+            L.task_kind = take((size_t)27 * bc * 4);
+            L.mirror = take((size_t)27 * bc * 4);
+        }
     }
     if (p->layout == P2P_LAYOUT_REDUNDANT || pt) {   // the per-box streams, or the task stream
         L.red_src = take((size_t)p->red_cap * p->rec_alloc_words * 16);
@@ -120,10 +125,10 @@ LoopArgs loop_args(const Plan* p, void* ws, int words) {
     // the indirect layout shifts the targets per neighbour range
     a.nbr_img = (p->periodic && p->layout == P2P_LAYOUT_INDIRECT) ? at<int32_t>(ws, L.nbr_img) : nullptr;
     a.edge = p->edge;
-    a.ent_box = a.pt_start = a.part_start = nullptr;
+    a.ent_box = a.pt_start = a.part_start = a.task_kind = nullptr;
     a.part = nullptr;
     a.part_cap = 0;
-    if (p->layout == P2P_LAYOUT_PAIRTASK) {
+    if (is_pairtask(p->layout)) {
         // targets and sources both come from the task stream
         a.rec = a.red = at<float4>(ws, L.red_src);
         a.ent_box = at<int32_t>(ws, L.ent_box);
@@ -131,6 +136,7 @@ LoopArgs loop_args(const Plan* p, void* ws, int words) {
         a.part_start = at<int32_t>(ws, L.part_start);
         a.part = at<float>(ws, L.part);
         a.part_cap = p->part_cap;
+        if (p->layout == P2P_LAYOUT_SYMMETRIC) a.task_kind = at<int32_t>(ws, L.task_kind);
     }
     return a;
 }
@@ -144,10 +150,10 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     if (!lo || !(edge > 0.0f) || !(edge < 3.0e38f)) return P2P_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
         if (!(lo[a] == lo[a]) || lo[a] > 3.0e38f || lo[a] < -3.0e38f) return P2P_ERR_INVALID_ARG;
-    if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT && layout != P2P_LAYOUT_PAIRTASK)
+    if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT && !is_pairtask(layout))
         return P2P_ERR_INVALID_ARG;
-    if (layout == P2P_LAYOUT_PAIRTASK && (n > P2P_MAX_N_PAIRTASK || (flags & P2P_PLAN_ADJOINT)))
-        return P2P_ERR_INVALID_ARG;
+    if (is_pairtask(layout) && (n > P2P_MAX_N_PAIRTASK || (flags & P2P_PLAN_ADJOINT))) return P2P_ERR_INVALID_ARG;
+    if (layout == P2P_LAYOUT_SYMMETRIC && kind == P2P_HELMHOLTZ && nrhs > 2) return P2P_ERR_INVALID_ARG;
     if (kind == P2P_GRAVITY && nrhs != 1) return P2P_ERR_INVALID_ARG;
     if (nrhs < 1 || nrhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
     if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING | P2P_PLAN_ADJOINT |
@@ -167,8 +173,9 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     p->flags = flags;
     const int64_t boxes = (int64_t)1 << (3 * level);
     p->box_cap = n < boxes ? n : boxes;
-    p->red_cap = (layout == P2P_LAYOUT_PAIRTASK ? 54 : 27) * n;
-    p->part_cap = (layout == P2P_LAYOUT_PAIRTASK) ? 27 * n : 0;
+    p->red_cap = (is_pairtask(layout) ? 54 : 27) * n;
+    // partial slots: one per (task, target); mutual tasks add one per source
+    p->part_cap = (layout == P2P_LAYOUT_PAIRTASK) ? 27 * n : (layout == P2P_LAYOUT_SYMMETRIC) ? 54 * n : 0;
     p->rec_words = (kind == P2P_GRAVITY) ? 1 : helmholtz_rec_words(nrhs);
     p->rec_alloc_words = p->rec_words;
     if (flags & P2P_PLAN_ADJOINT)
@@ -192,10 +199,10 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     // (level 6) and 2^22-point (level 7) Plummer spheres.
     const double items_est = (double)p->box_cap + (double)n / (32.0 * p->tpl);
     const double resident_warps = (double)num_sms() * 16.0;
-    p->group = (layout == P2P_LAYOUT_PAIRTASK || items_est > 256.0 * resident_warps) ? 1 : 4;
+    p->group = (is_pairtask(layout) || items_est > 256.0 * resident_warps) ? 1 : 4;
     p->split = nrhs;
     p->rmax = 2.0f * (edge / (float)(1 << level)) * 1.7320508f;
-    p->items_cap = (layout == P2P_LAYOUT_PAIRTASK) ? 27 * p->box_cap + (27 * n + 31) / 32 + 1
+    p->items_cap = is_pairtask(layout) ? 27 * p->box_cap + (27 * n + 31) / 32 + 1
                                                    : p->box_cap + (n + 31) / 32 + 1;
     compute_layout(p);
     return P2P_OK;
@@ -288,7 +295,7 @@ int p2p_plan_set_grid(p2p_plan* h, float grid_h, int points_per_box) {
     if (!h) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_HELMHOLTZ) return P2P_ERR_UNSUPPORTED;
-    if (p->layout == P2P_LAYOUT_PAIRTASK && points_per_box != 0) return P2P_ERR_UNSUPPORTED;
+    if (is_pairtask(p->layout) && points_per_box != 0) return P2P_ERR_UNSUPPORTED;
     if (points_per_box == 0) {
         p->pattern = 0;
         p->rec_words = helmholtz_rec_words(p->nrhs);
@@ -362,7 +369,7 @@ int p2p_gravity(p2p_plan* h, float eps, float* phi, float* acc, void* ws, size_t
     st = launch_gravity_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), eps, phi, acc, s);
     if (st) return st;
     ev_end(p, P2P_PHASE_KERNEL, s);
-    if (p->layout == P2P_LAYOUT_PAIRTASK) {
+    if (is_pairtask(p->layout)) {
         st = pairtask_reduce_gravity(p, ws, phi, acc, s);
         if (st) return st;
     }
@@ -396,7 +403,7 @@ int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void
                                  HelmOut{static_cast<float2*>(u), nullptr, p->nrhs}, s);
     if (st) return st;
     ev_end(p, P2P_PHASE_KERNEL, s);
-    if (p->layout == P2P_LAYOUT_PAIRTASK) {
+    if (is_pairtask(p->layout)) {
         st = pairtask_reduce_helmholtz(p, ws, static_cast<float2*>(u), s);
         if (st) return st;
     }
@@ -412,7 +419,7 @@ int p2p_helmholtz_adjoint(p2p_plan* h, float k, const float* pos, const void* q,
         return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_HELMHOLTZ || !(k == k) || !(fabsf(k) < 1.0e30f)) return P2P_ERR_INVALID_ARG;
-    if (p->layout == P2P_LAYOUT_PAIRTASK) return P2P_ERR_UNSUPPORTED;
+    if (is_pairtask(p->layout)) return P2P_ERR_UNSUPPORTED;
     int st = check_ws(p, ws, ws_bytes);
     if (st) return st;
     if (!p->tree_ready) return P2P_ERR_STATE;
@@ -457,7 +464,7 @@ int p2p_gravity_adjoint(p2p_plan* h, float eps, const float* pos, const float* m
         return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_GRAVITY || !(eps >= 0.0f) || !(eps < 1.0e19f)) return P2P_ERR_INVALID_ARG;
-    if (p->layout == P2P_LAYOUT_PAIRTASK) return P2P_ERR_UNSUPPORTED;
+    if (is_pairtask(p->layout)) return P2P_ERR_UNSUPPORTED;
     int st = check_ws(p, ws, ws_bytes);
     if (st) return st;
     if (!p->tree_ready) return P2P_ERR_STATE;
@@ -476,7 +483,8 @@ int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t*
     const Plan* p = &h->p;
     const Layout& L = p->L;
     const bool red = p->layout == P2P_LAYOUT_REDUNDANT;
-    const bool pt = p->layout == P2P_LAYOUT_PAIRTASK;
+    const bool pt = is_pairtask(p->layout);
+    const bool sym = p->layout == P2P_LAYOUT_SYMMETRIC;
     switch (which) {
         case P2P_ARR_PERM: *offset_bytes = L.perm; *capacity = p->n; break;
         case P2P_ARR_BOX_KEY: *offset_bytes = L.box_key; *capacity = p->box_cap; break;
@@ -505,6 +513,12 @@ int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t*
         case P2P_ARR_PART_START:
             if (!pt) return P2P_ERR_UNSUPPORTED;
             *offset_bytes = L.part_start; *capacity = 27 * p->box_cap + 1; break;
+        case P2P_ARR_TASK_KIND:
+            if (!sym) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.task_kind; *capacity = 27 * p->box_cap; break;
+        case P2P_ARR_MIRROR:
+            if (!sym) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.mirror; *capacity = 27 * p->box_cap; break;
         default: return P2P_ERR_INVALID_ARG;
     }
     return P2P_OK;

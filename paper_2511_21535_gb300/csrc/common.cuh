@@ -49,6 +49,7 @@ struct Layout {                        // byte offsets inside the workspace
         box_key, box_start, table, nbr_start, nbr_idx, src, box_S, red_start,
         red_self, red_src, gather, items, pattern, nbr_img,
         ent_box, pt_start, part_start, part,   // pair tasks (red_src/gather hold the task stream)
+        task_kind, mirror,                      // symmetric tasks
         total;
 };
 
@@ -65,7 +66,7 @@ struct Plan {
     int64_t box_cap;                   // min(n, 8^level)
     int64_t items_cap;
     int64_t red_cap;                   // 27 n records (pair tasks: 54 n)
-    int64_t part_cap;                  // pair tasks: 27 n partial-result slots
+    int64_t part_cap;                  // pair tasks: 27 n partial-result slots (symmetric: 54 n)
     int rec_words;                     // 16-byte words per source record (forward)
     int rec_alloc_words;               // words per record the workspace holds (>= adjoint records)
     int sort_tiles;
@@ -212,6 +213,12 @@ int build_items(Plan* p, void* ws, int tt, cudaStream_t s);
 int pairtask_restructure(Plan* p, void* ws, int words, cudaStream_t s);
 int pairtask_reduce_gravity(const Plan* p, void* ws, float* phi, float* acc, cudaStream_t s);
 int pairtask_reduce_helmholtz(const Plan* p, void* ws, float2* u, cudaStream_t s);
+// pair-task family: plain pair tasks or symmetric tasks
+inline bool is_pairtask(int layout) { return layout == P2P_LAYOUT_PAIRTASK || layout == P2P_LAYOUT_SYMMETRIC; }
+// the largest box a mutual task holds in one work item (two targets per lane)
+constexpr int kMutualMax = 64;
+// symmetric task kinds per neighbour entry (P2P_ARR_TASK_KIND)
+constexpr int kTaskNone = 0, kTaskSelf = 1, kTaskMutual = 2, kTaskOneSided = 3;
 // floats of partial result per (task, target)
 inline int pairtask_part_floats(int kind, int nrhs) { return kind == P2P_GRAVITY ? 4 : 2 * nrhs; }
 int helmholtz_targets_per_lane(const Plan* p, float k);

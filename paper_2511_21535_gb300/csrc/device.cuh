@@ -67,6 +67,26 @@ __device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* total) {
     return res;
 }
 
+// Sums of four per-lane values v0..v3 over the warp in one transposed
+// reduction (6 shuffles instead of 20): the halves exchange so that lanes
+// 0-15 keep sources {0,1} and 16-31 keep {2,3}, then octets split those, then
+// three butterfly steps; lanes 8u..8u+7 end with the total of v_u.
+__device__ __forceinline__ float warp_reduce4(float v0, float v1, float v2, float v3, int lane) {
+    const bool h16 = (lane & 16) != 0;
+    float k0 = h16 ? v2 : v0, k1 = h16 ? v3 : v1;
+    const float s0 = h16 ? v0 : v2, s1 = h16 ? v1 : v3;
+    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    const bool h8 = (lane & 8) != 0;
+    float kk = h8 ? k1 : k0;
+    const float ss = h8 ? k0 : k1;
+    kk += __shfl_xor_sync(0xffffffffu, ss, 8);
+    kk += __shfl_xor_sync(0xffffffffu, kk, 4);
+    kk += __shfl_xor_sync(0xffffffffu, kk, 2);
+    kk += __shfl_xor_sync(0xffffffffu, kk, 1);
+    return kk;
+}
+
 // ---------------------------------------------------------------------------
 // MUFU approximations, flush-to-zero forms (the kernels' arguments are normal
 // numbers: r^2 >= eps^2 or the squared distance of distinct points, and the

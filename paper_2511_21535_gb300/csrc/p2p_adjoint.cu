@@ -24,6 +24,7 @@ struct HelmAdjOp {
     static constexpr int NO = 2 * R + 3;        // outputs per target: grad_q (R complex), grad_x (3)
     static constexpr int kOuts = NO * K;
     static constexpr bool kPartial = false;   // adjoints are target-owned only
+    static constexpr int kMutFloats = 0;
 
     const float4* __restrict__ rec;
     const int32_t* __restrict__ perm;
@@ -290,6 +291,7 @@ struct GravAdjOp {
     static constexpr int NO = 4;                 // grad_m, grad_x (3)
     static constexpr int kOuts = NO * K;
     static constexpr bool kPartial = false;   // adjoints are target-owned only
+    static constexpr int kMutFloats = 0;
 
     const float4* __restrict__ rec;
     const int32_t* __restrict__ perm;

@@ -9,10 +9,14 @@
 
 namespace p2p {
 
-template <int K, bool COMP>
+// MUT: mutual (symmetric) pair tasks: each pair is evaluated once and
+// credited to both particles; a tile's B-side (source) sums [phi, a] are
+// reduced across the warp four sources at a time and written per source.
+template <int K, bool COMP, bool MUT = false>
 struct GravityOp {
     static constexpr int kOuts = 4 * K;   // floats per lane exchanged between cooperating warps
     static constexpr bool kPartial = true; // can write pair-task partial results
+    static constexpr int kMutFloats = MUT ? 4 : 0;
 
     const float4* __restrict__ rec;
     const int32_t* __restrict__ perm;
@@ -24,15 +28,39 @@ struct GravityOp {
     int self[K];
     float s[K][4], c[K][4], p[K][4];
     int tbase, nt;
+    // mutual tasks: the targets' masses (zero on idle lanes), the per-warp
+    // B-side scratch of one tile, and where the B-side sums go
+    float tm[K];
+    float4* bsum;
+    bool mut;
+    float4* mpart;
+    int64_t mslot;
+    int msrc0;
+
+    __device__ __forceinline__ void set_scratch(float* q) { bsum = reinterpret_cast<float4*>(q); }
+
+    __device__ __forceinline__ void set_mutual(bool on, void* part, int64_t, int64_t slot_b, int src0, int lane) {
+        mut = MUT && on;
+        if (!MUT || !on) return;
+        mpart = static_cast<float4*>(part);
+        mslot = slot_b;
+        msrc0 = src0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            tm[k] = (l < nt) ? rec[tbase + l].w : 0.f;
+        }
+    }
 
     __device__ __forceinline__ void begin(int tb, int ntg, int sw_lo, int lane) {
         tbase = tb;
         nt = ntg;
+        mut = false;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int l = lane + 32 * k;
-            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (l < nt) r = rec[tb + l];
+            // idle lanes sit on the first target: finite distances to every other particle
+            const float4 r = rec[tb + (l < nt ? l : 0)];
             tx[k] = r.x;
             ty[k] = r.y;
             tz[k] = r.z;
@@ -85,9 +113,66 @@ struct GravityOp {
         }
     }
 
+    // Mutual body: four sources per step (see the Helmholtz op); the source
+    // receives m_i (x_i - x_j) h^-3 = -m_i d h^-3 and m_i / h from target i.
+    template <bool ALLV>
+    __device__ __forceinline__ void body_mut(const float4* __restrict__ sm, int cnt) {
+        const int lane = threadIdx.x & 31;
+        for (int j0 = 0; j0 < cnt; j0 += 4) {
+            float v[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool valid = ALLV || (j0 + u < cnt);
+                const float4 src = sm[ALLV ? j0 + u : min(j0 + u, cnt - 1)];
+                const float m = valid ? src.w : 0.f;
+#pragma unroll
+                for (int o = 0; o < 4; ++o) v[u][o] = 0.f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float dx = src.x - tx[k];
+                    const float dy = src.y - ty[k];
+                    const float dz = src.z - tz[k];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                    const float inv = rsqrt_approx(r2);
+                    const float inv2 = inv * inv;
+                    const float mi = m * inv;
+                    const float mi3 = mi * inv2;
+                    float (&acc_k)[4] = COMP ? p[k] : s[k];
+                    acc_k[0] += mi;
+                    acc_k[1] = fmaf(mi3, dx, acc_k[1]);
+                    acc_k[2] = fmaf(mi3, dy, acc_k[2]);
+                    acc_k[3] = fmaf(mi3, dz, acc_k[3]);
+                    const float ti = tm[k] * inv;
+                    const float ti3 = ti * inv2;
+                    v[u][0] += ti;
+                    v[u][1] = fmaf(-ti3, dx, v[u][1]);
+                    v[u][2] = fmaf(-ti3, dy, v[u][2]);
+                    v[u][3] = fmaf(-ti3, dz, v[u][3]);
+                }
+            }
+            const int u_me = lane >> 3;
+            float t[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) t[o] = warp_reduce4(v[0][o], v[1][o], v[2][o], v[3][o], lane);
+            if ((lane & 7) == 0 && (ALLV || j0 + u_me < cnt)) bsum[j0 + u_me] = make_float4(t[0], t[1], t[2], t[3]);
+        }
+    }
+
     __device__ __forceinline__ void tile(const float4* sm, int cnt, int rec0, bool chk) {
-        if (chk) body<true>(sm, cnt, rec0);
-        else body<false>(sm, cnt, rec0);
+        if (MUT && mut) {
+            // a mutual task never holds the targets' own copies
+            if ((cnt & 3) == 0) body_mut<true>(sm, cnt);
+            else body_mut<false>(sm, cnt);
+            __syncwarp();
+            const int lane = threadIdx.x & 31;
+            const int64_t o = mslot + (rec0 - msrc0);
+            for (int l = lane; l < cnt; l += 32) mpart[o + l] = bsum[l];
+            __syncwarp();
+        } else if (chk) {
+            body<true>(sm, cnt, rec0);
+        } else {
+            body<false>(sm, cnt, rec0);
+        }
         if (COMP) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
@@ -148,12 +233,12 @@ struct GravityOp {
     }
 };
 
-template <int K, int G, bool COMP>
-__global__ void __launch_bounds__(kLoopThreads, 4)
+template <int K, int G, bool COMP, bool MUT = false>
+__global__ void __launch_bounds__(kLoopThreads, MUT ? 3 : 4)
     k_gravity(LoopArgs a, const int32_t* __restrict__ perm, float eps2, float* __restrict__ phi,
               float* __restrict__ acc) {
     pdl_wait();
-    GravityOp<K, COMP> op;
+    GravityOp<K, COMP, MUT> op;
     op.rec = a.rec;
     op.perm = perm;
     op.eps2 = eps2;
@@ -162,11 +247,12 @@ __global__ void __launch_bounds__(kLoopThreads, 4)
     warp_item_loop<K, G>(a, op);
 }
 
-template <int K, int G, bool COMP>
+template <int K, int G, bool COMP, bool MUT = false>
 static int launch_gravity(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps2, float* phi, float* acc,
                           cudaStream_t s) {
-    auto kern = k_gravity<K, G, COMP>;
-    const size_t smem = loop_smem_bytes(a.tile, a.words, GravityOp<K, COMP>::kOuts, G);
+    auto kern = k_gravity<K, G, COMP, MUT>;
+    using Op = GravityOp<K, COMP, MUT>;
+    const size_t smem = loop_smem_bytes(a.tile, a.words, Op::kOuts, G, Op::kMutFloats);
     P2P_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = p->ctas_per_sm;
     if (per_sm <= 0) {
@@ -181,6 +267,10 @@ static int launch_gravity(const Plan* p, const LoopArgs& a, const int32_t* perm,
 template <int G>
 static int launch_gravity_g(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps2, float* phi, float* acc,
                             bool comp, cudaStream_t s) {
+    if (a.task_kind) {   // symmetric tasks: two targets per lane, compensated
+        if (p->tpl != 2 || !comp) return P2P_ERR_UNSUPPORTED;
+        return launch_gravity<2, G, true, true>(p, a, perm, eps2, phi, acc, s);
+    }
     switch (p->tpl) {
         case 1: return comp ? launch_gravity<1, G, true>(p, a, perm, eps2, phi, acc, s)
                             : launch_gravity<1, G, false>(p, a, perm, eps2, phi, acc, s);

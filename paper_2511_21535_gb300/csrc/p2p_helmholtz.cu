@@ -19,8 +19,29 @@ static int fast_kg(const Plan* p, const LoopArgs& a, const int32_t* perm, float 
     }
 }
 
+// symmetric tasks: two targets per lane (a mutual task is one work item), one
+// or two right-hand sides in two-word records
+template <int G>
+static int mutual_g(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
+                    cudaStream_t s) {
+    if (p->tpl != 2 || a.words != 2) return P2P_ERR_UNSUPPORTED;
+    switch (R) {
+        case 1: return launch_helm<2, G, 1, true, false, 2, true>(p, a, perm, kk, r0, u, s);
+        case 2: return launch_helm<2, G, 2, true, false, 2, true>(p, a, perm, kk, r0, u, s);
+        default: return P2P_ERR_UNSUPPORTED;
+    }
+}
+
 int launch_helm_fast(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                      cudaStream_t s) {
+    if (a.task_kind) {
+        switch (p->group) {
+            case 1: return mutual_g<1>(p, a, perm, kk, r0, R, u, s);
+            case 2: return mutual_g<2>(p, a, perm, kk, r0, R, u, s);
+            case 4: return mutual_g<4>(p, a, perm, kk, r0, R, u, s);
+            default: return P2P_ERR_INVALID_ARG;
+        }
+    }
     const int K = p->tpl >= 2 ? 2 : 1;
     switch (p->group) {
         case 1: return K == 2 ? fast_kg<2, 1>(p, a, perm, kk, r0, R, u, s) : fast_kg<1, 1>(p, a, perm, kk, r0, R, u, s);
@@ -54,6 +75,8 @@ int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* per
         const int R = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         int st0 = fill32(&a.hdr->work_ctr, 0u, 1, s);
         if (st0) return st0;
+        // symmetric tasks run only in the compensated hardware-sin/cos kernel
+        if (a.task_kind && (precise || !comp)) return P2P_ERR_UNSUPPORTED;
         int st = precise ? launch_helm_precise(p, a, perm, k, r0, R, u, s)
                  : comp  ? launch_helm_fast(p, a, perm, k, r0, R, u, s)
                          : launch_helm_plain(p, a, perm, k, r0, R, u, s);

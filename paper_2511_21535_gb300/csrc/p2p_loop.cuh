@@ -17,7 +17,12 @@
 //   pair tasks:       an item is (task e = (b, c), targets); its targets and
 //                     its one source range both come from the task's block
 //                     [records of b | records of c], and its results go to
-//                     the task's own partial-result slots (reduced later).
+//                     the task's own partial-result slots (reduced later);
+//   symmetric tasks:  as pair tasks, but a mutual task evaluates each pair of
+//                     its unordered box pair once and also credits the
+//                     sources (the op's B-side sums, written per source to
+//                     the slots after the targets'); a self task's block is
+//                     the box alone.
 // Items are taken from a global counter (persistent grid, longest-first
 // order prepared by the restructuring pass).  Outputs are owned by exactly
 // one group, so no atomics touch results and the result does not depend on
@@ -56,13 +61,17 @@ struct LoopArgs {
     const int32_t* part_start; // pair tasks: first partial-result slot of each task
     void* part;                // pair tasks: partial results
     int64_t part_cap;          // pair tasks: slots per right-hand side
+    const int32_t* task_kind;  // symmetric tasks: 0 none, 1 self, 2 mutual, 3 one-sided; else nullptr
 };
 
+
 // dynamic shared memory: per warp two stages + mbarriers, then (G > 1) the
-// partial-sum exchange area of `outs` floats per lane
-inline size_t loop_smem_bytes(int tile, int words, int outs, int group) {
+// partial-sum exchange area of `outs` floats per lane, then (ops with
+// mutual tasks) per warp the B-side sums of one tile, `mut` floats a source
+inline size_t loop_smem_bytes(int tile, int words, int outs, int group, int mut = 0) {
     size_t b = (size_t)kLoopWarps * (2 * (size_t)tile * words * 16 + kBarBytes);
     if (group > 1) b += (size_t)kLoopWarps * 32 * outs * sizeof(float);
+    b += (size_t)kLoopWarps * tile * mut * sizeof(float);
     return b;
 }
 
@@ -107,6 +116,10 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
     float4* stage1 = reinterpret_cast<float4*>(wb + stage_bytes);
     uint64_t* bar = reinterpret_cast<uint64_t*>(wb + 2 * stage_bytes);
     float* partial = reinterpret_cast<float*>(smem_raw + (size_t)kLoopWarps * (2 * stage_bytes + kBarBytes));
+    if constexpr (Op::kMutFloats > 0) {
+        float* mut_area = partial + (G > 1 ? (size_t)kLoopWarps * 32 * Op::kOuts : 0);
+        op.set_scratch(mut_area + (size_t)warp * a.tile * Op::kMutFloats);
+    }
     if (lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -144,13 +157,22 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
         // source ranges: lane r holds range r (and its image code, periodic indirect)
         int nr, rs = 0, rc = 0, ri = 13, self_base, tgt = bs + t0;
         int64_t slot = 0;
+        bool mutual = false;
         if (pairtask) {
             const int e = it.x, tb = a.pt_start[e];
+            const int kind = a.task_kind ? a.task_kind[e] : kTaskOneSided;
             nr = 1;
-            rs = tb + nbox;
-            rc = a.pt_start[e + 1] - rs;
-            // only the task of the box with itself holds the targets' own copies
-            self_base = (a.nbr_idx[e] == b) ? rs : -(1 << 30);
+            if (kind == kTaskSelf) {       // the block is the box itself: sources = targets
+                rs = tb;
+                rc = nbox;
+                self_base = tb;
+            } else {
+                rs = tb + nbox;
+                rc = a.pt_start[e + 1] - rs;
+                // plain pair tasks: only the task of the box with itself holds the targets' own copies
+                self_base = (kind == kTaskOneSided && a.nbr_idx[e] == b) ? rs : -(1 << 30);
+            }
+            mutual = kind == kTaskMutual;   // a single item (t0 = 0): the B-side slots follow the targets'
             tgt = tb + t0;
             slot = (int64_t)a.part_start[e] + t0;
         } else if (redundant) {
@@ -171,6 +193,7 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
         }
         const int sw_lo = self_base + t0, sw_hi = sw_lo + nt;
         op.begin(tgt, nt, sw_lo, lane);
+        if constexpr (Op::kMutFloats > 0) op.set_mutual(mutual, a.part, a.part_cap, slot + nbox, rs, lane);
 
         // this warp's tiles: gw, gw + G, gw + 2G, ... of the item's tile sequence
         TileCursor pc{0, 0, 0, 0};

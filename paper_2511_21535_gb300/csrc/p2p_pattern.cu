@@ -63,6 +63,7 @@ template <int K, int R, bool COMPACT = false>
 struct HelmPatternOp : HelmOp<K, R, true, false, 0> {
     using Base = HelmOp<K, R, true, false, 0>;
     static constexpr bool kPartial = false;   // pattern plans are target-owned
+    static constexpr int kMutFloats = 0;
     const float2* tab;   // shared-memory table, already offset by the bias
     int tcode[K];
 

@@ -11,6 +11,15 @@
 // b).  The update step then adds, per target, the partials of b's tasks in
 // neighbour-list order: a fixed order, so the result is deterministic and
 // no two workers ever write the same output.
+//
+// Symmetric tasks (P2P_LAYOUT_SYMMETRIC) keep one task per unordered box
+// pair where one of the two boxes fits a work item: that "mutual" task sits
+// in the list of the lane box (the smaller index, else the other one), its
+// block is [lane box | other box], and its slots are the lane box's targets
+// followed by the other box's particles.  The mirror entry holds no task; the
+// reduction reads the other box's slots of the mutual task there.  Pairs of
+// two large boxes keep one one-sided task per direction; every box has a
+// self task whose block is the box alone.
 #include <algorithm>
 
 #include "common.cuh"
@@ -20,12 +29,15 @@ namespace p2p {
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// per entry: its target box, the block length n_b + n_c and the slot count n_b
+// per entry: its target box, the block length and the slot count (plain
+// pair tasks: n_b + n_c and n_b); symmetric tasks also get their kind and,
+// for entries without a task, the mirror entry (c -> b) in c's list
 __global__ void __launch_bounds__(256) k_pt_entries(const int32_t* __restrict__ box_start,
                                                    const int32_t* __restrict__ nbr_start,
-                                                   const int32_t* __restrict__ nbr_idx, const Header* hdr,
+                                                   const int32_t* __restrict__ nbr_idx, Header* hdr,
                                                    int32_t* __restrict__ ent_box, int32_t* __restrict__ blk_len,
-                                                   int32_t* __restrict__ slot_len) {
+                                                   int32_t* __restrict__ slot_len, int32_t* __restrict__ task_kind,
+                                                   int32_t* __restrict__ mirror) {
     pdl_wait();
     pdl_release();
     const int lane = threadIdx.x & 31;
@@ -36,14 +48,42 @@ __global__ void __launch_bounds__(256) k_pt_entries(const int32_t* __restrict__ 
         const int32_t occ = box_start[b + 1] - box_start[b];
         for (int32_t e = nbr_start[b] + lane; e < nbr_start[b + 1]; e += 32) {
             const int32_t c = nbr_idx[e];
+            const int32_t nc = box_start[c + 1] - box_start[c];
             ent_box[e] = (int32_t)b;
-            blk_len[e] = occ + (box_start[c + 1] - box_start[c]);
-            slot_len[e] = occ;
+            if (!task_kind) {
+                blk_len[e] = occ + nc;
+                slot_len[e] = occ;
+                continue;
+            }
+            int32_t kind, mir = -1;
+            if (c == b) {
+                kind = kTaskSelf;
+            } else {
+                const int32_t lo = min((int32_t)b, c), hi = max((int32_t)b, c);
+                const int32_t nlo = (lo == b) ? occ : nc, nhi = (hi == b) ? occ : nc;
+                const int32_t lane_box = nlo <= kMutualMax ? lo : (nhi <= kMutualMax ? hi : -1);
+                kind = lane_box < 0 ? kTaskOneSided : (lane_box == b ? kTaskMutual : kTaskNone);
+                if (kind == kTaskNone) {   // find b in c's ascending list
+                    int32_t l = nbr_start[c], h = nbr_start[c + 1];
+                    while (l < h) {
+                        const int32_t m = (l + h) >> 1;
+                        if (nbr_idx[m] < b) l = m + 1;
+                        else h = m;
+                    }
+                    if (l < nbr_start[c + 1] && nbr_idx[l] == b) mir = l;
+                    else atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);   // an inconsistent (imported) relation
+                }
+            }
+            task_kind[e] = kind;
+            mirror[e] = mir;
+            blk_len[e] = kind == kTaskNone ? 0 : (kind == kTaskSelf ? occ : occ + nc);
+            slot_len[e] = kind == kTaskNone ? 0 : (kind == kTaskMutual ? occ + nc : occ);
         }
     }
 }
 
 // one warp per task copies [records of b | records of c (at its periodic image)]
+// (symmetric self tasks: [records of b]; entries without a task: nothing)
 __global__ void __launch_bounds__(256) k_pt_gather(const float4* __restrict__ rec, int words,
                                                   const int32_t* __restrict__ box_start,
                                                   const int32_t* __restrict__ nbr_idx,
@@ -51,7 +91,7 @@ __global__ void __launch_bounds__(256) k_pt_gather(const float4* __restrict__ re
                                                   const int32_t* __restrict__ nbr_img, float edge,
                                                   const int32_t* __restrict__ pt_start, Header* hdr, int64_t cap,
                                                   int64_t part_cap, float4* __restrict__ pt,
-                                                  uint32_t* __restrict__ gather) {
+                                                  uint32_t* __restrict__ gather, const int32_t* __restrict__ task_kind) {
     pdl_wait();
     pdl_release();
     const int lane = threadIdx.x & 31;
@@ -65,9 +105,11 @@ __global__ void __launch_bounds__(256) k_pt_gather(const float4* __restrict__ re
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t ne = hdr->n_nbr;
     for (int64_t e = warp; e < ne; e += nwarps) {
+        const int32_t kind = task_kind ? task_kind[e] : kTaskOneSided;
+        if (kind == kTaskNone) continue;
         const int32_t b = ent_box[e], c = nbr_idx[e];
         const int32_t sb = box_start[b], nb = box_start[b + 1] - sb;
-        const int32_t sc = box_start[c], nc = box_start[c + 1] - sc;
+        const int32_t sc = box_start[c], nc = kind == kTaskSelf ? 0 : box_start[c + 1] - sc;
         const int64_t out = pt_start[e];
         warp_copy_records(rec + (int64_t)sb * words, pt + out * words, nb, words, lane, 13, edge);
         warp_copy_records(rec + (int64_t)sc * words, pt + (out + nb) * words, nc, words, lane,
@@ -87,8 +129,11 @@ int pairtask_restructure(Plan* p, void* ws, int words, cudaStream_t s) {
     int32_t* pt_start = at<int32_t>(ws, L.pt_start);
     int32_t* part_start = at<int32_t>(ws, L.part_start);
     const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
+    const bool sym = p->layout == P2P_LAYOUT_SYMMETRIC;
+    int32_t* kind = sym ? at<int32_t>(ws, L.task_kind) : nullptr;
     P2P_CUDA_TRY(launch_pdl(k_pt_entries, wb, 256, 0, s, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
-                                    at<int32_t>(ws, L.nbr_idx), hdr, ent_box, pt_start, part_start));
+                            at<int32_t>(ws, L.nbr_idx), hdr, ent_box, pt_start, part_start, kind,
+                            sym ? at<int32_t>(ws, L.mirror) : nullptr));
     P2P_LAUNCH_CHECK();
     int st = scan_exclusive(pt_start, pt_start, ecap, &hdr->n_nbr, &hdr->total_src, at<int32_t>(ws, L.scan_tmp), s);
     if (st) return st;
@@ -98,9 +143,23 @@ int pairtask_restructure(Plan* p, void* ws, int words, cudaStream_t s) {
                                             at<int32_t>(ws, L.nbr_idx), ent_box,
                                             p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr, p->edge, pt_start,
                                             hdr, p->red_cap, p->part_cap, at<float4>(ws, L.red_src),
-                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr));
+                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr,
+                                            kind));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
+}
+
+// First partial slot of box b's contribution from its neighbour entry e: the
+// entry's own task, or (symmetric, no task there) the other-box slots of the
+// mirror entry's mutual task, which follow that task's lane-box slots.
+__device__ __forceinline__ int64_t contrib_slot(int32_t e, const int32_t* __restrict__ part_start,
+                                                const int32_t* __restrict__ task_kind,
+                                                const int32_t* __restrict__ mirror,
+                                                const int32_t* __restrict__ nbr_idx,
+                                                const int32_t* __restrict__ box_start) {
+    if (!task_kind || task_kind[e] != kTaskNone) return part_start[e];
+    const int32_t c = nbr_idx[e];
+    return (int64_t)part_start[mirror[e]] + (box_start[c + 1] - box_start[c]);
 }
 
 // Update: per target, the partials of its box's tasks in neighbour order,
@@ -110,7 +169,10 @@ __global__ void __launch_bounds__(256) k_pt_reduce_gravity(const int32_t* __rest
                                                           const int32_t* __restrict__ part_start,
                                                           const int32_t* __restrict__ perm, const Header* hdr,
                                                           const float4* __restrict__ part, float* __restrict__ phi,
-                                                          float* __restrict__ acc) {
+                                                          float* __restrict__ acc,
+                                                          const int32_t* __restrict__ task_kind,
+                                                          const int32_t* __restrict__ mirror,
+                                                          const int32_t* __restrict__ nbr_idx) {
     pdl_wait();
     pdl_release();
     if (hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_TIMEOUT)) return;
@@ -124,7 +186,7 @@ __global__ void __launch_bounds__(256) k_pt_reduce_gravity(const int32_t* __rest
         for (int32_t l = lane; l < occ; l += 32) {
             float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
             for (int32_t e = e0; e < e1; ++e) {
-                const float4 v = part[(int64_t)part_start[e] + l];
+                const float4 v = part[contrib_slot(e, part_start, task_kind, mirror, nbr_idx, box_start) + l];
                 const float in[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int o = 0; o < 4; ++o) {
@@ -148,7 +210,10 @@ __global__ void __launch_bounds__(256) k_pt_reduce_helmholtz(const int32_t* __re
                                                             const int32_t* __restrict__ part_start,
                                                             const int32_t* __restrict__ perm, const Header* hdr,
                                                             const float2* __restrict__ part, int64_t cap, int nrhs,
-                                                            int64_t n, float2* __restrict__ u) {
+                                                            int64_t n, float2* __restrict__ u,
+                                                            const int32_t* __restrict__ task_kind,
+                                                            const int32_t* __restrict__ mirror,
+                                                            const int32_t* __restrict__ nbr_idx) {
     pdl_wait();
     pdl_release();
     if (hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_TIMEOUT)) return;
@@ -164,7 +229,7 @@ __global__ void __launch_bounds__(256) k_pt_reduce_helmholtz(const int32_t* __re
             for (int32_t l = lane; l < occ; l += 32) {
                 float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
                 for (int32_t e = e0; e < e1; ++e) {
-                    const float2 v = pr[(int64_t)part_start[e] + l];
+                    const float2 v = pr[contrib_slot(e, part_start, task_kind, mirror, nbr_idx, box_start) + l];
                     const float yr = v.x - cr, tr = sr + yr;
                     cr = (tr - sr) - yr;
                     sr = tr;
@@ -180,21 +245,26 @@ __global__ void __launch_bounds__(256) k_pt_reduce_helmholtz(const int32_t* __re
 
 int pairtask_reduce_gravity(const Plan* p, void* ws, float* phi, float* acc, cudaStream_t s) {
     const Layout& L = p->L;
+    const bool sym = p->layout == P2P_LAYOUT_SYMMETRIC;
     const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
     P2P_CUDA_TRY(launch_pdl(k_pt_reduce_gravity, wb, 256, 0, s, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
                                            at<int32_t>(ws, L.part_start), at<int32_t>(ws, L.perm),
-                                           at<Header>(ws, L.header), at<float4>(ws, L.part), phi, acc));
+                                           at<Header>(ws, L.header), at<float4>(ws, L.part), phi, acc,
+                                           sym ? at<int32_t>(ws, L.task_kind) : nullptr,
+                                           sym ? at<int32_t>(ws, L.mirror) : nullptr, at<int32_t>(ws, L.nbr_idx)));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }
 
 int pairtask_reduce_helmholtz(const Plan* p, void* ws, float2* u, cudaStream_t s) {
     const Layout& L = p->L;
+    const bool sym = p->layout == P2P_LAYOUT_SYMMETRIC;
     const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
     P2P_CUDA_TRY(launch_pdl(k_pt_reduce_helmholtz, wb, 256, 0, s, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
                                              at<int32_t>(ws, L.part_start), at<int32_t>(ws, L.perm),
                                              at<Header>(ws, L.header), at<float2>(ws, L.part), p->part_cap, p->nrhs,
-                                             p->n, u));
+                                             p->n, u, sym ? at<int32_t>(ws, L.task_kind) : nullptr,
+                                             sym ? at<int32_t>(ws, L.mirror) : nullptr, at<int32_t>(ws, L.nbr_idx)));
     P2P_LAUNCH_CHECK();
     return P2P_OK;
 }

@@ -240,6 +240,7 @@ struct Units {
     const int32_t* ent_box;    // pair tasks: target box per entry, else nullptr
     const int32_t* nbr_idx;    // pair tasks: source box per entry
     int64_t cap;               // units the grid covers
+    const int32_t* task_kind;  // symmetric tasks: entries without a task have no items; self tasks read the box
 };
 
 __device__ __forceinline__ int32_t unit_count(const Units& U, const Header* hdr) {
@@ -250,6 +251,7 @@ __device__ __forceinline__ void unit_shape(const Units& U, int64_t u, int32_t& o
         const int32_t b = U.ent_box[u], c = U.nbr_idx[u];
         occ = U.box_start[b + 1] - U.box_start[b];
         sb = U.box_start[c + 1] - U.box_start[c];
+        if (U.task_kind && U.task_kind[u] == kTaskNone) occ = 0;
     } else {
         occ = U.box_start[u + 1] - U.box_start[u];
         sb = U.S[u];
@@ -384,7 +386,7 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
                                             at<float4>(ws, L.red_src),
                                             (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr));
         P2P_LAUNCH_CHECK();
-    } else if (p->layout == P2P_LAYOUT_PAIRTASK) {
+    } else if (is_pairtask(p->layout)) {
         return pairtask_restructure(p, ws, words, s);
     }
     return P2P_OK;
@@ -466,11 +468,12 @@ int build_items(Plan* p, void* ws, int tt, cudaStream_t s) {
     const int32_t* S = at<int32_t>(ws, L.box_S);
     int st0 = fill32(reinterpret_cast<char*>(hdr) + kOpSectionOffset, 0u, (sizeof(Header) - kOpSectionOffset) / 4, s);
     if (st0) return st0;
-    Units U{at<int32_t>(ws, L.box_start), S, nullptr, nullptr, bc};
-    if (p->layout == P2P_LAYOUT_PAIRTASK) {
+    Units U{at<int32_t>(ws, L.box_start), S, nullptr, nullptr, bc, nullptr};
+    if (is_pairtask(p->layout)) {
         U.ent_box = at<int32_t>(ws, L.ent_box);
         U.nbr_idx = at<int32_t>(ws, L.nbr_idx);
         U.cap = 27 * bc;
+        if (p->layout == P2P_LAYOUT_SYMMETRIC) U.task_kind = at<int32_t>(ws, L.task_kind);
     }
     P2P_CUDA_TRY(launch_pdl(k_items_count, blocks_for(U.cap, 256), 256, 0, s, U, hdr, tt));
     P2P_LAUNCH_CHECK();

@@ -15,7 +15,7 @@ import torch
 from . import build as _build
 
 GRAVITY, HELMHOLTZ = 0, 1
-LAYOUTS = {"indirect": 0, "redundant": 1, "auto": 2, "pairtask": 3}
+LAYOUTS = {"indirect": 0, "redundant": 1, "auto": 2, "pairtask": 3, "symmetric": 4}
 PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING, PLAN_ADJOINT, PLAN_PERIODIC = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_DOMAIN, FLAG_TIMEOUT, FLAG_CAPACITY, FLAG_LATTICE = 0x1, 0x2, 0x4, 0x8
 
@@ -23,7 +23,7 @@ ARRAYS = {"perm": (0, torch.int32), "box_key": (1, torch.int32), "box_start": (2
           "nbr_start": (3, torch.int32), "nbr_idx": (4, torch.int32), "red_start": (5, torch.int32),
           "red_self": (6, torch.int32), "gather_idx": (7, torch.int32), "sorted_key": (8, torch.int32),
           "nbr_img": (9, torch.int32), "ent_box": (10, torch.int32), "pt_start": (11, torch.int32),
-          "part_start": (12, torch.int32)}
+          "part_start": (12, torch.int32), "task_kind": (13, torch.int32), "mirror": (14, torch.int32)}
 COUNTERS = ("n_boxes", "n_nbr", "flags", "total_src", "pairs", "n_items")
 PHASES = ("tree", "restructure", "kernel", "operator")
 

@@ -57,7 +57,7 @@ def _create(lib, kind=0, n=1000, level=3, lo=(0.0, 0.0, 0.0), edge=1.0, nrhs=1, 
 
 def test_plan_argument_checks(lib):
     bad = [dict(n=0), dict(n=(1 << 26) + 1), dict(level=0), dict(level=11), dict(edge=0.0), dict(edge=-1.0),
-           dict(kind=2), dict(layout=4), dict(layout=2), dict(nrhs=2), dict(kind=1, nrhs=0), dict(kind=1, nrhs=17),
+           dict(kind=2), dict(layout=5), dict(layout=2), dict(layout=4, kind=1, nrhs=3), dict(nrhs=2), dict(kind=1, nrhs=0), dict(kind=1, nrhs=17),
            dict(layout=3, n=(1 << 25) + 1), dict(layout=3, flags=0x8), dict(flags=0x10, level=1),
            dict(flags=0x100), dict(lo=(float("nan"), 0.0, 0.0))]
     for kw in bad:
