@@ -34,20 +34,25 @@ sys.path.insert(0, ROOT)
 from paper_2511_21535_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "P2P pair-interactions/s"
-KERNEL_SOURCES = {"helmholtz": ["common.cuh", "device.cuh", "p2p_loop.cuh", "p2p_helmholtz.cuh", "p2p_helmholtz.cu"],
-                  "gravity": ["common.cuh", "device.cuh", "p2p_loop.cuh", "p2p_gravity.cu"]}
 
 
-def kernel_traffic(kind: str, workload: str, layout: str, n: int):
+def kernel_name(kind: str, symmetric: bool) -> str:
+    """The dominant kernel of a step: symmetric Helmholtz runs k_helmsym."""
+    return "k_helmsym" if (kind == "helmholtz" and symmetric) else f"k_{kind}"
+
+
+def kernel_traffic(kernel: str, workload: str, layout: str, n: int, symmetric: bool):
     """DRAM bytes per launch from the committed ncu capture, if the kernel's
     sources are unchanged since that capture (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "kernel_traffic.json")
     try:
-        rec = json.load(open(path)).get(f"k_{kind}")
+        rec = json.load(open(path)).get(kernel)
     except (OSError, ValueError):
         return None
     if not rec or rec.get("workload") != workload or rec.get("layout") != layout:
+        return None
+    if bool(rec.get("symmetric", False)) != symmetric:
         return None
     if rec.get("n") is not None and rec["n"] != n:
         return None
@@ -97,9 +102,10 @@ def _make_problem(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def workload_config(prob, layout, pattern=False):
+def workload_config(prob, layout, pattern=False, symmetric=False):
     cfg = {"workload": prob.name, "n": prob.n, "level": prob.level, "kernel": prob.kind, "layout": layout,
            "kernel_mode": "pattern table" if pattern else "direct",
+           "evaluation": "symmetric (each pair of small box pairs once)" if symmetric else "one-sided",
            "boundary": "periodic" if prob.extra.get("periodic") else "open", "nrhs": prob.nrhs,
            "l2": "flushed between steps (512 MiB write)", "inputs": "seeded synthetic"}
     if prob.kind == "gravity":
@@ -187,8 +193,13 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     prob = make_problem(args.workload, args.periodic)
     layout = args.layout
+    # symmetric evaluation applies to the target-owned layouts in direct mode with <= 2 right-hand sides
+    # ("auto": the Helmholtz kernel, where it measured faster; the gravity workloads' large boxes gain little)
+    want = args.evaluation == "symmetric" or (args.evaluation == "auto" and prob.kind == "helmholtz")
+    symmetric = (want and not args.pattern and layout in ("redundant", "indirect")
+                 and (prob.kind == "gravity" or prob.nrhs <= 2))
     plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
-                    timing=True, periodic=args.periodic, device=dev)
+                    timing=True, periodic=args.periodic, symmetric=symmetric, device=dev)
     if args.tpl:
         plan.set_tuning(args.tpl, args.tile, args.ctas, args.group)
     if args.pattern:
@@ -354,7 +365,9 @@ def run_gpu(args, rank, world, local_rank):
     else:
         pipe, per_pair = "fp32", 13.0
         peak = pipes["fp32"] * sms * f_mhz * 1e6 / per_pair
-    achieved = geo_pairs / (kern_ms * 1e-3)
+    # pair evaluations the kernel performs (a symmetric plan's mutual evaluation serves two ordered pairs)
+    evals = cnt.get("evals", geo_pairs) if (symmetric or layout == "symmetric") else geo_pairs
+    achieved = evals / (kern_ms * 1e-3)
     result = {
         "metric": METRIC,
         "value": value,
@@ -368,13 +381,18 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": workload_config(prob, layout, args.pattern),
+        "config": workload_config(prob, layout, args.pattern, symmetric),
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
-        "roofline": {"bound": "alu", "pipe": pipe, "kernel": f"k_{prob.kind}", "achieved": achieved / 1e9,
+        "roofline": {"bound": "alu", "pipe": pipe, "kernel": kernel_name(prob.kind, symmetric),
+                     "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak,
-                     "traffic": None if args.periodic else kernel_traffic(prob.kind, prob.name, layout, prob.n),
+                     "traffic": None if args.periodic else kernel_traffic(kernel_name(prob.kind, symmetric),
+                                                                          prob.name, layout, prob.n, symmetric),
                      "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms,
+                     "evaluations_per_launch": evals,
+                     "work_unit": ("pair evaluation (a mutual one serves two ordered pairs)"
+                                   if evals != geo_pairs else "ordered pair"),
                      "peak_source": "pipe rates measured by p2p_measure_pipes x SMs x sampled SM clock",
                      "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in pipes.items()}},
         "phases_ms": {k: (sum(v) / len(v) if v else None) for k, v in phases.items()},
@@ -570,6 +588,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--pattern", action="store_true", help="tabulated-G kernel for grid workloads")
     ap.add_argument("--periodic", action="store_true", help="toroidal neighbourhoods (wrapped boxes)")
+    ap.add_argument("--evaluation", default="auto", choices=["auto", "symmetric", "one-sided"],
+                    help="symmetric: each pair of box pairs with a box of <= 64 particles is evaluated once for "
+                         "both particles; one-sided: every ordered pair is evaluated (pattern mode, pair tasks "
+                         "and more than two right-hand sides are one-sided); auto: symmetric for Helmholtz")
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -111,6 +111,12 @@ typedef enum {
 #define P2P_PLAN_PERIODIC    0x10u /* toroidal boundaries: neighbour cells wrap and  */
                                    /* a wrapped neighbour's sources interact through */
                                    /* their image one domain edge away (level >= 2)  */
+#define P2P_PLAN_SYMMETRIC   0x20u /* indirect / redundant layouts: each pair of a   */
+                                   /* box pair in which one box holds <= 64          */
+                                   /* particles is evaluated once and credited to    */
+                                   /* both particles (see P2P_ARR_TASK_KIND); forward */
+                                   /* operators only; Helmholtz nrhs <= 2, hardware  */
+                                   /* sine/cosine range, compensated; 2 targets/lane */
 
 /* device flag bits (p2p_read_counters: counters[P2P_CTR_FLAGS]) */
 #define P2P_FLAG_DOMAIN   0x1u     /* a position was outside the domain             */
@@ -375,9 +381,10 @@ typedef enum {
     P2P_ARR_ENT_BOX = 10,    /* int32 [n_nbr]   pair tasks: target box of entry e  */
     P2P_ARR_PT_START = 11,   /* int32 [n_nbr+1] pair tasks: record block bounds     */
     P2P_ARR_PART_START = 12, /* int32 [n_nbr+1] pair tasks: partial-result bounds   */
-    P2P_ARR_TASK_KIND = 13,  /* int32 [n_nbr]   symmetric tasks: task kind of entry e */
-    P2P_ARR_MIRROR = 14,     /* int32 [n_nbr]   symmetric tasks: entry (c -> b) of (b -> c) */
-    P2P_ARR_COUNT = 15
+    P2P_ARR_TASK_KIND = 13,  /* int32 [n_nbr]   symmetric: kind of entry e (0 none, 1 self, 2 mutual, 3 one-sided) */
+    P2P_ARR_MIRROR = 14,     /* int32 [n_nbr]   symmetric: entry (c -> b) of an entry (b -> c) without a task */
+    P2P_ARR_BSLOT = 15,      /* int32 [n_nbr]   P2P_PLAN_SYMMETRIC: first slot of a mutual entry's source sums */
+    P2P_ARR_COUNT = 16
 } p2p_array_id;
 
 /*
@@ -398,7 +405,9 @@ typedef enum {
     P2P_CTR_TOTAL_SRC = 3,   /* redundant records sum_b S_b (pair tasks: task-stream records) */
     P2P_CTR_PAIRS = 4,       /* ordered pairs sum_b n_b S_b - n (last op)   */
     P2P_CTR_N_ITEMS = 5,     /* work items of the last operator call        */
-    P2P_CTR_COUNT = 6
+    P2P_CTR_EVALS = 6,       /* pair evaluations: P2P_CTR_PAIRS, but a mutual evaluation of a */
+                             /* symmetric plan counts once for its two ordered pairs          */
+    P2P_CTR_COUNT = 7
 } p2p_counter_id;
 
 /*

@@ -383,6 +383,7 @@ int p2p_batch_counters(const p2p_batch* h, const void* ws, int64_t* out, void* s
     out[P2P_CTR_TOTAL_SRC] = hdr.total_src;
     out[P2P_CTR_PAIRS] = (int64_t)hdr.pairs_nS - b.N;
     out[P2P_CTR_N_ITEMS] = hdr.n_items;
+    out[P2P_CTR_EVALS] = (int64_t)hdr.evals_nS - b.N;
     if (hdr.flags & P2P_FLAG_TIMEOUT) return P2P_ERR_TIMEOUT;
     return P2P_OK;
 }

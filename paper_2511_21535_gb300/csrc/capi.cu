@@ -61,7 +61,7 @@ void compute_layout(Plan* p) {
     L.pattern = (p->kind == P2P_HELMHOLTZ) ? take((size_t)kPatternMaxEntries * 8) : 0;
     L.red_start = L.red_self = L.red_src = L.gather = 0;
     L.ent_box = L.pt_start = L.part_start = L.part = 0;
-    L.task_kind = L.mirror = 0;
+    L.task_kind = L.mirror = L.bslot = 0;
     if (p->layout == P2P_LAYOUT_REDUNDANT) {
         L.red_start = take((bc + 1) * 4);
         L.red_self = take(bc * 4);
@@ -74,6 +74,12 @@ void compute_layout(Plan* p) {
             L.task_kind = take((size_t)27 * bc * 4);
             L.mirror = take((size_t)27 * bc * 4);
         }
+    }
+    if (p->sym) {   // symmetric evaluation on a target-owned layout
+        L.task_kind = take((size_t)27 * bc * 4);
+        L.mirror = take((size_t)27 * bc * 4);
+        L.bslot = take(((size_t)27 * bc + 1) * 4);
+        L.part = take((size_t)p->part_cap * pairtask_part_floats(p->kind, p->nrhs) * 4);
     }
     if (p->layout == P2P_LAYOUT_REDUNDANT || pt) {   // the per-box streams, or the task stream
         L.red_src = take((size_t)p->red_cap * p->rec_alloc_words * 16);
@@ -108,7 +114,7 @@ static void ev_end(Plan* p, int ph, cudaStream_t s) {
 
 LoopArgs loop_args(const Plan* p, void* ws, int words) {
     const Layout& L = p->L;
-    LoopArgs a;
+    LoopArgs a{};   // every field not set below is null
     a.rec = at<float4>(ws, L.src);
     a.red = (p->layout == P2P_LAYOUT_REDUNDANT) ? at<float4>(ws, L.red_src) : nullptr;
     a.words = words;
@@ -138,6 +144,12 @@ LoopArgs loop_args(const Plan* p, void* ws, int words) {
         a.part_cap = p->part_cap;
         if (p->layout == P2P_LAYOUT_SYMMETRIC) a.task_kind = at<int32_t>(ws, L.task_kind);
     }
+    if (p->sym) {
+        a.task_kind = at<int32_t>(ws, L.task_kind);
+        a.bslot = at<int32_t>(ws, L.bslot);
+        a.part = at<float>(ws, L.part);
+        a.part_cap = p->part_cap;
+    }
     return a;
 }
 
@@ -157,11 +169,15 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     if (kind == P2P_GRAVITY && nrhs != 1) return P2P_ERR_INVALID_ARG;
     if (nrhs < 1 || nrhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
     if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING | P2P_PLAN_ADJOINT |
-                  P2P_PLAN_PERIODIC))
+                  P2P_PLAN_PERIODIC | P2P_PLAN_SYMMETRIC))
+        return P2P_ERR_INVALID_ARG;
+    if ((flags & P2P_PLAN_SYMMETRIC) &&
+        (is_pairtask(layout) || (flags & P2P_PLAN_ADJOINT) || (kind == P2P_HELMHOLTZ && nrhs > 2)))
         return P2P_ERR_INVALID_ARG;
     if ((flags & P2P_PLAN_PERIODIC) && level < 2) return P2P_ERR_INVALID_ARG;
     *p = Plan{};
     p->periodic = (flags & P2P_PLAN_PERIODIC) ? 1 : 0;
+    p->sym = (flags & P2P_PLAN_SYMMETRIC) ? 1 : 0;
     p->kind = kind;
     p->n = n;
     p->level = level;
@@ -175,7 +191,8 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     p->box_cap = n < boxes ? n : boxes;
     p->red_cap = (is_pairtask(layout) ? 54 : 27) * n;
     // partial slots: one per (task, target); mutual tasks add one per source
-    p->part_cap = (layout == P2P_LAYOUT_PAIRTASK) ? 27 * n : (layout == P2P_LAYOUT_SYMMETRIC) ? 54 * n : 0;
+    p->part_cap = (layout == P2P_LAYOUT_PAIRTASK || (flags & P2P_PLAN_SYMMETRIC)) ? 27 * n
+                  : (layout == P2P_LAYOUT_SYMMETRIC) ? 54 * n : 0;
     p->rec_words = (kind == P2P_GRAVITY) ? 1 : helmholtz_rec_words(nrhs);
     p->rec_alloc_words = p->rec_words;
     if (flags & P2P_PLAN_ADJOINT)
@@ -295,7 +312,7 @@ int p2p_plan_set_grid(p2p_plan* h, float grid_h, int points_per_box) {
     if (!h) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_HELMHOLTZ) return P2P_ERR_UNSUPPORTED;
-    if (is_pairtask(p->layout) && points_per_box != 0) return P2P_ERR_UNSUPPORTED;
+    if ((is_pairtask(p->layout) || p->sym) && points_per_box != 0) return P2P_ERR_UNSUPPORTED;
     if (points_per_box == 0) {
         p->pattern = 0;
         p->rec_words = helmholtz_rec_words(p->nrhs);
@@ -372,6 +389,9 @@ int p2p_gravity(p2p_plan* h, float eps, float* phi, float* acc, void* ws, size_t
     if (is_pairtask(p->layout)) {
         st = pairtask_reduce_gravity(p, ws, phi, acc, s);
         if (st) return st;
+    } else if (p->sym) {
+        st = sym_fixup_gravity(p, ws, phi, acc, s);
+        if (st) return st;
     }
     ev_end(p, P2P_PHASE_OPERATOR, s);
     return P2P_OK;
@@ -406,6 +426,9 @@ int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void
     if (is_pairtask(p->layout)) {
         st = pairtask_reduce_helmholtz(p, ws, static_cast<float2*>(u), s);
         if (st) return st;
+    } else if (p->sym) {
+        st = sym_fixup_helmholtz(p, ws, static_cast<float2*>(u), s);
+        if (st) return st;
     }
     ev_end(p, P2P_PHASE_OPERATOR, s);
     return P2P_OK;
@@ -419,7 +442,7 @@ int p2p_helmholtz_adjoint(p2p_plan* h, float k, const float* pos, const void* q,
         return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_HELMHOLTZ || !(k == k) || !(fabsf(k) < 1.0e30f)) return P2P_ERR_INVALID_ARG;
-    if (is_pairtask(p->layout)) return P2P_ERR_UNSUPPORTED;
+    if (is_pairtask(p->layout) || p->sym) return P2P_ERR_UNSUPPORTED;
     int st = check_ws(p, ws, ws_bytes);
     if (st) return st;
     if (!p->tree_ready) return P2P_ERR_STATE;
@@ -464,7 +487,7 @@ int p2p_gravity_adjoint(p2p_plan* h, float eps, const float* pos, const float* m
         return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_GRAVITY || !(eps >= 0.0f) || !(eps < 1.0e19f)) return P2P_ERR_INVALID_ARG;
-    if (is_pairtask(p->layout)) return P2P_ERR_UNSUPPORTED;
+    if (is_pairtask(p->layout) || p->sym) return P2P_ERR_UNSUPPORTED;
     int st = check_ws(p, ws, ws_bytes);
     if (st) return st;
     if (!p->tree_ready) return P2P_ERR_STATE;
@@ -484,7 +507,7 @@ int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t*
     const Layout& L = p->L;
     const bool red = p->layout == P2P_LAYOUT_REDUNDANT;
     const bool pt = is_pairtask(p->layout);
-    const bool sym = p->layout == P2P_LAYOUT_SYMMETRIC;
+    const bool sym = p->layout == P2P_LAYOUT_SYMMETRIC || p->sym;
     switch (which) {
         case P2P_ARR_PERM: *offset_bytes = L.perm; *capacity = p->n; break;
         case P2P_ARR_BOX_KEY: *offset_bytes = L.box_key; *capacity = p->box_cap; break;
@@ -519,6 +542,9 @@ int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t*
         case P2P_ARR_MIRROR:
             if (!sym) return P2P_ERR_UNSUPPORTED;
             *offset_bytes = L.mirror; *capacity = 27 * p->box_cap; break;
+        case P2P_ARR_BSLOT:
+            if (!p->sym) return P2P_ERR_UNSUPPORTED;
+            *offset_bytes = L.bslot; *capacity = 27 * p->box_cap + 1; break;
         default: return P2P_ERR_INVALID_ARG;
     }
     return P2P_OK;
@@ -538,6 +564,7 @@ int p2p_read_counters(const p2p_plan* h, const void* ws, int64_t* out, void* str
     out[P2P_CTR_TOTAL_SRC] = hdr.total_src;
     out[P2P_CTR_PAIRS] = (int64_t)hdr.pairs_nS - h->p.n;
     out[P2P_CTR_N_ITEMS] = hdr.n_items;
+    out[P2P_CTR_EVALS] = (int64_t)hdr.evals_nS - h->p.n;
     if (hdr.flags & P2P_FLAG_TIMEOUT) return P2P_ERR_TIMEOUT;
     if (hdr.flags & P2P_FLAG_DOMAIN) return P2P_ERR_DOMAIN;
     if (hdr.flags & (P2P_FLAG_CAPACITY | P2P_FLAG_LATTICE)) return P2P_ERR_INVALID_ARG;

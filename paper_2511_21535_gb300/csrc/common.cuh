@@ -27,7 +27,8 @@ struct Header {
     unsigned long long pairs_nS;       // sum_b n_b S_b
     int32_t total_src;                 // sum_b S_b (redundant records; pair tasks: task-stream records)
     int32_t part_total;                // pair tasks: partial-result slots, sum_e n_b(e)
-    int32_t restr_pad[12];
+    unsigned long long evals_nS;       // sum over streamed pairs (symmetric: mutual pairs once), self included
+    int32_t restr_pad[10];
     // operator section (zeroed at the start of each operator call), offset 128
     int32_t n_items;
     uint32_t work_ctr;
@@ -49,7 +50,8 @@ struct Layout {                        // byte offsets inside the workspace
         box_key, box_start, table, nbr_start, nbr_idx, src, box_S, red_start,
         red_self, red_src, gather, items, pattern, nbr_img,
         ent_box, pt_start, part_start, part,   // pair tasks (red_src/gather hold the task stream)
-        task_kind, mirror,                      // symmetric tasks
+        task_kind, mirror,                      // symmetric tasks (layout or plan flag)
+        bslot,                                  // plan flag: source-sum slots of mutual entries
         total;
 };
 
@@ -79,6 +81,7 @@ struct Plan {
     int split;                         // Helmholtz RHS from here on form a conjugated second output
     // pattern mode (regular grids): lattice spacing, points per box edge, table strides
     int periodic;
+    int sym;                           // P2P_PLAN_SYMMETRIC on a target-owned layout
     int pattern;
     float grid_h;
     int grid_t;
@@ -135,14 +138,14 @@ inline cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, si
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
-// Chained-scan scratch (lookback.cuh), three regions of 1 + tiles words:
-// the box CSR (tiles of kCsrTileElems sorted particles), the neighbour CSR
-// and the box statistics (tiles of kBoxTile boxes).  The key kernel clears
-// the first two, the record kernels of the restructuring the third.
+// Chained-scan scratch (lookback.cuh), regions of 1 + tiles words: the box
+// CSR (tiles of kCsrTileElems sorted particles), the neighbour CSR and two
+// chains of the box statistics (tiles of kBoxTile boxes).  The key kernel
+// clears the first two, the record kernels of the restructuring the others.
 constexpr int kCsrTileElems = 2048;
 constexpr int kBoxTile = 32;
 struct LbRegions {
-    int64_t csr, nbr, stats, tree_words, words;   // offsets and sizes in 8-byte words
+    int64_t csr, nbr, stats, stats2, tree_words, words;   // offsets and sizes in 8-byte words
 };
 inline LbRegions lb_regions(int64_t n, int64_t box_cap) {
     LbRegions r;
@@ -150,9 +153,10 @@ inline LbRegions lb_regions(int64_t n, int64_t box_cap) {
     const int64_t b = 1 + (box_cap + kBoxTile - 1) / kBoxTile;
     r.csr = 0;
     r.nbr = a;
-    r.stats = a + b;
+    r.stats = a + b;                   // stream bounds
+    r.stats2 = a + 2 * b;              // source-sum slots (symmetric plans)
     r.tree_words = a + b;
-    r.words = a + 2 * b;
+    r.words = a + 3 * b;
     return r;
 }
 
@@ -213,6 +217,10 @@ int build_items(Plan* p, void* ws, int tt, cudaStream_t s);
 int pairtask_restructure(Plan* p, void* ws, int words, cudaStream_t s);
 int pairtask_reduce_gravity(const Plan* p, void* ws, float* phi, float* acc, cudaStream_t s);
 int pairtask_reduce_helmholtz(const Plan* p, void* ws, float2* u, cudaStream_t s);
+// symmetric plans on target-owned layouts: add the source sums of the mutual
+// entries (written by other boxes' items) to the outputs
+int sym_fixup_gravity(const Plan* p, void* ws, float* phi, float* acc, cudaStream_t s);
+int sym_fixup_helmholtz(const Plan* p, void* ws, float2* u, cudaStream_t s);
 // pair-task family: plain pair tasks or symmetric tasks
 inline bool is_pairtask(int layout) { return layout == P2P_LAYOUT_PAIRTASK || layout == P2P_LAYOUT_SYMMETRIC; }
 // the largest box a mutual task holds in one work item (two targets per lane)

@@ -71,6 +71,7 @@ void noalloc_layout(Plan* p) {
     L.pattern = 0;
     L.nbr_img = 0;
     L.ent_box = L.pt_start = L.part_start = L.part = 0;
+    L.task_kind = L.mirror = L.bslot = 0;
     L.total = off;
 }
 
@@ -145,7 +146,7 @@ extern "C" int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t 
     if (st) return st;
     st = build_items(&p, ws, 32 * p.tpl, s);
     if (st) return st;
-    LoopArgs a;
+    LoopArgs a{};   // every field not set below is null
     a.rec = at<float4>(ws, p.L.src);
     a.red = (layout == P2P_LAYOUT_REDUNDANT) ? at<float4>(ws, p.L.red_src) : nullptr;
     a.words = 1;

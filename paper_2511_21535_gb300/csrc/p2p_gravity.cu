@@ -39,17 +39,11 @@ struct GravityOp {
 
     __device__ __forceinline__ void set_scratch(float* q) { bsum = reinterpret_cast<float4*>(q); }
 
-    __device__ __forceinline__ void set_mutual(bool on, void* part, int64_t, int64_t slot_b, int src0, int lane) {
+    // the current source range: mutual or not, its first source-sum slot and first record
+    __device__ __forceinline__ void set_range(bool on, int64_t slot_b, int src0) {
         mut = MUT && on;
-        if (!MUT || !on) return;
-        mpart = static_cast<float4*>(part);
         mslot = slot_b;
         msrc0 = src0;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int l = lane + 32 * k;
-            tm[k] = (l < nt) ? rec[tbase + l].w : 0.f;
-        }
     }
 
     __device__ __forceinline__ void begin(int tb, int ntg, int sw_lo, int lane) {
@@ -64,6 +58,7 @@ struct GravityOp {
             tx[k] = r.x;
             ty[k] = r.y;
             tz[k] = r.z;
+            tm[k] = (MUT && l < nt) ? r.w : 0.f;   // mutual ranges: the targets' masses (zero on idle lanes)
             self[k] = (l < nt) ? sw_lo + l : -1;
 #pragma unroll
             for (int o = 0; o < 4; ++o) s[k][o] = c[k][o] = p[k][o] = 0.f;
@@ -239,6 +234,7 @@ __global__ void __launch_bounds__(kLoopThreads, MUT ? 3 : 4)
               float* __restrict__ acc) {
     pdl_wait();
     GravityOp<K, COMP, MUT> op;
+    if constexpr (MUT) op.mpart = static_cast<float4*>(a.part);
     op.rec = a.rec;
     op.perm = perm;
     op.eps2 = eps2;
@@ -267,7 +263,7 @@ static int launch_gravity(const Plan* p, const LoopArgs& a, const int32_t* perm,
 template <int G>
 static int launch_gravity_g(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps2, float* phi, float* acc,
                             bool comp, cudaStream_t s) {
-    if (a.task_kind) {   // symmetric tasks: two targets per lane, compensated
+    if (a.task_kind) {   // symmetric tasks or plans: two targets per lane, compensated
         if (p->tpl != 2 || !comp) return P2P_ERR_UNSUPPORTED;
         return launch_gravity<2, G, true, true>(p, a, perm, eps2, phi, acc, s);
     }

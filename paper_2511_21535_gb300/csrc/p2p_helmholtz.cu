@@ -1,6 +1,7 @@
 // Helmholtz P2P: dispatch over right-hand-side passes, and the fast
 // (hardware sine/cosine, compensated) kernel variants.
 #include "p2p_helmholtz.cuh"
+#include "p2p_helmsym.cuh"
 
 namespace p2p {
 
@@ -19,15 +20,15 @@ static int fast_kg(const Plan* p, const LoopArgs& a, const int32_t* perm, float 
     }
 }
 
-// symmetric tasks: two targets per lane (a mutual task is one work item), one
-// or two right-hand sides in two-word records
+// symmetric tasks and plans: items of 64 targets (a mutual task or box is one
+// work item), one or two right-hand sides in two-word records
 template <int G>
 static int mutual_g(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                     cudaStream_t s) {
     if (p->tpl != 2 || a.words != 2) return P2P_ERR_UNSUPPORTED;
-    switch (R) {
-        case 1: return launch_helm<2, G, 1, true, false, 2, true>(p, a, perm, kk, r0, u, s);
-        case 2: return launch_helm<2, G, 2, true, false, 2, true>(p, a, perm, kk, r0, u, s);
+    switch (R) {   // four targets per lane, two source groups (measured best on GB300)
+        case 1: return launch_helmsym<G, 1, 4>(p, a, perm, kk, r0, u, s);
+        case 2: return launch_helmsym<G, 2, 4>(p, a, perm, kk, r0, u, s);
         default: return P2P_ERR_UNSUPPORTED;
     }
 }

@@ -16,14 +16,11 @@
 namespace p2p {
 
 // W: record stride in 16-byte words when known at compile time (0 = runtime)
-// MUT: mutual (symmetric) pair tasks: G of each pair is evaluated once and
-// credited to both particles; the B-side (source) sums of a tile are reduced
-// across the warp four sources at a time and written per source.
-template <int K, int R, bool COMP, bool PRECISE, int W = 0, bool MUT = false>
+template <int K, int R, bool COMP, bool PRECISE, int W = 0>
 struct HelmOp {
     static constexpr int kOuts = 2 * R * K;
     static constexpr bool kPartial = true;    // can write pair-task partial results
-    static constexpr int kMutFloats = MUT ? 2 * R : 0;
+    static constexpr int kMutFloats = 0;      // one-sided (symmetric plans use HelmSymOp)
 
     const float4* __restrict__ rec;
     const int32_t* __restrict__ perm;
@@ -38,45 +35,10 @@ struct HelmOp {
     int self[K];
     float sr[K][R], si[K][R], cr[K][R], ci[K][R], pr[K][R], pi_[K][R];
     int tbase, nt;
-    // mutual tasks: the targets' own strengths (zero on idle lanes), the
-    // per-warp B-side scratch of one tile, and where the B-side sums go
-    float tqr[K][R], tqi[K][R];
-    float2* bsum;
-    bool mut;
-    float2* mpart;
-    int64_t mcap, mslot;
-    int msrc0;
-
-    __device__ __forceinline__ void set_scratch(float* p) { bsum = reinterpret_cast<float2*>(p); }
-
-    __device__ __forceinline__ void set_mutual(bool on, void* part, int64_t cap, int64_t slot_b, int src0, int lane) {
-        mut = MUT && on;
-        if (!MUT || !on) return;
-        mpart = static_cast<float2*>(part);
-        mcap = cap;
-        mslot = slot_b;
-        msrc0 = src0;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int l = lane + 32 * k;
-            const float4* r = rec + (int64_t)(tbase + (l < nt ? l : 0)) * words;
-#pragma unroll
-            for (int w = 0; w < (R + 1) / 2; ++w) {
-                const float4 v = (l < nt) ? r[qw0 + w] : make_float4(0.f, 0.f, 0.f, 0.f);
-                tqr[k][2 * w] = v.x;
-                tqi[k][2 * w] = v.y;
-                if (2 * w + 1 < R) {
-                    tqr[k][2 * w + 1] = v.z;
-                    tqi[k][2 * w + 1] = v.w;
-                }
-            }
-        }
-    }
 
     __device__ __forceinline__ void begin(int tb, int ntg, int sw_lo, int lane) {
         tbase = tb;
         nt = ntg;
-        mut = false;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int l = lane + 32 * k;
@@ -158,86 +120,9 @@ struct HelmOp {
         }
     }
 
-    // Mutual body: four sources per step; A-side sums as in body(), B-side
-    // sums of the four sources reduced over the warp (lane 8u holds source u).
-    // ALLV: cnt is a multiple of four; otherwise the last step re-reads the
-    // last source with zero strength for the missing ones.
-    template <bool ALLV>
-    __device__ __forceinline__ void body_mut(const float4* __restrict__ sm, int cnt) {
-        const int stride = W ? W : words;
-        const int lane = threadIdx.x & 31;
-        for (int j0 = 0; j0 < cnt; j0 += 4) {
-            float vr[4][R], vi[4][R];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool valid = ALLV || (j0 + u < cnt);
-                const float4* rj = sm + (int64_t)(ALLV ? j0 + u : min(j0 + u, cnt - 1)) * stride;
-                const float4 ps = rj[0];
-                float qr[R], qi[R];
-#pragma unroll
-                for (int w = 0; w < (R + 1) / 2; ++w) {
-                    const float4 v = rj[qw0 + w];
-                    qr[2 * w] = valid ? v.x : 0.f;
-                    qi[2 * w] = valid ? v.y : 0.f;
-                    if (2 * w + 1 < R) {
-                        qr[2 * w + 1] = valid ? v.z : 0.f;
-                        qi[2 * w + 1] = valid ? v.w : 0.f;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < R; ++q) vr[u][q] = vi[u][q] = 0.f;
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const float dx = ps.x - tx[k];
-                    const float dy = ps.y - ty[k];
-                    const float dz = ps.z - tz[k];
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float inv = rsqrt_approx(r2);
-                    const float th = kk * (r2 * inv);
-                    const float sn = sin_approx(th), cs = cos_approx(th);
-                    const float gr = inv * cs, gi = inv * sn;
-#pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        float& ar = COMP ? pr[k][q] : sr[k][q];
-                        float& ai = COMP ? pi_[k][q] : si[k][q];
-                        ar = fmaf(gr, qr[q], fmaf(-gi, qi[q], ar));
-                        ai = fmaf(gr, qi[q], fmaf(gi, qr[q], ai));
-                        vr[u][q] = fmaf(gr, tqr[k][q], fmaf(-gi, tqi[k][q], vr[u][q]));
-                        vi[u][q] = fmaf(gr, tqi[k][q], fmaf(gi, tqr[k][q], vi[u][q]));
-                    }
-                }
-            }
-            const int u_me = lane >> 3;
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const float br = warp_reduce4(vr[0][q], vr[1][q], vr[2][q], vr[3][q], lane);
-                const float bi = warp_reduce4(vi[0][q], vi[1][q], vi[2][q], vi[3][q], lane);
-                if ((lane & 7) == 0 && (ALLV || j0 + u_me < cnt)) bsum[(j0 + u_me) * R + q] = make_float2(br, bi);
-            }
-        }
-    }
-
     __device__ __forceinline__ void tile(const float4* sm, int cnt, int rec0, bool chk) {
-        if (MUT && mut) {
-            // a mutual task never holds the targets' own copies
-            if ((cnt & 3) == 0) body_mut<true>(sm, cnt);
-            else body_mut<false>(sm, cnt);
-            __syncwarp();
-            const float inv4pi = 0.0795774715459476678844418816862571882f;  // 1 / (4 pi)
-            const int lane = threadIdx.x & 31;
-            const int64_t o = mslot + (rec0 - msrc0);
-            for (int l = lane; l < cnt; l += 32)
-#pragma unroll
-                for (int q = 0; q < R; ++q) {
-                    const float2 v = bsum[l * R + q];
-                    mpart[(int64_t)(r0 + q) * mcap + o + l] = make_float2(v.x * inv4pi, v.y * inv4pi);
-                }
-            __syncwarp();
-        } else if (chk) {
-            body<true>(sm, cnt, rec0);
-        } else {
-            body<false>(sm, cnt, rec0);
-        }
+        if (chk) body<true>(sm, cnt, rec0);
+        else body<false>(sm, cnt, rec0);
         if (COMP) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
@@ -315,11 +200,11 @@ struct HelmOp {
     }
 };
 
-template <int K, int G, int R, bool COMP, bool PRECISE, int W = 0, bool MUT = false>
-__global__ void __launch_bounds__(kLoopThreads, MUT ? 5 : 6)
+template <int K, int G, int R, bool COMP, bool PRECISE, int W = 0>
+__global__ void __launch_bounds__(kLoopThreads, 6)
     k_helmholtz(LoopArgs a, const int32_t* __restrict__ perm, float kk, int qw0, int64_t n, int r0, HelmOut out) {
     pdl_wait();
-    HelmOp<K, R, COMP, PRECISE, W, MUT> op;
+    HelmOp<K, R, COMP, PRECISE, W> op;
     op.rec = a.rec;
     op.perm = perm;
     op.kk = kk;
@@ -331,10 +216,10 @@ __global__ void __launch_bounds__(kLoopThreads, MUT ? 5 : 6)
     warp_item_loop<K, G>(a, op);
 }
 
-template <int K, int G, int R, bool COMP, bool PRECISE, int W = 0, bool MUT = false>
+template <int K, int G, int R, bool COMP, bool PRECISE, int W = 0>
 int launch_helm(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, HelmOut u, cudaStream_t s) {
-    auto kern = k_helmholtz<K, G, R, COMP, PRECISE, W, MUT>;
-    using Op = HelmOp<K, R, COMP, PRECISE, W, MUT>;
+    auto kern = k_helmholtz<K, G, R, COMP, PRECISE, W>;
+    using Op = HelmOp<K, R, COMP, PRECISE, W>;
     const size_t smem = loop_smem_bytes(a.tile, a.words, Op::kOuts, G, Op::kMutFloats);
     P2P_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = p->ctas_per_sm;

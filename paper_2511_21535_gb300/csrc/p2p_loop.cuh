@@ -62,6 +62,7 @@ struct LoopArgs {
     void* part;                // pair tasks: partial results
     int64_t part_cap;          // pair tasks: slots per right-hand side
     const int32_t* task_kind;  // symmetric tasks: 0 none, 1 self, 2 mutual, 3 one-sided; else nullptr
+    const int32_t* bslot;      // symmetric plans (target-owned layouts): source-sum slots per entry
 };
 
 
@@ -154,15 +155,17 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
         const int nbox = a.box_start[b + 1] - bs;
         const int nt = min(32 * K, nbox - t0);
 
-        // source ranges: lane r holds range r (and its image code, periodic indirect)
-        int nr, rs = 0, rc = 0, ri = 13, self_base, tgt = bs + t0;
+        // source ranges: lane r holds range r (and its image code, periodic indirect;
+        // its task kind and source-sum slots, symmetric plans)
+        int nr, rs = 0, rc = 0, ri = 13, rk = kTaskOneSided, rb = 0, self_base, tgt = bs + t0;
+        const bool sym = a.task_kind != nullptr && !pairtask;
         int64_t slot = 0;
         bool mutual = false;
         if (pairtask) {
             const int e = it.x, tb = a.pt_start[e];
             const int kind = a.task_kind ? a.task_kind[e] : kTaskOneSided;
             nr = 1;
-            if (kind == kTaskSelf) {       // the block is the box itself: sources = targets
+            if (kind == kTaskSelf) {   // the block is the box itself: sources = targets
                 rs = tb;
                 rc = nbox;
                 self_base = tb;
@@ -175,12 +178,13 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
             mutual = kind == kTaskMutual;   // a single item (t0 = 0): the B-side slots follow the targets'
             tgt = tb + t0;
             slot = (int64_t)a.part_start[e] + t0;
-        } else if (redundant) {
+        } else if (redundant && !sym) {
             nr = 1;
             rs = a.red_start[b];
             rc = a.red_start[b + 1] - rs;
             self_base = rs + a.red_self[b];
         } else {
+            // one range per neighbour entry (symmetric: entries without a task are empty)
             const int e0 = a.nbr_start[b];
             nr = a.nbr_start[b + 1] - e0;
             if (lane < nr) {
@@ -188,12 +192,24 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
                 rs = a.box_start[c];
                 rc = a.box_start[c + 1] - rs;
                 if (a.nbr_img) ri = a.nbr_img[e0 + lane];
+                if (sym) {
+                    rk = a.task_kind[e0 + lane];
+                    rb = a.bslot[e0 + lane];
+                    if (rk == kTaskNone) rc = 0;
+                }
             }
             self_base = bs;
+            if (redundant) {   // symmetric streams hold the streamed entries back to back
+                const int inc = warp_incl_scan(rc);
+                rs = a.red_start[b] + inc - rc;
+                self_base = a.red_start[b] + a.red_self[b];
+            }
         }
         const int sw_lo = self_base + t0, sw_hi = sw_lo + nt;
         op.begin(tgt, nt, sw_lo, lane);
-        if constexpr (Op::kMutFloats > 0) op.set_mutual(mutual, a.part, a.part_cap, slot + nbox, rs, lane);
+        if constexpr (Op::kMutFloats > 0) {
+            if (pairtask) op.set_range(mutual, slot + nbox, rs);
+        }
 
         // this warp's tiles: gw, gw + G, gw + 2G, ... of the item's tile sequence
         TileCursor pc{0, 0, 0, 0};
@@ -215,16 +231,26 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
         };
 
         bool failed = false;
-        int shift_r = -1;   // range whose image shift the targets carry
+        int cur_r = -1;   // range whose per-range state (image shift, task kind) the op holds
+        const bool per_range = a.nbr_img != nullptr || (Op::kMutFloats > 0 && sym);
         if (pc.r < nr) issue();
         while (cc.r < nr) {
             if (pc.r < nr) issue();
-            if (a.nbr_img && cc.r != shift_r) {
-                // periodic: meet this neighbour's image by moving the targets the other way
-                shift_r = cc.r;
-                const int code = __shfl_sync(FULL, ri, cc.r);
-                op.set_shift((float)(code % 3 - 1) * a.edge, (float)((code / 3) % 3 - 1) * a.edge,
-                             (float)(code / 9 - 1) * a.edge);
+            if (per_range && cc.r != cur_r) {
+                cur_r = cc.r;
+                if (a.nbr_img) {
+                    // periodic: meet this neighbour's image by moving the targets the other way
+                    const int code = __shfl_sync(FULL, ri, cc.r);
+                    op.set_shift((float)(code % 3 - 1) * a.edge, (float)((code / 3) % 3 - 1) * a.edge,
+                                 (float)(code / 9 - 1) * a.edge);
+                }
+                if constexpr (Op::kMutFloats > 0) {
+                    if (sym) {
+                        const int k = __shfl_sync(FULL, rk, cc.r);
+                        const int slot_b = __shfl_sync(FULL, rb, cc.r);
+                        op.set_range(k == kTaskMutual, slot_b, cc.s);
+                    }
+                }
             }
             const int st = cseq & 1;
             if (!warp_wait(&bar[st], (cseq >> 1) & 1)) {

@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(256) k_pt_entries(const int32_t* __restrict__ 
             }
             task_kind[e] = kind;
             mirror[e] = mir;
+            // the statistics counted every entry's work; a mirror entry's pairs are evaluated by its mutual task
+            if (kind == kTaskNone) atomicAdd(&hdr->evals_nS, 0ull - (unsigned long long)occ * (unsigned long long)nc);
             blk_len[e] = kind == kTaskNone ? 0 : (kind == kTaskSelf ? occ : occ + nc);
             slot_len[e] = kind == kTaskNone ? 0 : (kind == kTaskMutual ? occ + nc : occ);
         }
@@ -241,6 +243,129 @@ __global__ void __launch_bounds__(256) k_pt_reduce_helmholtz(const int32_t* __re
             }
         }
     }
+}
+
+// Symmetric plans on target-owned layouts: the kernel wrote every target's
+// own-item sums to the outputs; add, in neighbour order, the source sums
+// other boxes' mutual ranges left for it (entries without a task: the slots
+// of the mirror entry, one per particle of this box in box order).
+__global__ void __launch_bounds__(256) k_sym_fixup_gravity(const int32_t* __restrict__ box_start,
+                                                          const int32_t* __restrict__ nbr_start,
+                                                          const int32_t* __restrict__ task_kind,
+                                                          const int32_t* __restrict__ mirror,
+                                                          const int32_t* __restrict__ bslot,
+                                                          const int32_t* __restrict__ perm, const Header* hdr,
+                                                          const float4* __restrict__ part, float* __restrict__ phi,
+                                                          float* __restrict__ acc) {
+    pdl_wait();
+    pdl_release();
+    if (hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_TIMEOUT)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nb = hdr->n_boxes;
+    for (int64_t b = warp; b < nb; b += nwarps) {
+        const int32_t bs = box_start[b], occ = box_start[b + 1] - bs;
+        const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+        // lane e: the first slot of this box's sums in entry e's mirror task, if e holds no task
+        int32_t my_slot = -1;
+        if (lane < ne && task_kind[e0 + lane] == kTaskNone) my_slot = bslot[mirror[e0 + lane]];
+        const unsigned none = __ballot_sync(FULL, my_slot >= 0);
+        if (!none) continue;
+        for (int32_t l0 = 0; l0 < occ; l0 += 32) {   // whole warp in step: the shuffles need every lane
+            const int32_t l = l0 + lane;
+            const bool act = l < occ;
+            float sm[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+            for (unsigned m = none; m; m &= m - 1) {
+                const int32_t slot = __shfl_sync(FULL, my_slot, __ffs(m) - 1);
+                if (!act) continue;
+                const float4 v = part[(int64_t)slot + l];
+                const float in[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const float y = in[o] - c[o];
+                    const float t = sm[o] + y;
+                    c[o] = (t - sm[o]) - y;
+                    sm[o] = t;
+                }
+            }
+            if (!act) continue;
+            const int64_t o = perm[bs + l];
+            phi[o] -= sm[0] - c[0];
+            acc[3 * o + 0] += sm[1] - c[1];
+            acc[3 * o + 1] += sm[2] - c[2];
+            acc[3 * o + 2] += sm[3] - c[3];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sym_fixup_helmholtz(const int32_t* __restrict__ box_start,
+                                                            const int32_t* __restrict__ nbr_start,
+                                                            const int32_t* __restrict__ task_kind,
+                                                            const int32_t* __restrict__ mirror,
+                                                            const int32_t* __restrict__ bslot,
+                                                            const int32_t* __restrict__ perm, const Header* hdr,
+                                                            const float2* __restrict__ part, int64_t cap, int nrhs,
+                                                            int64_t n, float2* __restrict__ u) {
+    pdl_wait();
+    pdl_release();
+    if (hdr->flags & (P2P_FLAG_CAPACITY | P2P_FLAG_TIMEOUT)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t nb = hdr->n_boxes;
+    for (int64_t b = warp; b < nb; b += nwarps) {
+        const int32_t bs = box_start[b], occ = box_start[b + 1] - bs;
+        const int32_t e0 = nbr_start[b], e1 = nbr_start[b + 1];
+        int32_t my_slot = -1;
+        if (lane < e1 - e0 && task_kind[e0 + lane] == kTaskNone) my_slot = bslot[mirror[e0 + lane]];
+        const unsigned none = __ballot_sync(FULL, my_slot >= 0);
+        if (!none) continue;
+        for (int r = 0; r < nrhs; ++r) {
+            const float2* pr = part + (int64_t)r * cap;
+            for (int32_t l0 = 0; l0 < occ; l0 += 32) {   // whole warp in step: the shuffles need every lane
+                const int32_t l = l0 + lane;
+                const bool act = l < occ;
+                float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
+                for (unsigned m = none; m; m &= m - 1) {
+                    const int32_t slot = __shfl_sync(FULL, my_slot, __ffs(m) - 1);
+                    if (!act) continue;
+                    const float2 v = pr[(int64_t)slot + l];
+                    const float yr = v.x - cr, tr = sr + yr;
+                    cr = (tr - sr) - yr;
+                    sr = tr;
+                    const float yi = v.y - ci, ti = si + yi;
+                    ci = (ti - si) - yi;
+                    si = ti;
+                }
+                if (!act) continue;
+                float2& out = u[(int64_t)r * n + perm[bs + l]];
+                out = make_float2(out.x + (sr - cr), out.y + (si - ci));
+            }
+        }
+    }
+}
+
+int sym_fixup_gravity(const Plan* p, void* ws, float* phi, float* acc, cudaStream_t s) {
+    const Layout& L = p->L;
+    const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
+    P2P_CUDA_TRY(launch_pdl(k_sym_fixup_gravity, wb, 256, 0, s, at<int32_t>(ws, L.box_start),
+                            at<int32_t>(ws, L.nbr_start), at<int32_t>(ws, L.task_kind), at<int32_t>(ws, L.mirror),
+                            at<int32_t>(ws, L.bslot), at<int32_t>(ws, L.perm), at<Header>(ws, L.header),
+                            at<float4>(ws, L.part), phi, acc));
+    P2P_LAUNCH_CHECK();
+    return P2P_OK;
+}
+
+int sym_fixup_helmholtz(const Plan* p, void* ws, float2* u, cudaStream_t s) {
+    const Layout& L = p->L;
+    const unsigned wb = (unsigned)std::min<int64_t>(blocks_for(p->box_cap * 32, 256), (int64_t)num_sms() * 16);
+    P2P_CUDA_TRY(launch_pdl(k_sym_fixup_helmholtz, wb, 256, 0, s, at<int32_t>(ws, L.box_start),
+                            at<int32_t>(ws, L.nbr_start), at<int32_t>(ws, L.task_kind), at<int32_t>(ws, L.mirror),
+                            at<int32_t>(ws, L.bslot), at<int32_t>(ws, L.perm), at<Header>(ws, L.header),
+                            at<float2>(ws, L.part), p->part_cap, p->nrhs, p->n, u));
+    P2P_LAUNCH_CHECK();
+    return P2P_OK;
 }
 
 int pairtask_reduce_gravity(const Plan* p, void* ws, float* phi, float* acc, cudaStream_t s) {

@@ -14,6 +14,8 @@
 //   gravity    [x, y, z, m]
 //   Helmholtz  [x, y, z, 0] then nrhs complex q values packed two per word
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 
 #include "common.cuh"
 #include "device.cuh"
@@ -151,28 +153,49 @@ __global__ void k_records_grav_adjoint(const float* __restrict__ pos, const floa
 }
 
 // Per-box statistics, a tile of kBoxTile boxes per block, four per warp
-// (lane e reads neighbour e): S[b] = sum of the occupancies of b's
-// neighbours; self[b] = offset of b's own particles in its stream (neighbours
-// are ascending, so it is the sum over neighbours with a smaller index); the
-// pair count sum_b n_b S_b.  For the redundant layout the stream bounds
-// red_start = exclusive scan of S are chained across tiles in the same pass
-// (lookback.cuh), and the tile holding the last box closes them.
+// (lane e reads neighbour e): S[b] = sum of the occupancies of the
+// neighbours in b's stream; self[b] = offset of b's own particles in it
+// (neighbours are ascending, so it is the sum over streamed neighbours with a
+// smaller index); the pair count sum_b n_b S_b over all neighbours.  For the
+// redundant layout the stream bounds red_start = exclusive scan of S are
+// chained across tiles in the same pass (lookback.cuh), and the tile holding
+// the last box closes them.
+//
+// Symmetric plans (task_kind != nullptr) also classify each entry (b -> c):
+// self; mutual when b is the pair's lane box (the smaller index if it holds
+// <= kMutualMax particles, else the other one if that one does); none for
+// the other entry of such a pair (its mirror entry is found in c's list);
+// one-sided when neither box fits.  Only self, mutual and one-sided entries
+// are streamed, and the mutual entries' source-sum slots (one per source
+// particle) are a second chained scan.
 constexpr int kStatsPerWarp = kBoxTile / 8;
+
+__device__ __forceinline__ int32_t entry_kind(int32_t b, int32_t c, int32_t nb_occ, int32_t nc) {
+    if (c == b) return kTaskSelf;
+    const int32_t lo = min(b, c), hi = max(b, c);
+    const int32_t nlo = (lo == b) ? nb_occ : nc, nhi = (hi == b) ? nb_occ : nc;
+    const int32_t lane_box = nlo <= kMutualMax ? lo : (nhi <= kMutualMax ? hi : -1);
+    return lane_box < 0 ? kTaskOneSided : (lane_box == b ? kTaskMutual : kTaskNone);
+}
 
 __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ box_start,
                                                   const int32_t* __restrict__ nbr_start,
                                                   const int32_t* __restrict__ nbr_idx, Header* hdr,
                                                   int32_t* __restrict__ S, int32_t* __restrict__ self_off,
-                                                  int32_t* __restrict__ red_start, unsigned long long* lb) {
+                                                  int32_t* __restrict__ red_start, unsigned long long* lb,
+                                                  int32_t* __restrict__ task_kind, int32_t* __restrict__ mirror,
+                                                  int32_t* __restrict__ bslot, unsigned long long* lb2,
+                                                  int64_t part_cap) {
     pdl_wait();
     pdl_release();
     __shared__ int tile_s;
-    __shared__ int32_t s_s[kBoxTile];
-    __shared__ int32_t pre_s[kBoxTile + 1];
-    __shared__ unsigned long long pairs_s;
+    __shared__ int32_t s_s[kBoxTile], b_s[kBoxTile];
+    __shared__ int32_t pre_s[kBoxTile + 1], bpre_s[kBoxTile + 1];
+    __shared__ unsigned long long pairs_s, evals_s;
     if (threadIdx.x == 0) {
         tile_s = lb_ticket(lb);
         pairs_s = 0ull;
+        evals_s = 0ull;
     }
     __syncthreads();
     const int tile = tile_s;
@@ -180,50 +203,109 @@ __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ b
     const int64_t b0 = (int64_t)tile * kBoxTile;
     if (b0 >= nb) return;   // past the last box (whole block): no later tile waits on it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long pairs = 0ull;
+    unsigned long long pairs = 0ull, evals = 0ull;
+    int32_t cbx[kStatsPerWarp];   // symmetric: this lane's offset among its box's mutual source slots
 #pragma unroll
     for (int q = 0; q < kStatsPerWarp; ++q) {
         const int64_t b = b0 + warp * kStatsPerWarp + q;
-        int32_t cnt = 0, lower = 0;
+        int32_t all = 0, cnt = 0, lower = 0, cb = 0;
         if (b < nb) {
             const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
             if (lane < ne) {
-                const int32_t c = nbr_idx[e0 + lane];
-                cnt = box_start[c + 1] - box_start[c];
-                lower = c < b ? cnt : 0;
+                const int32_t e = e0 + lane;
+                const int32_t c = nbr_idx[e];
+                const int32_t nc = box_start[c + 1] - box_start[c];
+                all = nc;
+                int32_t kind = kTaskOneSided;
+                if (task_kind) {
+                    kind = entry_kind((int32_t)b, c, box_start[b + 1] - box_start[b], nc);
+                    int32_t mir = -1;
+                    if (kind == kTaskNone) {
+                        // b's position in c's ascending list: independent loads, one latency
+                        const int32_t c0 = nbr_start[c], cn = nbr_start[c + 1] - c0;
+                        int32_t below = 0;
+                        bool found = false;
+#pragma unroll
+                        for (int i = 0; i < 27; ++i) {
+                            const int32_t v = i < cn ? nbr_idx[c0 + i] : INT32_MAX;
+                            below += v < b ? 1 : 0;
+                            found |= v == b;
+                        }
+                        if (found && cn <= 27) mir = c0 + below;
+                        else atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);   // inconsistent (imported) relation
+                    }
+                    task_kind[e] = kind;
+                    mirror[e] = mir;
+                }
+                cnt = kind == kTaskNone ? 0 : nc;
+                lower = (c < b) ? cnt : 0;
+                cb = kind == kTaskMutual ? nc : 0;
             }
         }
+        const int32_t cbi = warp_incl_scan(cb);
+        cbx[q] = cbi - cb;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
+            all += __shfl_xor_sync(FULL, all, o);
             cnt += __shfl_xor_sync(FULL, cnt, o);
             lower += __shfl_xor_sync(FULL, lower, o);
         }
+        const int32_t cbt = __shfl_sync(FULL, cbi, 31);
         if (lane == 0) {
             s_s[warp * kStatsPerWarp + q] = cnt;
+            b_s[warp * kStatsPerWarp + q] = cbt;
             if (b < nb) {
                 S[b] = cnt;
                 if (self_off) self_off[b] = lower;
-                pairs += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)cnt;
+                pairs += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)all;
+                evals += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)cnt;
             }
         }
     }
     if (lane == 0 && pairs) atomicAdd(&pairs_s, pairs);
+    if (lane == 0 && evals) atomicAdd(&evals_s, evals);
     __syncthreads();
     if (threadIdx.x == 0 && pairs_s) atomicAdd(&hdr->pairs_nS, pairs_s);
-    if (!red_start) return;
-    if (warp == 0) {
-        const int32_t v = s_s[lane];
-        const int32_t inc = warp_incl_scan(v);
-        const int32_t agg = __shfl_sync(FULL, inc, 31);
-        const int32_t ex = lb_exclusive(lb, tile, agg, hdr);
-        pre_s[lane] = ex + inc - v;
-        if (lane == 31) pre_s[kBoxTile] = ex + inc;
+    if (threadIdx.x == 0 && evals_s) atomicAdd(&hdr->evals_nS, evals_s);
+    const bool last = nb - 1 >= b0 && nb - 1 < b0 + kBoxTile;
+    if (red_start) {
+        if (warp == 0) {
+            const int32_t v = s_s[lane];
+            const int32_t inc = warp_incl_scan(v);
+            const int32_t agg = __shfl_sync(FULL, inc, 31);
+            const int32_t ex = lb_exclusive(lb, tile, agg, hdr);
+            pre_s[lane] = ex + inc - v;
+            if (lane == 31) pre_s[kBoxTile] = ex + inc;
+        }
+        __syncthreads();
+        if (threadIdx.x < kBoxTile && b0 + threadIdx.x < nb) red_start[b0 + threadIdx.x] = pre_s[threadIdx.x];
+        if (threadIdx.x == 0 && last) {
+            red_start[nb] = pre_s[kBoxTile];
+            hdr->total_src = pre_s[kBoxTile];
+        }
     }
-    __syncthreads();
-    if (threadIdx.x < kBoxTile && b0 + threadIdx.x < nb) red_start[b0 + threadIdx.x] = pre_s[threadIdx.x];
-    if (threadIdx.x == 0 && nb - 1 >= b0 && nb - 1 < b0 + kBoxTile) {
-        red_start[nb] = pre_s[kBoxTile];
-        hdr->total_src = pre_s[kBoxTile];
+    if (bslot) {
+        if (warp == 0) {
+            const int32_t v = b_s[lane];
+            const int32_t inc = warp_incl_scan(v);
+            const int32_t agg = __shfl_sync(FULL, inc, 31);
+            const int32_t ex = lb_exclusive(lb2, tile, agg, hdr);
+            bpre_s[lane] = ex + inc - v;
+            if (lane == 31) bpre_s[kBoxTile] = ex + inc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kStatsPerWarp; ++q) {
+            const int64_t b = b0 + warp * kStatsPerWarp + q;
+            if (b < nb) {
+                const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+                if (lane < ne) bslot[e0 + lane] = bpre_s[warp * kStatsPerWarp + q] + cbx[q];
+            }
+        }
+        if (threadIdx.x == 0 && last) {
+            hdr->part_total = bpre_s[kBoxTile];
+            if ((int64_t)bpre_s[kBoxTile] > part_cap) atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);
+        }
     }
 }
 
@@ -331,7 +413,8 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
                                                    const int32_t* __restrict__ nbr_img, float edge,
                                                    const int32_t* __restrict__ red_start, Header* hdr,
                                                    int64_t red_cap, float4* __restrict__ red,
-                                                   uint32_t* __restrict__ gather) {
+                                                   uint32_t* __restrict__ gather,
+                                                   const int32_t* __restrict__ task_kind) {
     pdl_wait();
     pdl_release();
     const int lane = threadIdx.x & 31;
@@ -346,6 +429,7 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
     for (int64_t b = warp; b < nb; b += nwarps) {
         int64_t out = red_start[b];
         for (int32_t e = nbr_start[b]; e < nbr_start[b + 1]; ++e) {
+            if (task_kind && task_kind[e] == kTaskNone) continue;   // symmetric: the mirror's mutual item covers it
             const int32_t c = nbr_idx[e];
             const int32_t s0 = box_start[c];
             const int32_t cnt = box_start[c + 1] - s0;
@@ -372,10 +456,15 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
                      (kOpSectionOffset - kRestrSectionOffset) / 4, s);
     if (st0) return st0;
     int32_t* red_start = red ? at<int32_t>(ws, L.red_start) : nullptr;
-    unsigned long long* lb = at<unsigned long long>(ws, L.lookback) + lb_regions(p->n, bc).stats;
+    unsigned long long* lb = at<unsigned long long>(ws, L.lookback) + lb_regions(p->n, bc).stats;   // stream bounds
+    const LbRegions lr = lb_regions(p->n, bc);
+    unsigned long long* lb2 = at<unsigned long long>(ws, L.lookback) + lr.stats2;
+    int32_t* kinds = p->sym ? at<int32_t>(ws, L.task_kind) : nullptr;
     P2P_CUDA_TRY(launch_pdl(k_box_stats, blocks_for(bc, kBoxTile), 256, 0, s, at<int32_t>(ws, L.box_start),
                             at<int32_t>(ws, L.nbr_start), at<int32_t>(ws, L.nbr_idx), hdr, S,
-                            red ? at<int32_t>(ws, L.red_self) : nullptr, red_start, lb));
+                            red ? at<int32_t>(ws, L.red_self) : nullptr, red_start, lb, kinds,
+                            p->sym ? at<int32_t>(ws, L.mirror) : nullptr, p->sym ? at<int32_t>(ws, L.bslot) : nullptr,
+                            lb2, p->part_cap));
     P2P_LAUNCH_CHECK();
     if (red) {
         const int sms = num_sms();
@@ -384,7 +473,8 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
                                             p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr, p->edge, red_start,
                                             hdr, p->red_cap,
                                             at<float4>(ws, L.red_src),
-                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr));
+                                            (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr,
+                                            kinds));
         P2P_LAUNCH_CHECK();
     } else if (is_pairtask(p->layout)) {
         return pairtask_restructure(p, ws, words, s);

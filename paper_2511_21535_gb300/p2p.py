@@ -17,14 +17,16 @@ from . import build as _build
 GRAVITY, HELMHOLTZ = 0, 1
 LAYOUTS = {"indirect": 0, "redundant": 1, "auto": 2, "pairtask": 3, "symmetric": 4}
 PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING, PLAN_ADJOINT, PLAN_PERIODIC = 0x1, 0x2, 0x4, 0x8, 0x10
+PLAN_SYMMETRIC = 0x20
 FLAG_DOMAIN, FLAG_TIMEOUT, FLAG_CAPACITY, FLAG_LATTICE = 0x1, 0x2, 0x4, 0x8
 
 ARRAYS = {"perm": (0, torch.int32), "box_key": (1, torch.int32), "box_start": (2, torch.int32),
           "nbr_start": (3, torch.int32), "nbr_idx": (4, torch.int32), "red_start": (5, torch.int32),
           "red_self": (6, torch.int32), "gather_idx": (7, torch.int32), "sorted_key": (8, torch.int32),
           "nbr_img": (9, torch.int32), "ent_box": (10, torch.int32), "pt_start": (11, torch.int32),
-          "part_start": (12, torch.int32), "task_kind": (13, torch.int32), "mirror": (14, torch.int32)}
-COUNTERS = ("n_boxes", "n_nbr", "flags", "total_src", "pairs", "n_items")
+          "part_start": (12, torch.int32), "task_kind": (13, torch.int32), "mirror": (14, torch.int32),
+          "bslot": (15, torch.int32)}
+COUNTERS = ("n_boxes", "n_nbr", "flags", "total_src", "pairs", "n_items", "evals")
 PHASES = ("tree", "restructure", "kernel", "operator")
 
 EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_destroy",
@@ -155,8 +157,8 @@ class Plan:
 
     def __init__(self, kind: str, n: int, level: int, lo, edge: float, nrhs: int = 1,
                  layout: str = "redundant", gather_map: bool = False, plain_fp32: bool = False,
-                 timing: bool = False, adjoint: bool = False, periodic: bool = False, device=None,
-                 workspace: torch.Tensor | None = None):
+                 timing: bool = False, adjoint: bool = False, periodic: bool = False, symmetric: bool = False,
+                 device=None, workspace: torch.Tensor | None = None):
         lib = load()
         self.kind = kind
         self.n = int(n)
@@ -164,10 +166,11 @@ class Plan:
         self.level = int(level)
         self.layout = layout
         self.periodic = bool(periodic)
+        self.symmetric = bool(symmetric)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         flags = (PLAN_GATHER_MAP if gather_map else 0) | (PLAN_PLAIN_FP32 if plain_fp32 else 0) | \
                 (PLAN_TIMING if timing else 0) | (PLAN_ADJOINT if adjoint else 0) | \
-                (PLAN_PERIODIC if periodic else 0)
+                (PLAN_PERIODIC if periodic else 0) | (PLAN_SYMMETRIC if symmetric else 0)
         lo_arr = (ctypes.c_float * 3)(*[float(v) for v in lo])
         h = ctypes.c_void_p()
         kid = {"gravity": GRAVITY, "helmholtz": HELMHOLTZ}[kind]

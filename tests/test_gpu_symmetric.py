@@ -201,3 +201,135 @@ def test_symmetric_refusals(dev):
     with pytest.raises(p2p.P2PError) as e:
         plan.gravity(g.eps)
     assert e.value.status == 5
+
+
+# ---------------------------------------------------------------------------
+# symmetric evaluation on the target-owned layouts (P2P_PLAN_SYMMETRIC)
+# ---------------------------------------------------------------------------
+
+def expected_flag_arrays(t):
+    """Kinds, mirrors and source-sum slots of a symmetric plan, from the tree."""
+    kinds, mirror, _, _ = expected_tasks(t)
+    ni = t["nbr_idx"].astype(np.int64)
+    occ = np.diff(t["box_start"].astype(np.int64))
+    bsz = np.where(kinds == MUTUAL, occ[ni], 0)
+    bslot = np.concatenate([[0], np.cumsum(bsz)])[:-1]
+    return kinds, mirror, bslot, int(bsz.sum())
+
+
+def run_flag(prob, dev, layout, group=None, periodic=False):
+    plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
+                    periodic=periodic, symmetric=True, device=dev)
+    if group:
+        plan.set_tuning(2, 64, 0, group)
+    pos = torch.from_numpy(prob.pos).to(dev)
+    plan.tree_build(pos)
+    plan.restructure(pos, torch.from_numpy(prob.strength).to(dev))
+    if prob.kind == "gravity":
+        phi, acc = plan.gravity(prob.eps)
+        torch.cuda.synchronize()
+        return plan, (phi.cpu().numpy(), acc.cpu().numpy())
+    u = plan.helmholtz(prob.k)
+    torch.cuda.synchronize()
+    return plan, u.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+def test_symmetric_flag_structures(dev, name, layout):
+    prob = CASES[name]()
+    plan, _ = run_flag(prob, dev, layout)
+    t = oracle.tree(prob.pos, prob.level, prob.lo, prob.edge)
+    kinds, mirror, bslot, btotal = expected_flag_arrays(t)
+    E = t["n_nbr"]
+    c = plan.counters(check=True)
+    np.testing.assert_array_equal(plan.array("task_kind", E).cpu().numpy(), kinds)
+    got_m = plan.array("mirror", E).cpu().numpy()
+    np.testing.assert_array_equal(got_m[kinds == NONE], mirror[kinds == NONE])
+    got_b = plan.array("bslot", E).cpu().numpy()
+    np.testing.assert_array_equal(got_b[kinds == MUTUAL], bslot[kinds == MUTUAL])
+    assert c["pairs"] == oracle.pair_count(prob.pos, prob.level, prob.lo, prob.edge)
+    # evaluations: every ordered pair except the mirror entries' (evaluated by the mutual side)
+    occ = np.diff(t["box_start"].astype(np.int64))
+    ent = np.repeat(np.arange(t["n_boxes"]), np.diff(t["nbr_start"]))
+    ni = t["nbr_idx"].astype(np.int64)
+    assert c["evals"] == int((occ[ent] * occ[ni])[kinds != NONE].sum()) - prob.n
+    if layout == "redundant":
+        assert c["total_src"] == int(occ[ni][kinds != NONE].sum())
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+@pytest.mark.parametrize("group", [1, 2, 4])
+def test_symmetric_flag_parity(dev, name, layout, group):
+    prob = CASES[name]()
+    _, out = run_flag(prob, dev, layout, group)
+    if prob.kind == "gravity":
+        ophi, oacc, _ = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps)
+        phi, acc = out
+        assert np.all(np.isfinite(phi)) and np.all(np.isfinite(acc))
+        if prob.n > 1:
+            assert rel_l2(phi, ophi) <= TOL_REAL and rel_l2(acc, oacc) <= TOL_REAL
+    else:
+        ou, _ = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k)
+        assert np.all(np.isfinite(out))
+        assert rel_l2(out, ou) <= TOL_COMPLEX
+
+
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+def test_symmetric_flag_periodic(dev, layout):
+    prob = wl.uniform_gravity(n=20000, level=4, seed=6)
+    _, (phi, acc) = run_flag(prob, dev, layout, periodic=True)
+    ophi, oacc, _ = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps, periodic=True)
+    assert rel_l2(phi, ophi) <= TOL_REAL and rel_l2(acc, oacc) <= TOL_REAL
+    hprob = wl.grid_helmholtz(edge_points=16, nrhs=2, seed=7)
+    _, u = run_flag(hprob, dev, layout, periodic=True)
+    ou, _ = oracle.helmholtz(hprob.pos, hprob.strength, hprob.level, hprob.lo, hprob.edge, hprob.k, periodic=True)
+    assert rel_l2(u, ou) <= TOL_COMPLEX
+
+
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+def test_symmetric_flag_grid_64_full(dev, layout):
+    prob = wl.grid_helmholtz()
+    plan, u = run_flag(prob, dev, layout)
+    ou, pairs = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k)
+    assert plan.counters(check=True)["pairs"] == pairs
+    assert rel_l2(u, ou) <= TOL_COMPLEX
+
+
+def test_symmetric_flag_deterministic_and_momentum(dev):
+    prob = wl.uniform_gravity(n=30000, level=4, seed=10)
+    _, (p1, a1) = run_flag(prob, dev, "redundant")
+    _, (p2, a2) = run_flag(prob, dev, "redundant")
+    np.testing.assert_array_equal(p1, p2)
+    np.testing.assert_array_equal(a1, a2)
+    f = a1.astype(np.float64) * prob.strength.astype(np.float64)[:, None]
+    assert np.abs(f.sum(axis=0)).max() <= 1e-6 * np.abs(f).sum()
+
+
+def test_symmetric_flag_plummer_sampled(dev):
+    prob = wl.plummer_gravity(n=1 << 20, level=6)
+    plan, (phi, acc) = run_flag(prob, dev, "redundant")
+    tg = np.random.default_rng(3).choice(prob.n, 3000, replace=False)
+    ophi, oacc, _ = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps, targets=tg)
+    assert rel_l2(phi[tg], ophi) <= TOL_REAL and rel_l2(acc[tg], oacc) <= TOL_REAL
+
+
+def test_symmetric_flag_refusals(dev):
+    for kw in (dict(kind="helmholtz", nrhs=3, layout="redundant"), dict(kind="gravity", layout="pairtask"),
+               dict(kind="gravity", layout="redundant", adjoint=True)):
+        kind = kw.pop("kind")
+        with pytest.raises(p2p.P2PError) as e:
+            p2p.Plan(kind, 100, 2, (0, 0, 0), 1.0, symmetric=True, device=dev, **kw)
+        assert e.value.status == 1
+    prob = wl.grid_helmholtz(edge_points=16)
+    plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, symmetric=True, device=dev)
+    with pytest.raises(p2p.P2PError) as e:
+        plan.set_grid(wl.SPACING, 4)
+    assert e.value.status == 5
+    pos = torch.from_numpy(prob.pos).to(dev)
+    q = torch.from_numpy(prob.strength).to(dev)
+    plan.tree_build(pos)
+    with pytest.raises(p2p.P2PError) as e:
+        plan.helmholtz_adjoint(prob.k, pos, q)
+    assert e.value.status == 5
