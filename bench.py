@@ -194,9 +194,7 @@ def run_gpu(args, rank, world, local_rank):
     prob = make_problem(args.workload, args.periodic)
     layout = args.layout
     # symmetric evaluation applies to the target-owned layouts in direct mode with <= 2 right-hand sides
-    # ("auto": the Helmholtz kernel, where it measured faster; the gravity workloads' large boxes gain little)
-    want = args.evaluation == "symmetric" or (args.evaluation == "auto" and prob.kind == "helmholtz")
-    symmetric = (want and not args.pattern and layout in ("redundant", "indirect")
+    symmetric = (args.evaluation == "symmetric" and not args.pattern and layout in ("redundant", "indirect")
                  and (prob.kind == "gravity" or prob.nrhs <= 2))
     plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
                     timing=True, periodic=args.periodic, symmetric=symmetric, device=dev)
@@ -405,6 +403,104 @@ def run_gpu(args, rank, world, local_rank):
 
 
 # ---------------------------------------------------------------------------
+# secondary measurements of the default line
+# ---------------------------------------------------------------------------
+
+def timed_graph_steps(step, steps: int, flush, stream):
+    """CUDA-graph replay of `step`, mean ms per replay over `steps` (L2 flushed between)."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(3):
+        flush.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def evaluation_variant(prob, layout: str, dev, steps: int, mufu_peak: float):
+    """The same workload with symmetric evaluation (each pair of a small box pair once)."""
+    import torch
+    from paper_2511_21535_gb300 import p2p
+    plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
+                    timing=True, periodic=bool(prob.extra.get("periodic")), symmetric=True, device=dev)
+    pos = torch.from_numpy(prob.pos).to(dev)
+    strength = torch.from_numpy(prob.strength).to(dev)
+    u = torch.empty(prob.nrhs, prob.n, dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        plan.tree_build(pos)
+        plan.restructure(pos, strength)
+        plan.helmholtz(prob.k, u)
+
+    ms = timed_graph_steps(step, steps, flush, torch.cuda.current_stream())
+    t = plan.timing()
+    c = plan.counters(check=True)
+    evals_per_s = c["evals"] / (t["kernel"] * 1e-3)
+    return {"evaluation": "symmetric", "layout": layout, "value": c["pairs"] * prob.nrhs / (ms * 1e-3),
+            "unit": "pairs/s", "ms_per_step": ms, "kernel_ms": t["kernel"],
+            "phases_ms": t, "evaluations_per_launch": c["evals"],
+            "roofline": {"pipe": "mufu", "achieved": evals_per_s / 1e9, "peak": mufu_peak / 1e9,
+                         "unit": "G evaluations/s", "frac": evals_per_s / mufu_peak}}
+
+
+def dbim_forward_adjoint(dev, steps: int, edge_points: int = 128):
+    """Differentiable 128^3 configuration: L = ||P(chi u_inc) - d||^2 and dL/dchi through
+    the autograd wrapper (forward P2P + hand-written adjoint P2P), per step."""
+    import torch
+    from paper_2511_21535_gb300 import p2p
+    prob = wl.diff_helmholtz(edge_points=edge_points)
+    plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, nrhs=1, device=dev)
+    pos = torch.from_numpy(prob.pos).to(dev)
+    uinc = torch.from_numpy(prob.extra["uinc"]).to(dev)
+    with torch.no_grad():
+        d = p2p.helmholtz_p2p(pos, (torch.from_numpy(prob.extra["chi2"]).to(dev) * uinc)[None], plan, prob.k)
+    chi0 = torch.from_numpy(prob.extra["chi"]).to(dev)
+
+    def step():
+        chi = chi0.clone().requires_grad_(True)
+        u = p2p.helmholtz_p2p(pos, (chi * uinc)[None], plan, prob.k)
+        loss = torch.sum(torch.abs(u - d) ** 2)
+        loss.backward()
+        return chi.grad
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        g = step()
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    pairs = plan.counters(check=True)["pairs"]
+    return {"workload": f"{edge_points}^3 grid, contrast sphere r = 0.3 of the extent, plane wave; "
+                        "L = ||P(chi u_inc) - d||^2, dL/dchi by the adjoint kernel",
+            "n": prob.n, "ms_per_step": ms, "pairs_per_step": 2 * pairs,
+            "value": 2 * pairs / (ms * 1e-3), "unit": "pairs/s (forward + adjoint)",
+            "grad_finite": bool(torch.isfinite(g).all())}
+
+
+# ---------------------------------------------------------------------------
 # batched forward + adjoint (64 uneven grid instances x 8 RHS) vs plain launches
 # ---------------------------------------------------------------------------
 
@@ -588,10 +684,11 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--pattern", action="store_true", help="tabulated-G kernel for grid workloads")
     ap.add_argument("--periodic", action="store_true", help="toroidal neighbourhoods (wrapped boxes)")
-    ap.add_argument("--evaluation", default="auto", choices=["auto", "symmetric", "one-sided"],
-                    help="symmetric: each pair of box pairs with a box of <= 64 particles is evaluated once for "
-                         "both particles; one-sided: every ordered pair is evaluated (pattern mode, pair tasks "
-                         "and more than two right-hand sides are one-sided); auto: symmetric for Helmholtz")
+    ap.add_argument("--evaluation", default="one-sided", choices=["one-sided", "symmetric"],
+                    help="one-sided: every ordered pair is evaluated (the paper's operator); symmetric: each pair "
+                         "of box pairs with a box of <= 64 particles is evaluated once for both particles (pattern "
+                         "mode, pair tasks and more than two right-hand sides stay one-sided).  The default line "
+                         "also reports the symmetric evaluation of a Helmholtz workload")
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -622,7 +719,13 @@ def main():
     res, prob = run_gpu(args, rank, world, local_rank)
     if not args.no_batched:
         import torch as _t
-        res["batched"] = batched_vs_plain(_t.device("cuda", local_rank), 10)
+        dev = _t.device("cuda", local_rank)
+        res["batched"] = batched_vs_plain(dev, 10)
+        res["adjoint"] = dbim_forward_adjoint(dev, 10)
+        if (prob.kind == "helmholtz" and prob.nrhs <= 2 and args.evaluation == "one-sided" and not args.pattern
+                and args.layout in ("redundant", "indirect")):
+            mufu_peak = res["roofline"]["peak"] * 1e9
+            res["symmetric"] = evaluation_variant(prob, args.layout, dev, 100, mufu_peak)
     if rank == 0:
         if not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
