@@ -400,7 +400,9 @@ __global__ void __launch_bounds__(256) k_items_fill(Units U, Header* hdr, int tt
     }
 }
 
-// Redundant gather: one warp per target box copies the records of each
+constexpr int kGatherParts = 4;
+
+// Redundant gather: kGatherParts warps per target box copy the records of each
 // neighbour box, in neighbour order, into the box's stream (16-byte words,
 // coalesced), and optionally the sorted index of every copied record.  With
 // periodic boundaries a wrapped neighbour's records are copied with their
@@ -426,9 +428,22 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t nb = hdr->n_boxes;
-    for (int64_t b = warp; b < nb; b += nwarps) {
-        int64_t out = red_start[b];
-        for (int32_t e = nbr_start[b]; e < nbr_start[b + 1]; ++e) {
+    // kGatherParts warps per box, each copying a contiguous chunk of its entries
+    for (int64_t w = warp; w < (int64_t)nb * kGatherParts; w += nwarps) {
+        const int64_t b = w / kGatherParts;
+        const int part = (int)(w % kGatherParts);
+        const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+        const int32_t lo = part * ne / kGatherParts, hi = (part + 1) * ne / kGatherParts;
+        // the chunk's offset in the stream: the streamed counts of the entries before it
+        int32_t before = 0;
+        if (lane < lo && !(task_kind && task_kind[e0 + lane] == kTaskNone)) {
+            const int32_t c = nbr_idx[e0 + lane];
+            before = box_start[c + 1] - box_start[c];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(FULL, before, o);
+        int64_t out = (int64_t)red_start[b] + before;
+        for (int32_t e = e0 + lo; e < e0 + hi; ++e) {
             if (task_kind && task_kind[e] == kTaskNone) continue;   // symmetric: the mirror's mutual item covers it
             const int32_t c = nbr_idx[e];
             const int32_t s0 = box_start[c];
