@@ -174,6 +174,7 @@ struct HelmSymOp {
     __device__ __forceinline__ void body_mut(const float4* __restrict__ sm, int cnt) {
         const int lane = threadIdx.x & 31, sg = lane % SP;
         const int u_me = ((lane >> 4) << 1) | ((lane >> 3) & 1);
+#pragma unroll 2
         for (int g = 0; g < cnt; g += 4 * SP) {
             float vr[4][R], vi[4][R];
 #pragma unroll
