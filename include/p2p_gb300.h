@@ -90,7 +90,9 @@ typedef enum {
     P2P_ERR_UNSUPPORTED = 5,   /* valid request this build does not handle       */
     P2P_ERR_DOMAIN = 6,        /* a position lies outside the boxing domain      */
     P2P_ERR_WORKSPACE = 7,     /* workspace missing, misaligned or too small     */
-    P2P_ERR_STATE = 8          /* call out of order (e.g. operator before tree)  */
+    P2P_ERR_STATE = 8,         /* call out of order (e.g. operator before tree)  */
+    P2P_ERR_BOUNDS = 9         /* checked builds: an index check failed and the  */
+                               /* access was skipped (results are incomplete)    */
 } p2p_status;
 
 typedef enum { P2P_GRAVITY = 0, P2P_HELMHOLTZ = 1 } p2p_kernel_kind;
@@ -125,6 +127,7 @@ typedef enum {
                                    /* array; the affected step was skipped          */
 #define P2P_FLAG_LATTICE  0x8u     /* pattern mode: a point is off the grid lattice */
                                    /* or its box; the operator call was skipped     */
+#define P2P_FLAG_BOUNDS   0x10u    /* checked builds: an index was outside its array */
 
 /* limits of this build */
 #define P2P_MAX_N      (1LL << 26) /* particles per plan (27 n must fit in int32)   */
@@ -364,6 +367,18 @@ int p2p_batch_counters(const p2p_batch* batch, const void* ws, int64_t* out, voi
  * is a caller-owned device uint32 (overwritten).  Synchronises the stream.
  */
 int p2p_selftest_bounded_wait(uint64_t limit_ns, uint32_t* flags_dev, void* stream);
+
+/*
+ * Testing aids.
+ * p2p_build_checked: 1 if this library was built with device index checks
+ * (P2P_CHECKED: every work item's ranges, slots and output indices, the
+ * stream and partial-slot writes are checked; a failed check sets
+ * P2P_FLAG_BOUNDS and skips the access instead of faulting), else 0.
+ * p2p_fail_host_allocs: the next `count` host allocations of plan and batch
+ * creation fail (they return P2P_ERR_OOM); 0 clears.  Returns P2P_OK.
+ */
+int p2p_build_checked(void);
+int p2p_fail_host_allocs(int count);
 
 /* identifiers of workspace arrays for p2p_plan_array */
 typedef enum {

@@ -111,7 +111,7 @@ int p2p_batch_create(p2p_batch** out, int kind, int n_instances, const int64_t* 
     if (flags & ~(P2P_PLAN_PLAIN_FP32)) return P2P_ERR_INVALID_ARG;
     const int total_rhs = pair ? 2 * nrhs : nrhs;
     if (nrhs < 1 || total_rhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
-    p2p_batch* h = new (std::nothrow) p2p_batch;
+    p2p_batch* h = host_alloc_should_fail() ? nullptr : new (std::nothrow) p2p_batch;
     if (!h) return P2P_ERR_OOM;
     Batch& b = h->b;
     b.kind = kind;
@@ -384,6 +384,7 @@ int p2p_batch_counters(const p2p_batch* h, const void* ws, int64_t* out, void* s
     out[P2P_CTR_PAIRS] = (int64_t)hdr.pairs_nS - b.N;
     out[P2P_CTR_N_ITEMS] = hdr.n_items;
     out[P2P_CTR_EVALS] = (int64_t)hdr.evals_nS - b.N;
+    if (hdr.flags & P2P_FLAG_BOUNDS) return P2P_ERR_BOUNDS;
     if (hdr.flags & P2P_FLAG_TIMEOUT) return P2P_ERR_TIMEOUT;
     return P2P_OK;
 }

@@ -16,6 +16,15 @@ namespace p2p {
 static std::atomic<long long> g_launches{0};
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+static std::atomic<int> g_fail_allocs{0};
+bool host_alloc_should_fail() {
+    int v = g_fail_allocs.load();
+    while (v > 0) {
+        if (g_fail_allocs.compare_exchange_weak(v, v - 1)) return true;
+    }
+    return false;
+}
+
 bool pdl_enabled() {
     static const bool on = [] {
         const char* v = getenv("P2P_NO_PDL");
@@ -131,12 +140,18 @@ LoopArgs loop_args(const Plan* p, void* ws, int words) {
     // the indirect layout shifts the targets per neighbour range
     a.nbr_img = (p->periodic && p->layout == P2P_LAYOUT_INDIRECT) ? at<int32_t>(ws, L.nbr_img) : nullptr;
     a.edge = p->edge;
+    a.rec_cap = p->n;
+    a.red_cap = p->red_cap;
+    a.items_cap = p->items_cap;
+    a.box_cap = p->box_cap;
+    a.n = p->n;
     a.ent_box = a.pt_start = a.part_start = a.task_kind = nullptr;
     a.part = nullptr;
     a.part_cap = 0;
     if (is_pairtask(p->layout)) {
         // targets and sources both come from the task stream
         a.rec = a.red = at<float4>(ws, L.red_src);
+        a.rec_cap = p->red_cap;
         a.ent_box = at<int32_t>(ws, L.ent_box);
         a.pt_start = at<int32_t>(ws, L.pt_start);
         a.part_start = at<int32_t>(ws, L.part_start);
@@ -242,11 +257,19 @@ const char* p2p_status_string(int status) {
         case P2P_ERR_DOMAIN: return "position outside the boxing domain";
         case P2P_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
         case P2P_ERR_STATE: return "call out of order";
+        case P2P_ERR_BOUNDS: return "index check failed (checked build)";
         default: return "unknown status";
     }
 }
 
 int p2p_abi_version(void) { return P2P_ABI_VERSION; }
+
+int p2p_build_checked(void) { return kChecked ? 1 : 0; }
+
+int p2p_fail_host_allocs(int count) {
+    g_fail_allocs.store(count > 0 ? count : 0);
+    return P2P_OK;
+}
 
 int64_t p2p_launch_count(void) { return (int64_t)g_launches.load(); }
 
@@ -257,7 +280,7 @@ int p2p_plan_create(p2p_plan** out, int kind, int64_t n, int level, const float*
     Plan tmp{};
     int st = plan_init(&tmp, kind, n, level, lo, edge, nrhs, layout, flags);
     if (st) return st;
-    p2p_plan* h = new (std::nothrow) p2p_plan;
+    p2p_plan* h = host_alloc_should_fail() ? nullptr : new (std::nothrow) p2p_plan;
     if (!h) return P2P_ERR_OOM;
     h->p = tmp;
     Plan* p = &h->p;
@@ -565,6 +588,7 @@ int p2p_read_counters(const p2p_plan* h, const void* ws, int64_t* out, void* str
     out[P2P_CTR_PAIRS] = (int64_t)hdr.pairs_nS - h->p.n;
     out[P2P_CTR_N_ITEMS] = hdr.n_items;
     out[P2P_CTR_EVALS] = (int64_t)hdr.evals_nS - h->p.n;
+    if (hdr.flags & P2P_FLAG_BOUNDS) return P2P_ERR_BOUNDS;
     if (hdr.flags & P2P_FLAG_TIMEOUT) return P2P_ERR_TIMEOUT;
     if (hdr.flags & P2P_FLAG_DOMAIN) return P2P_ERR_DOMAIN;
     if (hdr.flags & (P2P_FLAG_CAPACITY | P2P_FLAG_LATTICE)) return P2P_ERR_INVALID_ARG;

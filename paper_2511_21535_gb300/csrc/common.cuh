@@ -100,6 +100,22 @@ struct Plan {
 // launch accounting
 void count_launch(int k = 1);
 
+// host allocation failure injection (testing): true while failures are pending
+bool host_alloc_should_fail();
+
+// Checked builds (P2P_CHECKED): index checks that record P2P_FLAG_BOUNDS and
+// let the caller skip the access instead of faulting.
+#ifdef P2P_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+__device__ __forceinline__ bool dcheck(bool cond, Header* hdr) {
+    if (!kChecked || cond) return true;
+    atomicOr(&hdr->flags, P2P_FLAG_BOUNDS);
+    return false;
+}
+
 // error helper
 #define P2P_CUDA_TRY(expr)                                  \
     do {                                                    \

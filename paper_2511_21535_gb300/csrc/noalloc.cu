@@ -160,6 +160,11 @@ extern "C" int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t 
     a.hdr = at<Header>(ws, p.L.header);
     a.nbr_img = nullptr;
     a.edge = p.edge;
+    a.rec_cap = p.n;
+    a.red_cap = p.red_cap;
+    a.items_cap = p.items_cap;
+    a.box_cap = p.box_cap;
+    a.n = p.n;
     a.ent_box = a.pt_start = a.part_start = nullptr;
     a.part = nullptr;
     a.part_cap = 0;

@@ -63,6 +63,12 @@ struct LoopArgs {
     int64_t part_cap;          // pair tasks: slots per right-hand side
     const int32_t* task_kind;  // symmetric tasks: 0 none, 1 self, 2 mutual, 3 one-sided; else nullptr
     const int32_t* bslot;      // symmetric plans (target-owned layouts): source-sum slots per entry
+    // capacities (checked builds verify every item against them)
+    int64_t rec_cap;           // records in rec
+    int64_t red_cap;           // records in red
+    int64_t items_cap;         // work items
+    int64_t box_cap;           // boxes
+    int64_t n;                 // particles (output indices)
 };
 
 
@@ -148,9 +154,18 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
             if (abort_flag[group]) item = n_items;
         }
         if (item >= n_items) break;
+        if constexpr (kChecked) {
+            if (!dcheck(item < a.items_cap, a.hdr)) break;   // item is the same in every warp of the group
+        }
         const int2 it = a.items[item];
         const int t0 = it.y;
+        if constexpr (kChecked) {
+            if (!dcheck(it.x >= 0 && it.x < (pairtask ? a.hdr->n_nbr : a.hdr->n_boxes), a.hdr)) continue;
+        }
         const int b = pairtask ? a.ent_box[it.x] : it.x;
+        if constexpr (kChecked) {
+            if (!dcheck(b >= 0 && b < a.hdr->n_boxes, a.hdr)) continue;
+        }
         const int bs = a.box_start[b];
         const int nbox = a.box_start[b + 1] - bs;
         const int nt = min(32 * K, nbox - t0);
@@ -204,6 +219,17 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
                 rs = a.red_start[b] + inc - rc;
                 self_base = a.red_start[b] + a.red_self[b];
             }
+        }
+        if constexpr (kChecked) {
+            // every range inside the buffer it is copied from, the targets and slots inside theirs
+            const int64_t bufcap = redundant ? a.red_cap : a.rec_cap;
+            bool good = b < a.box_cap && t0 >= 0 && nt > 0 &&
+                        tgt >= 0 && (int64_t)tgt + nt <= (pairtask ? a.red_cap : a.rec_cap);
+            const bool range_ok = lane >= nr || rc == 0 || (rs >= 0 && (int64_t)rs + rc <= bufcap);
+            const bool slot_ok = !sym || lane >= nr || rk != kTaskMutual || (rb >= 0 && (int64_t)rb + rc <= a.part_cap);
+            good = __all_sync(FULL, range_ok && slot_ok) && good;
+            if (pairtask) good = good && slot + nt <= a.part_cap && (!mutual || slot + nbox + rc <= a.part_cap);
+            if (!dcheck(good, a.hdr)) continue;   // the same decision in every warp of the group
         }
         const int sw_lo = self_base + t0, sw_hi = sw_lo + nt;
         op.begin(tgt, nt, sw_lo, lane);

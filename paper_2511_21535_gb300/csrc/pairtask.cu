@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(256) k_pt_entries(const int32_t* __restrict__ 
                                                    int32_t* __restrict__ mirror) {
     pdl_wait();
     pdl_release();
+    if (hdr->flags & P2P_FLAG_CAPACITY) return;   // an inconsistent imported structure
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(256) k_pt_gather(const float4* __restrict__ re
     pdl_release();
     const int lane = threadIdx.x & 31;
     // an imported, inconsistent neighbour relation can exceed the capacities
-    if (hdr->total_src < 0 || (int64_t)hdr->total_src > cap || hdr->part_total < 0 ||
+    if ((hdr->flags & P2P_FLAG_CAPACITY) || hdr->total_src < 0 || (int64_t)hdr->total_src > cap || hdr->part_total < 0 ||
         (int64_t)hdr->part_total > part_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);
         return;

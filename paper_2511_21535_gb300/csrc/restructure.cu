@@ -27,12 +27,12 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 
 __global__ void k_records_gravity(const float* __restrict__ pos, const float* __restrict__ mass,
                                   const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec,
-                                  unsigned long long* __restrict__ lb, int64_t lb_words) {
+                                  unsigned long long* __restrict__ lb, int64_t lb_words, const Header* __restrict__ hdr) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
-    if (s >= n) return;
+    if (s >= n || (hdr->flags & P2P_FLAG_CAPACITY)) return;   // an inconsistent imported structure
     const int64_t i = perm[s];
     rec[s] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass[i]);
 }
@@ -91,7 +91,7 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
-    if (s >= n) return;
+    if (s >= n || (hdr->flags & P2P_FLAG_CAPACITY)) return;   // an inconsistent imported structure
     const int64_t i = perm[s];
     float4* r = rec + s * words;
     float w = 0.0f;
@@ -117,12 +117,12 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
 __global__ void k_records_helm_adjoint(const float* __restrict__ pos, const float2* __restrict__ q,
                                        const float2* __restrict__ gbar, const int32_t* __restrict__ perm, int64_t n,
                                        int nrhs, int words, float4* __restrict__ rec,
-                                  unsigned long long* __restrict__ lb, int64_t lb_words) {
+                                  unsigned long long* __restrict__ lb, int64_t lb_words, const Header* __restrict__ hdr) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
-    if (s >= n) return;
+    if (s >= n || (hdr->flags & P2P_FLAG_CAPACITY)) return;   // an inconsistent imported structure
     const int64_t i = perm[s];
     float4* r = rec + s * words;
     const int half = (nrhs + 1) / 2;
@@ -141,12 +141,12 @@ __global__ void k_records_helm_adjoint(const float* __restrict__ pos, const floa
 __global__ void k_records_grav_adjoint(const float* __restrict__ pos, const float* __restrict__ mass,
                                        const float* __restrict__ gphi, const float* __restrict__ gacc,
                                        const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec,
-                                  unsigned long long* __restrict__ lb, int64_t lb_words) {
+                                  unsigned long long* __restrict__ lb, int64_t lb_words, const Header* __restrict__ hdr) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
-    if (s >= n) return;
+    if (s >= n || (hdr->flags & P2P_FLAG_CAPACITY)) return;   // an inconsistent imported structure
     const int64_t i = perm[s];
     rec[2 * s] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass[i]);
     rec[2 * s + 1] = make_float4(gphi[i], gacc[3 * i], gacc[3 * i + 1], gacc[3 * i + 2]);
@@ -193,12 +193,15 @@ __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ b
     __shared__ int32_t pre_s[kBoxTile + 1], bpre_s[kBoxTile + 1];
     __shared__ unsigned long long pairs_s, evals_s;
     if (threadIdx.x == 0) {
-        tile_s = lb_ticket(lb);
+        // a rejected structure: the block takes no tile (later tiles wait only on taken ones);
+        // one thread reads the flag, which other blocks of this launch may be setting
+        tile_s = (hdr->flags & P2P_FLAG_CAPACITY) ? -1 : lb_ticket(lb);
         pairs_s = 0ull;
         evals_s = 0ull;
     }
     __syncthreads();
     const int tile = tile_s;
+    if (tile < 0) return;
     const int32_t nb = hdr->n_boxes;
     const int64_t b0 = (int64_t)tile * kBoxTile;
     if (b0 >= nb) return;   // past the last box (whole block): no later tile waits on it
@@ -344,6 +347,7 @@ __device__ __forceinline__ void unit_shape(const Units& U, int64_t u, int32_t& o
 __global__ void __launch_bounds__(256) k_items_count(Units U, Header* hdr, int tt) {
     pdl_wait();
     pdl_release();
+    if (hdr->flags & P2P_FLAG_CAPACITY) return;   // no items: the operator does nothing
     __shared__ int32_t cls[kCostClasses];
     __shared__ int32_t items_s;
     for (int c = threadIdx.x; c < kCostClasses; c += blockDim.x) cls[c] = 0;
@@ -368,6 +372,7 @@ __global__ void __launch_bounds__(256) k_items_count(Units U, Header* hdr, int t
 __global__ void __launch_bounds__(256) k_items_fill(Units U, Header* hdr, int tt, int2* __restrict__ items) {
     pdl_wait();
     pdl_release();
+    if (hdr->flags & P2P_FLAG_CAPACITY) return;
     __shared__ int32_t cls_base[kCostClasses];
     __shared__ int32_t local_cnt[kCostClasses];
     __shared__ int32_t local_cur[kCostClasses];
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
     pdl_release();
     const int lane = threadIdx.x & 31;
     // an imported, inconsistent neighbour relation can exceed the stream capacity
-    if (hdr->total_src < 0 || (int64_t)hdr->total_src > red_cap) {
+    if ((hdr->flags & P2P_FLAG_CAPACITY) || hdr->total_src < 0 || (int64_t)hdr->total_src > red_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);
         return;
     }
@@ -507,7 +512,7 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
     const int64_t lbc_words = lr.words - lr.stats;
     if (p->kind == P2P_GRAVITY) {
         P2P_CUDA_TRY(launch_pdl(k_records_gravity, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float*>(strength),
-                                perm, n, rec, lbc, lbc_words));
+                                perm, n, rec, lbc, lbc_words, at<Header>(ws, L.header)));
     } else {
         const int split = strength2 ? p->split : p->nrhs;
         LatticeArgs lat{};
@@ -552,13 +557,13 @@ int restructure_adjoint(Plan* p, const float* pos, const void* a, const void* b,
         P2P_CUDA_TRY(launch_pdl(k_records_grav_adjoint, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float*>(a),
                                                                  static_cast<const float*>(b),
                                                                  static_cast<const float*>(c), perm, n, rec, lbc,
-                                                                 lbc_words));
+                                                                 lbc_words, at<Header>(ws, L.header)));
     } else {
         w = helmholtz_adjoint_words(p->nrhs);
         if (w > p->rec_alloc_words) return P2P_ERR_UNSUPPORTED;
         P2P_CUDA_TRY(launch_pdl(k_records_helm_adjoint, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float2*>(a),
                                                                  static_cast<const float2*>(b), perm, n, p->nrhs, w,
-                                                                 rec, lbc, lbc_words));
+                                                                 rec, lbc, lbc_words, at<Header>(ws, L.header)));
     }
     P2P_LAUNCH_CHECK();
     p->src_ready = 0;   // the forward records are overwritten

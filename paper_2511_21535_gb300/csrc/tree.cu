@@ -392,6 +392,35 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // import of a caller-built structure
 // ---------------------------------------------------------------------------
+// An imported structure is checked before anything indexes through it:
+// perm in [0, n), box bounds strictly increasing from 0 to n, neighbour
+// bounds non-decreasing from 0 to n_nbr with at most 27 entries a box, and
+// neighbour indices in [0, n_boxes).  A violation sets P2P_FLAG_CAPACITY;
+// every later kernel of the plan then skips its work.
+__global__ void __launch_bounds__(256) k_validate_import(const int32_t* __restrict__ perm, int64_t n,
+                                                        const int32_t* __restrict__ box_start, int32_t nb,
+                                                        const int32_t* __restrict__ nbr_start,
+                                                        const int32_t* __restrict__ nbr_idx, int32_t ne,
+                                                        Header* hdr) {
+    pdl_wait();
+    pdl_release();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    for (int64_t i = t0; i < n; i += stride) bad |= perm[i] < 0 || perm[i] >= n;
+    for (int64_t b = t0; b <= nb; b += stride) {
+        if (b == 0) bad |= box_start[0] != 0 || nbr_start[0] != 0;
+        if (b == nb) bad |= box_start[nb] != n || nbr_start[nb] != ne;
+        if (b < nb) {
+            bad |= box_start[b + 1] <= box_start[b];
+            const int32_t d = nbr_start[b + 1] - nbr_start[b];
+            bad |= d < 0 || d > 27;
+        }
+    }
+    for (int64_t e = t0; e < ne; e += stride) bad |= nbr_idx[e] < 0 || nbr_idx[e] >= nb;
+    if (bad) atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);
+}
+
 __global__ void k_set_counts(Header* hdr, int32_t n_boxes, int32_t n_nbr) {
     pdl_wait();
     pdl_release();
@@ -414,6 +443,10 @@ int tree_import(Plan* p, const int32_t* perm, const int32_t* box_start, int32_t 
     P2P_CUDA_TRY(cudaMemcpyAsync(at<int32_t>(ws, L.nbr_idx), nbr_idx, (size_t)n_nbr * sizeof(int32_t),
                                  cudaMemcpyDeviceToDevice, s));
     P2P_CUDA_TRY(launch_pdl(k_set_counts, 1, 1, 0, s, hdr, n_boxes, n_nbr));
+    P2P_LAUNCH_CHECK();
+    P2P_CUDA_TRY(launch_pdl(k_validate_import, (unsigned)num_sms() * 4, 256, 0, s, at<int32_t>(ws, L.perm), p->n,
+                            at<int32_t>(ws, L.box_start), n_boxes, at<int32_t>(ws, L.nbr_start),
+                            at<int32_t>(ws, L.nbr_idx), n_nbr, hdr));
     P2P_LAUNCH_CHECK();
     p->tree_ready = 1;
     p->src_ready = 0;

@@ -37,7 +37,7 @@ EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_
            "p2p_batch_create", "p2p_batch_destroy", "p2p_batch_workspace_bytes", "p2p_batch_build",
            "p2p_batch_set_tuning", "p2p_batch_run", "p2p_batch_autotune", "p2p_batch_capture",
            "p2p_batch_launch", "p2p_batch_counters", "p2p_selftest_bounded_wait",
-           "p2p_plan_set_grid")
+           "p2p_plan_set_grid", "p2p_build_checked", "p2p_fail_host_allocs")
 
 
 class P2PError(RuntimeError):
@@ -50,7 +50,12 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The release library, or the checked variant when the environment sets
+    P2P_GB300_VARIANT=checked before the first load."""
+    variant = os.environ.get("P2P_GB300_VARIANT", "release")
+    if variant not in _build.VARIANTS:
+        raise ValueError(f"P2P_GB300_VARIANT={variant!r}: expected one of {sorted(_build.VARIANTS)}")
+    return _build.VARIANTS[variant][0]
 
 
 def load(build_if_missing: bool = False) -> ctypes.CDLL:
@@ -61,7 +66,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     path = library_path()
     if not os.path.exists(path):
         if build_if_missing:
-            _build.build()
+            _build.build(variants=(os.environ.get("P2P_GB300_VARIANT", "release"),))
         else:
             raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
     lib = ctypes.CDLL(path)
@@ -99,6 +104,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_batch_counters": (I, [P, P, ctypes.POINTER(I64), P]),
         "p2p_selftest_bounded_wait": (I, [ctypes.c_uint64, P, P]),
         "p2p_plan_set_grid": (I, [P, F, I]),
+        "p2p_build_checked": (I, []),
+        "p2p_fail_host_allocs": (I, [I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

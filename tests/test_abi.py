@@ -105,6 +105,43 @@ def test_workspace_layout_scales(lib):
 
 def test_status_strings(lib):
     lib.p2p_status_string.restype = ctypes.c_char_p
-    for s in range(9):
+    for s in range(10):
         assert lib.p2p_status_string(s)
     assert lib.p2p_abi_version() == 1
+
+
+def test_injected_host_allocation_failure(lib):
+    """Plan and batch creation report P2P_ERR_OOM (3) when their host
+    allocation fails, leave *out null, and work again once the injection is used up."""
+    assert lib.p2p_build_checked() == 0
+    assert lib.p2p_fail_host_allocs(1) == 0
+    st, h = _create(lib)
+    assert st == 3 and not h.value
+    st, h = _create(lib)
+    assert st == 0 and h.value
+    lib.p2p_plan_destroy(h)
+    I64, I, F = ctypes.c_int64, ctypes.c_int, ctypes.c_float
+    n, lv, lo, ed = (I64 * 2)(500, 700), (I * 2)(2, 3), (F * 6)(*([0.0] * 6)), (F * 2)(1.0, 1.0)
+    lib.p2p_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), I, I] + [ctypes.c_void_p] * 4 + [I, I, I,
+                                                                                                       ctypes.c_uint]
+    lib.p2p_batch_destroy.argtypes = [ctypes.c_void_p]
+    args = lambda b: (ctypes.byref(b), 1, 2, ctypes.cast(n, ctypes.c_void_p), ctypes.cast(lv, ctypes.c_void_p),
+                      ctypes.cast(lo, ctypes.c_void_p), ctypes.cast(ed, ctypes.c_void_p), 1, 0, 1, 0)
+    lib.p2p_fail_host_allocs(1)
+    b = ctypes.c_void_p()
+    assert lib.p2p_batch_create(*args(b)) == 3 and not b.value
+    assert lib.p2p_batch_create(*args(b)) == 0 and b.value
+    assert lib.p2p_batch_destroy(b) == 0
+    lib.p2p_fail_host_allocs(2)
+    lib.p2p_fail_host_allocs(0)                  # clears
+    st, h = _create(lib)
+    assert st == 0 and h.value
+    lib.p2p_plan_destroy(h)
+
+
+def test_checked_variant_exports_the_same_symbols():
+    path = cuda_build.build(variants=("checked",))
+    chk = ctypes.CDLL(path)
+    assert chk.p2p_build_checked() == 1
+    missing = [n for n in declared_functions() if not hasattr(chk, n)]
+    assert not missing, missing
