@@ -36,9 +36,18 @@ from paper_2511_21535_gb300 import workloads as wl  # noqa: E402
 METRIC = "P2P pair-interactions/s"
 
 
-def kernel_name(kind: str, symmetric: bool) -> str:
-    """The dominant kernel of a step: symmetric Helmholtz runs k_helmsym."""
-    return "k_helmsym" if (kind == "helmholtz" and symmetric) else f"k_{kind}"
+def kernel_name(kind: str, symmetric: bool, pattern: bool = False, tile2d: bool = False) -> str:
+    """The dominant kernel of a step: Helmholtz runs k_helmholtz_pattern in pattern mode,
+    k_helmsym for a symmetric evaluation, k_helmtile for one-sided plans of one or two
+    right-hand sides with four targets per lane (the default), else k_helmholtz."""
+    if kind == "helmholtz":
+        if pattern:
+            return "k_helmholtz_pattern"
+        if symmetric:
+            return "k_helmsym"
+        if tile2d:
+            return "k_helmtile"
+    return f"k_{kind}"
 
 
 def kernel_traffic(kernel: str, workload: str, layout: str, n: int, symmetric: bool):
@@ -363,6 +372,10 @@ def run_gpu(args, rank, world, local_rank):
     else:
         pipe, per_pair = "fp32", 13.0
         peak = pipes["fp32"] * sms * f_mhz * 1e6 / per_pair
+    # the default Helmholtz tuning for one or two right-hand sides, one-sided: four targets per lane
+    tile2d = (prob.kind == "helmholtz" and not symmetric and layout != "symmetric" and prob.nrhs <= 2
+              and args.tpl in (0, 4))
+    kname = kernel_name(prob.kind, symmetric or layout == "symmetric", args.pattern, tile2d)
     # pair evaluations the kernel performs (a symmetric plan's mutual evaluation serves two ordered pairs)
     evals = cnt.get("evals", geo_pairs) if (symmetric or layout == "symmetric") else geo_pairs
     achieved = evals / (kern_ms * 1e-3)
@@ -382,11 +395,11 @@ def run_gpu(args, rank, world, local_rank):
         "config": workload_config(prob, layout, args.pattern, symmetric),
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
-        "roofline": {"bound": "alu", "pipe": pipe, "kernel": kernel_name(prob.kind, symmetric),
+        "roofline": {"bound": "alu", "pipe": pipe, "kernel": kname,
                      "achieved": achieved / 1e9,
                      "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak,
-                     "traffic": None if args.periodic else kernel_traffic(kernel_name(prob.kind, symmetric),
-                                                                          prob.name, layout, prob.n, symmetric),
+                     "traffic": None if args.periodic else kernel_traffic(kname, prob.name, layout, prob.n,
+                                                                          symmetric),
                      "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms,
                      "evaluations_per_launch": evals,
                      "work_unit": ("pair evaluation (a mutual one serves two ordered pairs)"

@@ -173,9 +173,12 @@ int p2p_plan_workspace_bytes(const p2p_plan* plan, size_t* bytes);
 
 /*
  * Tuning knobs (the autotuner's search space, Section 3.5: threads per box
- * and redundancy grain).  targets_per_lane: 1, 2 or 4 (4: gravity only)
- * targets held in registers by each lane; a work item is 32*targets_per_lane
- * targets of one box.  tile: source records per shared-memory stage (32 or
+ * and redundancy grain).  targets_per_lane: 1, 2 or 4 targets held in
+ * registers by each lane; a gravity work item is 32*targets_per_lane targets
+ * of one box.  Helmholtz items hold at most 64 targets: with 4, a lane holds
+ * four of them and takes every other source of a tile (two source groups per
+ * warp; one-sided compensated passes of one or two right-hand sides, others
+ * run as with 2; symmetric plans take 2).  tile: source records per shared-memory stage (32 or
  * 64).  ctas_per_sm: 0 = as many as fit.  warps_per_item: 1, 2 or 4 warps
  * share one item, splitting its source tiles and adding their partial sums
  * in warp order.  Returns P2P_ERR_INVALID_ARG on values outside these sets.
@@ -455,11 +458,13 @@ int64_t p2p_launch_count(void);
  * Measured peak rates of the pipes that bind the P2P kernels (a measurement
  * utility, not part of the operator; it allocates its own small scratch and
  * synchronises).  On the current device, one CTA of 1024 threads per SM runs
- * independent chains of one instruction kind; host double out[4]:
+ * independent chains of one instruction kind; host double out[5]:
  *   out[0]  FP32 FFMA lane-operations per SM per clock
  *   out[1]  MUFU rsqrt.approx lane-operations per SM per clock
  *   out[2]  MUFU sin.approx lane-operations per SM per clock
  *   out[3]  SM clock in MHz during the FFMA run (clock64 span / event time)
+ *   out[4]  packed fma.rn.f32x2: FP32 lane-operations (two per instruction
+ *           and lane) per SM per clock
  */
 int p2p_measure_pipes(double* out, void* stream);
 

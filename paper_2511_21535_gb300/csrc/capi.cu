@@ -219,7 +219,9 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
         p->tpl = 2;
         p->tile = 64;
     } else {
-        p->tpl = nrhs >= 4 ? 1 : 2;
+        // one or two right-hand sides, one-sided: four targets per lane in two source groups
+        const bool sym = (flags & P2P_PLAN_SYMMETRIC) || layout == P2P_LAYOUT_SYMMETRIC;
+        p->tpl = nrhs >= 4 ? 1 : (nrhs <= 2 && !sym) ? 4 : 2;
         p->tile = nrhs >= 4 ? 32 : 64;
     }
     p->ctas_per_sm = 0;
@@ -229,7 +231,8 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     // per item balances well and saves the group's exchange; few, heavy items
     // need cooperating warps.  Crossover measured on GB300 between the 2^20-point
     // (level 6) and 2^22-point (level 7) Plummer spheres.
-    const double items_est = (double)p->box_cap + (double)n / (32.0 * p->tpl);
+    const int item_lanes = (kind == P2P_GRAVITY || p->tpl < 2) ? p->tpl : 2;   // Helmholtz items: <= 64 targets
+    const double items_est = (double)p->box_cap + (double)n / (32.0 * item_lanes);
     const double resident_warps = (double)num_sms() * 16.0;
     p->group = (is_pairtask(layout) || items_est > 256.0 * resident_warps) ? 1 : 4;
     p->split = nrhs;
@@ -319,8 +322,7 @@ int p2p_plan_workspace_bytes(const p2p_plan* h, size_t* bytes) {
 int p2p_plan_set_tuning(p2p_plan* h, int targets_per_lane, int tile, int ctas_per_sm, int warps_per_item) {
     if (!h) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
-    const bool tpl_ok = targets_per_lane == 1 || targets_per_lane == 2 ||
-                        (targets_per_lane == 4 && p->kind == P2P_GRAVITY);
+    const bool tpl_ok = targets_per_lane == 1 || targets_per_lane == 2 || targets_per_lane == 4;
     const bool g_ok = warps_per_item == 1 || warps_per_item == 2 || warps_per_item == 4;
     if (!tpl_ok || !g_ok || (tile != 32 && tile != 64) || ctas_per_sm < 0 || ctas_per_sm > 32)
         return P2P_ERR_INVALID_ARG;

@@ -30,6 +30,27 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_ffma(float b, float c, int it
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// packed two-wide FFMA (fma.rn.f32x2): each instruction does two lane-operations
+__global__ void __launch_bounds__(kMbThreads) k_mb_ffma2(float b, float c, int iters, float* sink,
+                                                         long long* cycles) {
+    float2 a[kMbChains];
+#pragma unroll
+    for (int i = 0; i < kMbChains; ++i) a[i] = make_float2(threadIdx.x * 1e-3f + i, threadIdx.x * 2e-3f - i);
+    const float2 b2 = make_float2(b, b), c2 = make_float2(c, c);
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < kMbChains; ++i) a[i] = __ffma2_rn(a[i], b2, c2);
+    __syncthreads();
+    const long long t1 = clock64();
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < kMbChains; ++i) s += a[i].x + a[i].y;
+    if (s == 12345.f) sink[threadIdx.x] = s;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 template <int OP>
 __global__ void __launch_bounds__(kMbThreads) k_mb_mufu(int iters, float* sink, long long* cycles) {
     float a[kMbChains];
@@ -101,14 +122,15 @@ extern "C" int p2p_measure_pipes(double* out, void* stream) {
     cudaEventCreate(&e1);
     int rc = P2P_OK;
     long long* host = new long long[sms];
-    for (int which = 0; which < 3 && rc == P2P_OK; ++which) {
-        const int iters = which == 0 ? 40000 : 4000;
+    for (int which = 0; which < 4 && rc == P2P_OK; ++which) {
+        const int iters = (which == 0 || which == 3) ? 40000 : 4000;
         double best = 0.0, mhz = 0.0;
         for (int rep = 0; rep < 3; ++rep) {
             cudaEventRecord(e0, s);
             if (which == 0) k_mb_ffma<<<sms, kMbThreads, 0, s>>>(1.0000001f, 1e-7f, iters, sink, cyc);
             else if (which == 1) k_mb_mufu<0><<<sms, kMbThreads, 0, s>>>(iters, sink, cyc);
-            else k_mb_mufu<1><<<sms, kMbThreads, 0, s>>>(iters, sink, cyc);
+            else if (which == 2) k_mb_mufu<1><<<sms, kMbThreads, 0, s>>>(iters, sink, cyc);
+            else k_mb_ffma2<<<sms, kMbThreads, 0, s>>>(1.0000001f, 1e-7f, iters, sink, cyc);
             count_launch();
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) { rc = P2P_ERR_CUDA; break; }
@@ -121,14 +143,14 @@ extern "C" int p2p_measure_pipes(double* out, void* stream) {
                 mx = host[b] > mx ? host[b] : mx;
                 mean += (double)host[b] / sms;
             }
-            const double ops = (double)kMbThreads * kMbChains * iters;
+            const double ops = (double)kMbThreads * kMbChains * iters * (which == 3 ? 2 : 1);
             const double rate = ops / mean;           // lane-ops per SM per clock
             if (rate > best) {
                 best = rate;
                 mhz = ms > 0.f ? (double)mx / (ms * 1e3) : 0.0;
             }
         }
-        out[which] = best;
+        out[which == 3 ? 4 : which] = best;
         if (which == 0) out[3] = mhz;
     }
     delete[] host;

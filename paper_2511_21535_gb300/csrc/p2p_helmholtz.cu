@@ -1,5 +1,6 @@
 // Helmholtz P2P: dispatch over right-hand-side passes, and the fast
 // (hardware sine/cosine, compensated) kernel variants.
+#include "p2p_helm2d.cuh"
 #include "p2p_helmholtz.cuh"
 #include "p2p_helmsym.cuh"
 
@@ -9,6 +10,11 @@ template <int K, int G>
 static int fast_kg(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                    cudaStream_t s) {
     const bool w2 = a.words == 2;   // records of one or two right-hand sides
+    if (K == 2 && p->tpl == 4 && w2) {
+        // four targets per lane in two source groups (items of 64 targets, as with two per lane)
+        if (R == 1) return launch_helmtile<G, 1>(p, a, perm, kk, r0, u, s);
+        if (R == 2) return launch_helmtile<G, 2>(p, a, perm, kk, r0, u, s);
+    }
     switch (R) {
         case 1: return w2 ? launch_helm<K, G, 1, true, false, 2>(p, a, perm, kk, r0, u, s)
                           : launch_helm<K, G, 1, true, false>(p, a, perm, kk, r0, u, s);

@@ -127,10 +127,11 @@ def launch_count() -> int:
 
 
 def measure_pipes(stream=None) -> dict:
-    """FP32 and MUFU lane-ops per SM per clock, and the SM clock (MHz), measured on the device."""
-    out = (ctypes.c_double * 4)()
+    """FP32 (scalar and packed two-wide) and MUFU lane-ops per SM per clock, and the SM
+    clock (MHz), measured on the device."""
+    out = (ctypes.c_double * 5)()
     _check(load().p2p_measure_pipes(out, _stream(stream)), "p2p_measure_pipes")
-    return {"fp32": out[0], "mufu_rsqrt": out[1], "mufu_sin": out[2], "sm_mhz": out[3]}
+    return {"fp32": out[0], "mufu_rsqrt": out[1], "mufu_sin": out[2], "sm_mhz": out[3], "fp32x2": out[4]}
 
 
 def selftest_bounded_wait(limit_ns: int = 2_000_000, device=None, stream=None) -> int:

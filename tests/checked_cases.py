@@ -47,7 +47,7 @@ def draw(rng):
     tuning = None
     if rng.integers(2):
         # targets per lane: 1, 2 (4 for gravity); symmetric kernels take 2
-        tpls = [2] if sym else ([1, 2, 4] if kind == "gravity" else [1, 2])
+        tpls = [2] if sym else [1, 2, 4]
         tuning = (int(tpls[rng.integers(len(tpls))]), int([32, 64][rng.integers(2)]), 0,
                   int([1, 2, 4][rng.integers(3)]))
     return dict(kind=kind, mode=mode, level=level, n=n, dist=dist, periodic=periodic, nrhs=nrhs, tuning=tuning)

@@ -59,12 +59,14 @@ def test_accuracy_plummer_gravity(dev, plain):
     assert ep <= (1e-5 if not plain else 1e-4) and ea <= (1e-5 if not plain else 1e-4)
 
 
-@pytest.mark.parametrize("mode", ["symmetric", "pattern", "indirect", "pairtask"])
+@pytest.mark.parametrize("mode", ["symmetric", "pattern", "indirect", "pairtask", "four_per_lane"])
 def test_accuracy_grid_helmholtz_64_variants(dev, mode):
     prob = wl.grid_helmholtz()
     kw = dict(layout="indirect") if mode == "indirect" else dict(layout="pairtask") if mode == "pairtask" else {}
     plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, symmetric=(mode == "symmetric"),
                     device=dev, **kw)
+    if mode == "four_per_lane":
+        plan.set_tuning(4, 64, 0, 4)
     if mode == "pattern":
         plan.set_grid(wl.SPACING, wl.LEAF_EDGE_POINTS)
     pos = torch.from_numpy(prob.pos).to(dev)

@@ -95,7 +95,7 @@ def test_pairtask_structures_bit_exact(dev, name):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-@pytest.mark.parametrize("tpl,tile,group", [(1, 32, 1), (2, 64, 2), (2, 64, 4)])
+@pytest.mark.parametrize("tpl,tile,group", [(1, 32, 1), (2, 64, 2), (2, 64, 4), (4, 64, 1)])
 def test_pairtask_parity(dev, name, tpl, tile, group):
     prob = CASES[name]()
     _, out = run(prob, dev, tpl, tile, group)

@@ -220,7 +220,8 @@ HELM_CASES = {
 
 @pytest.mark.parametrize("name", sorted(HELM_CASES))
 @pytest.mark.parametrize("layout", ["indirect", "redundant"])
-@pytest.mark.parametrize("tpl,tile,group", [(1, 32, 1), (2, 64, 2), (2, 64, 4), (1, 64, 4)])
+@pytest.mark.parametrize("tpl,tile,group", [(1, 32, 1), (2, 64, 2), (2, 64, 4), (1, 64, 4), (4, 64, 4), (4, 32, 1),
+                                            (4, 64, 2)])
 def test_helmholtz_parity(dev, name, layout, tpl, tile, group):
     prob = HELM_CASES[name]()
     _, u = run_helmholtz(prob, dev, layout, tpl, tile, group=group)

@@ -125,7 +125,7 @@ def test_periodic_gravity_parity(dev, name, layout, tpl, tile, group):
 
 @pytest.mark.parametrize("name", sorted(HELM_CASES))
 @pytest.mark.parametrize("layout", ["indirect", "redundant"])
-@pytest.mark.parametrize("tpl,tile,group", [(1, 32, 1), (2, 64, 4)])
+@pytest.mark.parametrize("tpl,tile,group", [(1, 32, 1), (2, 64, 4), (4, 64, 4)])
 def test_periodic_helmholtz_parity(dev, name, layout, tpl, tile, group):
     prob = HELM_CASES[name]()
     plan, u = helm_plan(prob, dev, layout, tpl, tile, group)
