@@ -39,7 +39,8 @@ METRIC = "P2P pair-interactions/s"
 def kernel_name(kind: str, symmetric: bool, pattern: bool = False, tile2d: bool = False) -> str:
     """The dominant kernel of a step: Helmholtz runs k_helmholtz_pattern in pattern mode,
     k_helmsym for a symmetric evaluation, k_helmtile for one-sided plans of one or two
-    right-hand sides with four targets per lane (the default), else k_helmholtz."""
+    right-hand sides with four targets per lane (the default), else k_helmholtz; gravity
+    runs k_gravity_pk (packed, two or four targets per lane: tile2d) one-sided, else k_gravity."""
     if kind == "helmholtz":
         if pattern:
             return "k_helmholtz_pattern"
@@ -47,7 +48,8 @@ def kernel_name(kind: str, symmetric: bool, pattern: bool = False, tile2d: bool 
             return "k_helmsym"
         if tile2d:
             return "k_helmtile"
-    return f"k_{kind}"
+        return "k_helmholtz"
+    return "k_gravity_pk" if (tile2d and not symmetric) else "k_gravity"
 
 
 def kernel_traffic(kernel: str, workload: str, layout: str, n: int, symmetric: bool):
@@ -373,8 +375,10 @@ def run_gpu(args, rank, world, local_rank):
         pipe, per_pair = "fp32", 13.0
         peak = pipes["fp32"] * sms * f_mhz * 1e6 / per_pair
     # the default Helmholtz tuning for one or two right-hand sides, one-sided: four targets per lane
-    tile2d = (prob.kind == "helmholtz" and not symmetric and layout != "symmetric" and prob.nrhs <= 2
-              and args.tpl in (0, 4))
+    if prob.kind == "helmholtz":
+        tile2d = not symmetric and layout != "symmetric" and prob.nrhs <= 2 and args.tpl in (0, 4)
+    else:
+        tile2d = not symmetric and layout != "symmetric" and args.tpl in (0, 2, 4)
     kname = kernel_name(prob.kind, symmetric or layout == "symmetric", args.pattern, tile2d)
     # pair evaluations the kernel performs (a symmetric plan's mutual evaluation serves two ordered pairs)
     evals = cnt.get("evals", geo_pairs) if (symmetric or layout == "symmetric") else geo_pairs

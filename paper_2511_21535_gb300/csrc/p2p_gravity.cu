@@ -228,6 +228,193 @@ struct GravityOp {
     }
 };
 
+// One-sided, compensated, K in {2, 4}: the same arithmetic as GravityOp with
+// the FP32 work of each pair of targets in packed two-wide instructions
+// (add/mul/fma.rn.f32x2: two lane-operations per issue slot, each half rounded
+// as the scalar operation would be, so the sums are bitwise those of the
+// scalar kernel); rsqrt stays scalar on the MUFU pipe.  The scalar kernel
+// issues about as many instructions per pair as the FP32 pipe has cycles.
+template <int K>
+struct GravityPackOp {
+    static_assert(K == 2 || K == 4, "target pairs");
+    static constexpr int KP = K / 2;
+    static constexpr int kOuts = 4 * K;
+    static constexpr bool kPartial = true;
+    static constexpr int kMutFloats = 0;
+
+    const float4* __restrict__ rec;
+    const int32_t* __restrict__ perm;
+    float eps2;
+    float* __restrict__ phi;
+    float* __restrict__ acc;
+
+    float2 ntx[KP], nty[KP], ntz[KP];   // negated target coordinates of lanes' targets (2h, 2h+1)
+    float2 pp[KP][4];                   // the current tile's partial sums, packed
+    float s[K][4], c[K][4];
+    int self[K];
+    int tbase, nt;
+
+    __device__ __forceinline__ void load_positions(int lane, float sx, float sy, float sz) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            // idle lanes sit on the first target: finite distances to every other particle
+            const float4 r = rec[tbase + (l < nt ? l : 0)];
+            const float x = sx - r.x, y = sy - r.y, z = sz - r.z;
+            if (k & 1) {
+                ntx[k / 2].y = x;
+                nty[k / 2].y = y;
+                ntz[k / 2].y = z;
+            } else {
+                ntx[k / 2].x = x;
+                nty[k / 2].x = y;
+                ntz[k / 2].x = z;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void begin(int tb, int ntg, int sw_lo, int lane) {
+        tbase = tb;
+        nt = ntg;
+        load_positions(lane, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            self[k] = (l < nt) ? sw_lo + l : -1;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s[k][o] = c[k][o] = 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < KP; ++h)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) pp[h][o] = make_float2(0.f, 0.f);
+    }
+
+    // periodic image of the current neighbour range: targets move by -shift
+    __device__ __forceinline__ void set_shift(float sx, float sy, float sz) {
+        load_positions(threadIdx.x & 31, sx, sy, sz);
+    }
+
+    template <bool CHECK>
+    __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
+        const float2 e2 = make_float2(eps2, eps2);
+#pragma unroll 4
+        for (int j = 0; j < cnt; ++j) {
+            const float4 src = sm[j];
+            const float2 sx = make_float2(src.x, src.x), sy = make_float2(src.y, src.y),
+                         sz = make_float2(src.z, src.z);
+#pragma unroll
+            for (int h = 0; h < KP; ++h) {
+                const float2 dx = __fadd2_rn(sx, ntx[h]), dy = __fadd2_rn(sy, nty[h]), dz = __fadd2_rn(sz, ntz[h]);
+                float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                float2 m = make_float2(src.w, src.w);
+                if (CHECK) {
+                    const bool me0 = (rec0 + j) == self[2 * h], me1 = (rec0 + j) == self[2 * h + 1];
+                    m.x = me0 ? 0.f : m.x;
+                    m.y = me1 ? 0.f : m.y;
+                    r2.x = me0 ? 1.f : r2.x;
+                    r2.y = me1 ? 1.f : r2.y;
+                }
+                const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                const float2 mi = __fmul2_rn(m, inv);
+                const float2 mi3 = __fmul2_rn(mi, __fmul2_rn(inv, inv));
+                pp[h][0] = __fadd2_rn(pp[h][0], mi);
+                pp[h][1] = __ffma2_rn(mi3, dx, pp[h][1]);
+                pp[h][2] = __ffma2_rn(mi3, dy, pp[h][2]);
+                pp[h][3] = __ffma2_rn(mi3, dz, pp[h][3]);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void tile(const float4* sm, int cnt, int rec0, bool chk) {
+        if (chk) body<true>(sm, cnt, rec0);
+        else body<false>(sm, cnt, rec0);
+#pragma unroll
+        for (int h = 0; h < KP; ++h)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                kahan_add(s[2 * h][o], c[2 * h][o], pp[h][o].x);
+                kahan_add(s[2 * h + 1][o], c[2 * h + 1][o], pp[h][o].y);
+                pp[h][o] = make_float2(0.f, 0.f);
+            }
+    }
+
+    __device__ __forceinline__ void store_partial(float* dst, int lane) const {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) dst[(k * 4 + o) * 32 + lane] = s[k][o] - c[k][o];
+    }
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                s[k][o] -= c[k][o];
+                c[k][o] = 0.f;
+            }
+    }
+    __device__ __forceinline__ void add_partial(const float* src, int lane) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s[k][o] += src[(k * 4 + o) * 32 + lane];
+    }
+    __device__ __forceinline__ void end_partial(int lane, void* part, int64_t, int64_t slot) {
+        float4* o = static_cast<float4*>(part) + slot;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            if (l < nt)
+                o[l] = make_float4(s[k][0] - c[k][0], s[k][1] - c[k][1], s[k][2] - c[k][2], s[k][3] - c[k][3]);
+        }
+    }
+    __device__ __forceinline__ void end(int lane) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            if (l < nt) {
+                const int64_t o = perm[tbase + l];
+                phi[o] = -(s[k][0] - c[k][0]);
+                acc[3 * o + 0] = s[k][1] - c[k][1];
+                acc[3 * o + 1] = s[k][2] - c[k][2];
+                acc[3 * o + 2] = s[k][3] - c[k][3];
+            }
+        }
+    }
+};
+
+template <int K, int G>
+__global__ void __launch_bounds__(kLoopThreads, 4)
+    k_gravity_pk(LoopArgs a, const int32_t* __restrict__ perm, float eps2, float* __restrict__ phi,
+                 float* __restrict__ acc) {
+    pdl_wait();
+    GravityPackOp<K> op;
+    op.rec = a.rec;
+    op.perm = perm;
+    op.eps2 = eps2;
+    op.phi = phi;
+    op.acc = acc;
+    warp_item_loop<K, G>(a, op);
+}
+
+template <int K, int G>
+static int launch_gravity_pk(const Plan* p, const LoopArgs& a, const int32_t* perm, float eps2, float* phi,
+                             float* acc, cudaStream_t s) {
+    auto kern = k_gravity_pk<K, G>;
+    using Op = GravityPackOp<K>;
+    const size_t smem = loop_smem_bytes(a.tile, a.words, Op::kOuts, G, Op::kMutFloats);
+    P2P_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = p->ctas_per_sm;
+    if (per_sm <= 0) {
+        P2P_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem));
+        if (per_sm < 1) per_sm = 1;
+    }
+    P2P_CUDA_TRY(launch_pdl(kern, num_sms() * per_sm, kLoopThreads, smem, s, a, perm, eps2, phi, acc));
+    P2P_LAUNCH_CHECK();
+    return P2P_OK;
+}
+
 template <int K, int G, bool COMP, bool MUT = false>
 __global__ void __launch_bounds__(kLoopThreads, MUT ? 3 : 4)
     k_gravity(LoopArgs a, const int32_t* __restrict__ perm, float eps2, float* __restrict__ phi,
@@ -270,9 +457,9 @@ static int launch_gravity_g(const Plan* p, const LoopArgs& a, const int32_t* per
     switch (p->tpl) {
         case 1: return comp ? launch_gravity<1, G, true>(p, a, perm, eps2, phi, acc, s)
                             : launch_gravity<1, G, false>(p, a, perm, eps2, phi, acc, s);
-        case 2: return comp ? launch_gravity<2, G, true>(p, a, perm, eps2, phi, acc, s)
+        case 2: return comp ? launch_gravity_pk<2, G>(p, a, perm, eps2, phi, acc, s)
                             : launch_gravity<2, G, false>(p, a, perm, eps2, phi, acc, s);
-        case 4: return comp ? launch_gravity<4, G, true>(p, a, perm, eps2, phi, acc, s)
+        case 4: return comp ? launch_gravity_pk<4, G>(p, a, perm, eps2, phi, acc, s)
                             : launch_gravity<4, G, false>(p, a, perm, eps2, phi, acc, s);
         default: return P2P_ERR_INVALID_ARG;
     }

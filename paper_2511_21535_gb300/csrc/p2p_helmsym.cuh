@@ -11,6 +11,11 @@
 //   A side (target i):  u_i += G(r_ij) q_j,   B side (source j):  u_j += G(r_ij) q_i
 //   G = exp(i k r) / r, the 1/(4 pi) applied when written.
 //
+// The FP32 work of each pair of a lane's targets (differences, r^2, k r, G,
+// the complex products of both sides) runs as packed two-wide instructions
+// (add/mul/fma.rn.f32x2); a source's sums over the lane's targets are kept as
+// an (even, odd) pair and added before the cross-lane reduction.
+//
 // Summation is blocked: per lane a tile's partial (<= 16 sources) is added
 // to the lane's running sum, the four lanes' sums are added at the end, and
 // the update step adds the items' and tasks' partials compensated.
@@ -59,9 +64,11 @@ struct HelmSymOp {
     float2* mpart;
     int64_t mcap;
 
-    float tx[KT], ty[KT], tz[KT];
-    float tqr[KT][R], tqi[KT][R];
-    float sr[KT][R], si[KT][R], pr[KT][R], pi_[KT][R];
+    static constexpr int KP = KT / 2;             // target pairs per lane (packed two-wide arithmetic)
+    float2 ntx[KP], nty[KP], ntz[KP];             // negated target coordinates, packed in pairs
+    float2 tqr[KP][R], tqi[KP][R], ntqi[KP][R];   // the targets' charges (zero for idle targets), packed
+    float2 pr[KP][R], pi_[KP][R];                 // the current tile's target partial sums, packed
+    float sr[KT][R], si[KT][R];
     int tbase, nt, self0;
     float2* bsum;
     bool mut;
@@ -82,9 +89,16 @@ struct HelmSymOp {
             const int t = t0 + k;
             // idle targets sit on the first target: finite distances to every other particle
             const float4 r = rec[(int64_t)(tbase + (t < nt ? t : 0)) * W];
-            tx[k] = r.x - sx;
-            ty[k] = r.y - sy;
-            tz[k] = r.z - sz;
+            const float x = sx - r.x, y = sy - r.y, z = sz - r.z;
+            if (k & 1) {
+                ntx[k / 2].y = x;
+                nty[k / 2].y = y;
+                ntz[k / 2].y = z;
+            } else {
+                ntx[k / 2].x = x;
+                nty[k / 2].x = y;
+                ntz[k / 2].x = z;
+            }
         }
     }
 
@@ -102,16 +116,30 @@ struct HelmSymOp {
 #pragma unroll
             for (int w = 0; w < (R + 1) / 2; ++w) {
                 const float4 v = (t < nt) ? rq[qw0 + w] : make_float4(0.f, 0.f, 0.f, 0.f);
-                tqr[k][2 * w] = v.x;
-                tqi[k][2 * w] = v.y;
-                if (2 * w + 1 < R) {
-                    tqr[k][2 * w + 1] = v.z;
-                    tqi[k][2 * w + 1] = v.w;
+#pragma unroll
+                for (int e = 0; e < 2 && 2 * w + e < R; ++e) {
+                    const float re = e ? v.z : v.x, im = e ? v.w : v.y;
+                    float2& a = tqr[k / 2][2 * w + e];
+                    float2& b = tqi[k / 2][2 * w + e];
+                    float2& c = ntqi[k / 2][2 * w + e];
+                    if (k & 1) {
+                        a.y = re;
+                        b.y = im;
+                        c.y = -im;
+                    } else {
+                        a.x = re;
+                        b.x = im;
+                        c.x = -im;
+                    }
                 }
             }
 #pragma unroll
-            for (int q = 0; q < R; ++q) sr[k][q] = si[k][q] = pr[k][q] = pi_[k][q] = 0.f;
+            for (int q = 0; q < R; ++q) sr[k][q] = si[k][q] = 0.f;
         }
+#pragma unroll
+        for (int h = 0; h < KP; ++h)
+#pragma unroll
+            for (int q = 0; q < R; ++q) pr[h][q] = pi_[h][q] = make_float2(0.f, 0.f);
     }
 
     // periodic image of the current neighbour range: targets move by -shift
@@ -119,20 +147,49 @@ struct HelmSymOp {
         load_positions(threadIdx.x & 31, sx, sy, sz);
     }
 
-    __device__ __forceinline__ void source(const float4* __restrict__ sm, int j, bool valid, float4& ps, float (&qr)[R],
-                                           float (&qi)[R]) const {
+    // source j of the tile: position and charges duplicated into both halves
+    // (zero charges for an invalid source)
+    __device__ __forceinline__ void source(const float4* __restrict__ sm, int j, bool valid, float2& sx, float2& sy,
+                                           float2& sz, float2 (&qr)[R], float2 (&qi)[R], float2 (&nqi)[R]) const {
         const float4* rj = sm + (int64_t)j * W;
-        ps = rj[0];
+        const float4 ps = rj[0];
+        sx = make_float2(ps.x, ps.x);
+        sy = make_float2(ps.y, ps.y);
+        sz = make_float2(ps.z, ps.z);
 #pragma unroll
         for (int w = 0; w < (R + 1) / 2; ++w) {
             const float4 v = rj[qw0 + w];
-            qr[2 * w] = valid ? v.x : 0.f;
-            qi[2 * w] = valid ? v.y : 0.f;
-            if (2 * w + 1 < R) {
-                qr[2 * w + 1] = valid ? v.z : 0.f;
-                qi[2 * w + 1] = valid ? v.w : 0.f;
+#pragma unroll
+            for (int e = 0; e < 2 && 2 * w + e < R; ++e) {
+                const float re = valid ? (e ? v.z : v.x) : 0.f, im = valid ? (e ? v.w : v.y) : 0.f;
+                qr[2 * w + e] = make_float2(re, re);
+                qi[2 * w + e] = make_float2(im, im);
+                nqi[2 * w + e] = make_float2(-im, -im);
             }
         }
+    }
+
+    // G = exp(i k r) / r for a source and the target pair h, packed (self pairs: 0)
+    template <bool CHECK>
+    __device__ __forceinline__ void kernel_g(float2 sx, float2 sy, float2 sz, int h, bool me0, bool me1,
+                                             float2& gr, float2& gi, float2& dr2) const {
+        const float2 dx = __fadd2_rn(sx, ntx[h]), dy = __fadd2_rn(sy, nty[h]), dz = __fadd2_rn(sz, ntz[h]);
+        float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        if (CHECK) {
+            r2.x = me0 ? 1.f : r2.x;
+            r2.y = me1 ? 1.f : r2.y;
+        }
+        const float2 inv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 th = __fmul2_rn(make_float2(kk, kk), __fmul2_rn(r2, inv));
+        gr = __fmul2_rn(inv, make_float2(cos_approx(th.x), cos_approx(th.y)));
+        gi = __fmul2_rn(inv, make_float2(sin_approx(th.x), sin_approx(th.y)));
+        if (CHECK) {
+            gr.x = me0 ? 0.f : gr.x;
+            gi.x = me0 ? 0.f : gi.x;
+            gr.y = me1 ? 0.f : gr.y;
+            gi.y = me1 ? 0.f : gi.y;
+        }
+        dr2 = r2;
     }
 
     // one-sided ranges (self and large boxes): A side only
@@ -141,29 +198,19 @@ struct HelmSymOp {
         const int lane = threadIdx.x & 31, sg = lane % SP, t0 = (lane / SP) * KT;
 #pragma unroll 2
         for (int j = sg; j < cnt; j += SP) {
-            float4 ps;
-            float qr[R], qi[R];
-            source(sm, j, true, ps, qr, qi);
+            float2 sx, sy, sz, qr[R], qi[R], nqi[R];
+            source(sm, j, true, sx, sy, sz, qr, qi, nqi);
 #pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                const float dx = ps.x - tx[k], dy = ps.y - ty[k], dz = ps.z - tz[k];
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                bool me = false;
-                if (CHECK) {
-                    me = (rec0 + j) == self0 + t0 + k && t0 + k < nt;
-                    r2 = me ? 1.f : r2;
-                }
-                const float inv = rsqrt_approx(r2);
-                const float th = kk * (r2 * inv);
-                float gr = inv * cos_approx(th), gi = inv * sin_approx(th);
-                if (CHECK) {
-                    gr = me ? 0.f : gr;
-                    gi = me ? 0.f : gi;
-                }
+            for (int h = 0; h < KP; ++h) {
+                const int t = t0 + 2 * h;
+                const bool me0 = CHECK && (rec0 + j) == self0 + t && t < nt;
+                const bool me1 = CHECK && (rec0 + j) == self0 + t + 1 && t + 1 < nt;
+                float2 gr, gi, r2;
+                kernel_g<CHECK>(sx, sy, sz, h, me0, me1, gr, gi, r2);
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    pr[k][q] = fmaf(gr, qr[q], fmaf(-gi, qi[q], pr[k][q]));
-                    pi_[k][q] = fmaf(gr, qi[q], fmaf(gi, qr[q], pi_[k][q]));
+                    pr[h][q] = __ffma2_rn(gr, qr[q], __ffma2_rn(gi, nqi[q], pr[h][q]));
+                    pi_[h][q] = __ffma2_rn(gr, qi[q], __ffma2_rn(gi, qr[q], pi_[h][q]));
                 }
             }
         }
@@ -174,32 +221,34 @@ struct HelmSymOp {
     __device__ __forceinline__ void body_mut(const float4* __restrict__ sm, int cnt) {
         const int lane = threadIdx.x & 31, sg = lane % SP;
         const int u_me = ((lane >> 4) << 1) | ((lane >> 3) & 1);
-#pragma unroll 2
+#pragma unroll 1
         for (int g = 0; g < cnt; g += 4 * SP) {
             float vr[4][R], vi[4][R];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int j = g + SP * u + sg;
                 const bool valid = ALLV || j < cnt;
-                float4 ps;
-                float qr[R], qi[R];
-                source(sm, ALLV ? j : min(j, cnt - 1), valid, ps, qr, qi);
+                float2 sx, sy, sz, qr[R], qi[R], nqi[R];
+                source(sm, ALLV ? j : min(j, cnt - 1), valid, sx, sy, sz, qr, qi, nqi);
+                float2 br[R], bi[R];   // the source's sums over the lane's target pairs (even, odd)
 #pragma unroll
-                for (int q = 0; q < R; ++q) vr[u][q] = vi[u][q] = 0.f;
+                for (int q = 0; q < R; ++q) br[q] = bi[q] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int k = 0; k < KT; ++k) {
-                    const float dx = ps.x - tx[k], dy = ps.y - ty[k], dz = ps.z - tz[k];
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float inv = rsqrt_approx(r2);
-                    const float th = kk * (r2 * inv);
-                    const float gr = inv * cos_approx(th), gi = inv * sin_approx(th);
+                for (int h = 0; h < KP; ++h) {
+                    float2 gr, gi, r2;
+                    kernel_g<false>(sx, sy, sz, h, false, false, gr, gi, r2);
 #pragma unroll
                     for (int q = 0; q < R; ++q) {
-                        pr[k][q] = fmaf(gr, qr[q], fmaf(-gi, qi[q], pr[k][q]));
-                        pi_[k][q] = fmaf(gr, qi[q], fmaf(gi, qr[q], pi_[k][q]));
-                        vr[u][q] = fmaf(gr, tqr[k][q], fmaf(-gi, tqi[k][q], vr[u][q]));
-                        vi[u][q] = fmaf(gr, tqi[k][q], fmaf(gi, tqr[k][q], vi[u][q]));
+                        pr[h][q] = __ffma2_rn(gr, qr[q], __ffma2_rn(gi, nqi[q], pr[h][q]));
+                        pi_[h][q] = __ffma2_rn(gr, qi[q], __ffma2_rn(gi, qr[q], pi_[h][q]));
+                        br[q] = __ffma2_rn(gr, tqr[h][q], __ffma2_rn(gi, ntqi[h][q], br[q]));
+                        bi[q] = __ffma2_rn(gr, tqi[h][q], __ffma2_rn(gi, tqr[h][q], bi[q]));
                     }
+                }
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    vr[u][q] = br[q].x + br[q].y;
+                    vi[u][q] = bi[q].x + bi[q].y;
                 }
             }
             const int j_me = g + SP * u_me + sg;
@@ -235,12 +284,14 @@ struct HelmSymOp {
             body<false>(sm, cnt, rec0);
         }
 #pragma unroll
-        for (int k = 0; k < KT; ++k)
+        for (int h = 0; h < KP; ++h)
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                sr[k][q] += pr[k][q];
-                si[k][q] += pi_[k][q];
-                pr[k][q] = pi_[k][q] = 0.f;
+                sr[2 * h][q] += pr[h][q].x;
+                si[2 * h][q] += pi_[h][q].x;
+                sr[2 * h + 1][q] += pr[h][q].y;
+                si[2 * h + 1][q] += pi_[h][q].y;
+                pr[h][q] = pi_[h][q] = make_float2(0.f, 0.f);
             }
     }
 

@@ -171,6 +171,20 @@ def test_gravity_layouts_agree_bitwise(dev):
     assert rel_l2(p1, p2) < 1e-6 and rel_l2(a1, a2) < 1e-6
 
 
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+def test_gravity_packed_kernels_agree(dev, layout):
+    """Two and four targets per lane run the packed two-wide kernel: the same
+    per-target operation order, so bitwise equal; one per lane is the scalar
+    kernel (the compiler may contract its products into FMAs): equal to rounding."""
+    prob = wl.plummer_gravity(n=40000, level=5, eps=1e-3, seed=2)
+    _, p1, a1 = run_gravity(prob, dev, layout, 1, 64, group=4)
+    _, p2, a2 = run_gravity(prob, dev, layout, 2, 64, group=4)
+    _, p4, a4 = run_gravity(prob, dev, layout, 4, 64, group=4)
+    np.testing.assert_array_equal(p2, p4)
+    np.testing.assert_array_equal(a2, a4)
+    assert rel_l2(p1, p2) < 1e-6 and rel_l2(a1, a2) < 1e-6
+
+
 def test_gravity_deterministic(dev):
     prob = wl.plummer_gravity(n=40000, level=5, eps=1e-3, seed=4)
     _, p1, a1 = run_gravity(prob, dev, "redundant")
