@@ -110,6 +110,8 @@ def _make_problem(name: str):
         return wl.grid_helmholtz(edge_points=128)
     if name == "plummer_gravity_1m":
         return wl.plummer_gravity(n=1 << 20, level=6)
+    if name == "grid_helmholtz_r8":
+        return wl.grid_helmholtz(nrhs=8)
     raise SystemExit(f"unknown workload {name}")
 
 

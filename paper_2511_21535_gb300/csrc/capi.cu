@@ -219,10 +219,11 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
         p->tpl = 2;
         p->tile = 64;
     } else {
-        // one or two right-hand sides, one-sided: four targets per lane in two source groups
+        // one or two right-hand sides, one-sided: four targets per lane in two source groups;
+        // otherwise two per lane
         const bool sym = (flags & P2P_PLAN_SYMMETRIC) || layout == P2P_LAYOUT_SYMMETRIC;
-        p->tpl = nrhs >= 4 ? 1 : (nrhs <= 2 && !sym) ? 4 : 2;
-        p->tile = nrhs >= 4 ? 32 : 64;
+        p->tpl = (nrhs <= 2 && !sym) ? 4 : 2;
+        p->tile = nrhs > 8 ? 32 : 64;
     }
     p->ctas_per_sm = 0;
     // Warps per work item.  A pair task holds one box's sources, usually a

@@ -200,8 +200,10 @@ struct HelmOp {
     }
 };
 
+// register bound by the accumulators' size: four or eight right-hand sides
+// per pass with two targets per lane need 123 / 168 registers (no spills)
 template <int K, int G, int R, bool COMP, bool PRECISE, int W = 0>
-__global__ void __launch_bounds__(kLoopThreads, 6)
+__global__ void __launch_bounds__(kLoopThreads, R >= 8 ? (K >= 2 ? 3 : 4) : R == 4 ? (K >= 2 ? 4 : 5) : 6)
     k_helmholtz(LoopArgs a, const int32_t* __restrict__ perm, float kk, int qw0, int64_t n, int r0, HelmOut out) {
     pdl_wait();
     HelmOp<K, R, COMP, PRECISE, W> op;
