@@ -236,6 +236,9 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     const double items_est = (double)p->box_cap + (double)n / (32.0 * item_lanes);
     const double resident_warps = (double)num_sms() * 16.0;
     p->group = (is_pairtask(layout) || items_est > 256.0 * resident_warps) ? 1 : 4;
+    // symmetric Helmholtz items (self plus about half the neighbours as mutual
+    // ranges) are uneven: two warps per item measured best on the 64^3 grid
+    if (p->group == 4 && kind == P2P_HELMHOLTZ && (flags & P2P_PLAN_SYMMETRIC)) p->group = 2;
     p->split = nrhs;
     p->rmax = 2.0f * (edge / (float)(1 << level)) * 1.7320508f;
     p->items_cap = is_pairtask(layout) ? 27 * p->box_cap + (27 * n + 31) / 32 + 1
