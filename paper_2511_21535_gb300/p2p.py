@@ -487,7 +487,28 @@ class Batch:
         _check(load().p2p_batch_set_tuning(self._h, LAYOUTS[layout], targets_per_lane, tile, ctas_per_sm,
                                            warps_per_item), "p2p_batch_set_tuning")
 
-    def autotune(self, pos, q, y=None, u=None, g=None, stream=None) -> dict:
+    def autotune(self, pos, q, y=None, u=None, g=None, stream=None, cache=None) -> dict:
+        """Time the tuning space on these buffers and keep the fastest choice.
+        cache: a tune_cache.TuneCache (or True for the default file): a stored
+        choice for this GPU, batch shape class and kernel build is applied
+        without timing, and a new choice is stored."""
+        from . import tune_cache as _tc
+        if cache is True:
+            cache = _tc.TuneCache()
+        key = None
+        if cache:
+            key = _tc.TuneCache.key(torch.cuda.get_device_name(self.device),
+                                    _tc.shape_class(self.sizes, self.nrhs, self.pair))
+            hit = cache.get(key)
+            if hit is not None:
+                self.set_tuning(hit["layout"], hit["targets_per_lane"], hit["tile"], hit["warps_per_item"])
+                return dict(hit, cached=True)
+        res = self._autotune(pos, q, y, u, g, stream)
+        if cache:
+            cache.put(key, res)
+        return dict(res, cached=False)
+
+    def _autotune(self, pos, q, y, u, g, stream) -> dict:
         u, g = self._args(pos, q, y, u, g)
         best = (ctypes.c_int * 5)()
         ms = ctypes.c_float()

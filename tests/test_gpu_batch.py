@@ -106,6 +106,28 @@ def test_batch_autotune_and_graph(dev):
     assert torch.equal(u0, u1) and torch.equal(g0, g1)
 
 
+def test_batch_autotune_cache(dev, tmp_path):
+    """A second batch of the same shape class on the same GPU and kernel build
+    takes the stored choice without timing, and computes the same result."""
+    from paper_2511_21535_gb300 import tune_cache
+    cache = tune_cache.TuneCache(str(tmp_path / "autotune.json"))
+    nrhs = 2
+    probs = small_set(nrhs)
+    b1, pos, q, y = make_batch(probs, nrhs, True, "auto", dev)
+    b1.build(pos)
+    first = b1.autotune(pos, q, y, cache=cache)
+    assert first["cached"] is False and first["ms"] > 0
+    u1, g1 = b1.run(pos, q, y)
+    b2, _, _, _ = make_batch(probs, nrhs, True, "auto", dev)
+    b2.build(pos)
+    second = b2.autotune(pos, q, y, cache=cache)
+    assert second["cached"] is True
+    for k in ("layout", "targets_per_lane", "tile", "warps_per_item"):
+        assert second[k] == first[k]
+    u2, g2 = b2.run(pos, q, y)
+    assert torch.equal(u1, u2) and torch.equal(g1, g2)
+
+
 def test_batched_64_instances_sampled(dev):
     probs = wl.batched_helmholtz()
     nrhs = 8
