@@ -127,8 +127,10 @@ LoopArgs loop_args(const Plan* p, void* ws, int words) {
     a.rec = at<float4>(ws, L.src);
     a.red = (p->layout == P2P_LAYOUT_REDUNDANT) ? at<float4>(ws, L.red_src) : nullptr;
     a.words = words;
-    // wide adjoint records: keep a stage within ~2.5 KB
-    a.tile = (words * p->tile > 160) ? 32 : p->tile;
+    // wide records: halve the tile until a stage stays within ~2.5 KB (32 at least)
+    int tile = p->tile;
+    while (tile > 32 && words * tile > 160) tile >>= 1;
+    a.tile = tile;
     a.box_start = at<int32_t>(ws, L.box_start);
     a.nbr_start = at<int32_t>(ws, L.nbr_start);
     a.nbr_idx = at<int32_t>(ws, L.nbr_idx);
@@ -217,7 +219,7 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     // defaults; p2p_plan_set_tuning / the autotuner may change them
     if (kind == P2P_GRAVITY) {
         p->tpl = 2;
-        p->tile = 64;
+        p->tile = 128;   // 2 KB stages of 16-byte records: half the per-tile overhead of 64 (measured)
     } else {
         // one or two right-hand sides, one-sided: four targets per lane in two source groups;
         // otherwise two per lane
@@ -328,7 +330,7 @@ int p2p_plan_set_tuning(p2p_plan* h, int targets_per_lane, int tile, int ctas_pe
     Plan* p = &h->p;
     const bool tpl_ok = targets_per_lane == 1 || targets_per_lane == 2 || targets_per_lane == 4;
     const bool g_ok = warps_per_item == 1 || warps_per_item == 2 || warps_per_item == 4;
-    if (!tpl_ok || !g_ok || (tile != 32 && tile != 64) || ctas_per_sm < 0 || ctas_per_sm > 32)
+    if (!tpl_ok || !g_ok || (tile != 32 && tile != 64 && tile != 128) || ctas_per_sm < 0 || ctas_per_sm > 32)
         return P2P_ERR_INVALID_ARG;
     p->tpl = targets_per_lane;
     p->tile = tile;
