@@ -10,6 +10,11 @@ nodes inside the graph).  Default workload: the Helmholtz near
 field on a 64^3 grid at lambda/10 spacing, 4^3-point leaf boxes, one complex
 right-hand side, redundant layout.
 
+`e2e` is the same step from pinned host buffers through the library's
+host-buffer call (p2p_helmholtz_host / p2p_gravity_host): the positions' and
+strengths' copies to the device and the results' copy back are inside the
+timed region.
+
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
 (the only other code path this script may run), on a bounded sample of the
 same workload.
@@ -210,7 +215,7 @@ def run_gpu(args, rank, world, local_rank):
     symmetric = (args.evaluation == "symmetric" and not args.pattern and layout in ("redundant", "indirect")
                  and (prob.kind == "gravity" or prob.nrhs <= 2))
     plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
-                    timing=True, periodic=args.periodic, symmetric=symmetric, device=dev)
+                    timing=True, periodic=args.periodic, symmetric=symmetric, host_io=True, device=dev)
     if args.tpl:
         plan.set_tuning(args.tpl, args.tile, args.ctas, args.group)
     if args.pattern:
@@ -316,7 +321,9 @@ def run_gpu(args, rank, world, local_rank):
     ms = sum(step_ms) / len(step_ms)
     value, ms, _ = replica_throughput(pairs, ms, dist, dev)
 
-    # end to end through the API from pinned host buffers: H2D, full step, D2H
+    # end to end through the C ABI's host-buffer step (p2p_*_host) from pinned
+    # host buffers: H2D of positions and strengths (the strengths' copy
+    # overlapped with the tree build), full step, D2H of the results
     hpos = torch.from_numpy(prob.pos).pin_memory()
     hstr = torch.from_numpy(prob.strength).pin_memory()
     if prob.kind == "gravity":
@@ -324,21 +331,12 @@ def run_gpu(args, rank, world, local_rank):
                 torch.empty(prob.n, 3, dtype=torch.float32).pin_memory())
     else:
         hout = (torch.empty(prob.nrhs, prob.n, dtype=torch.complex64).pin_memory(),)
-    dpos = torch.empty_like(pos)
-    dstr = torch.empty_like(strength)
 
     def e2e_step():
-        dpos.copy_(hpos, non_blocking=True)
-        dstr.copy_(hstr, non_blocking=True)
-        plan.tree_build(dpos)
-        plan.restructure(dpos, dstr)
         if prob.kind == "gravity":
-            plan.gravity(prob.eps, out_a, out_b)
-            hout[0].copy_(out_a, non_blocking=True)
-            hout[1].copy_(out_b, non_blocking=True)
+            plan.gravity_host(prob.eps, hpos, hstr, hout[0], hout[1])
         else:
-            plan.helmholtz(prob.k, out_u)
-            hout[0].copy_(out_u, non_blocking=True)
+            plan.helmholtz_host(prob.k, hpos, hstr, hout[0])
 
     for _ in range(max(1, args.warmup)):
         flush.zero_()

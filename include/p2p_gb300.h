@@ -119,6 +119,10 @@ typedef enum {
                                    /* both particles (see P2P_ARR_TASK_KIND); forward */
                                    /* operators only; Helmholtz nrhs <= 2, hardware  */
                                    /* sine/cosine range, compensated; 2 targets/lane */
+#define P2P_PLAN_HOST_IO     0x40u /* the workspace also holds device copies of the */
+                                   /* inputs and outputs for p2p_*_host; the plan   */
+                                   /* creates a second stream for input copies on   */
+                                   /* the first such call (destroyed with the plan) */
 
 /* device flag bits (p2p_read_counters: counters[P2P_CTR_FLAGS]) */
 #define P2P_FLAG_DOMAIN   0x1u     /* a position was outside the domain             */
@@ -383,6 +387,25 @@ int p2p_selftest_bounded_wait(uint64_t limit_ns, uint32_t* flags_dev, void* stre
  */
 int p2p_build_checked(void);
 int p2p_fail_host_allocs(int count);
+
+/*
+ * One step from host buffers (plans created with P2P_PLAN_HOST_IO), the
+ * paper's transfer phase included: copies the positions (float [n][3]) and
+ * strengths (gravity: float [n]; Helmholtz: complex64 [nrhs][n]) from host
+ * memory into the workspace, builds the tree, restructures, evaluates, and
+ * copies the results back (gravity: phi float [n], acc float [n][3];
+ * Helmholtz: u complex64 [nrhs][n]).  The strengths' copy runs on a stream
+ * of the plan's own, overlapped with the tree build.  All host pointers are
+ * caller-owned; page-locked buffers let the copies run asynchronously
+ * (pageable ones work, with synchronous copies).  Asynchronous on `stream`:
+ * the results are in host memory once the stream has passed this call.
+ * Returns P2P_ERR_UNSUPPORTED for plans without P2P_PLAN_HOST_IO, and the
+ * statuses of p2p_tree_build / p2p_restructure / the operator.
+ */
+int p2p_gravity_host(p2p_plan* plan, float eps, const float* pos, const float* mass, float* phi, float* acc,
+                     void* ws, size_t ws_bytes, void* stream);
+int p2p_helmholtz_host(p2p_plan* plan, float k, const float* pos, const void* q, void* u, void* ws,
+                       size_t ws_bytes, void* stream);
 
 /* identifiers of workspace arrays for p2p_plan_array */
 typedef enum {

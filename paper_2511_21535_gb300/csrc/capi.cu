@@ -94,6 +94,13 @@ void compute_layout(Plan* p) {
         L.red_src = take((size_t)p->red_cap * p->rec_alloc_words * 16);
         L.gather = (p->flags & P2P_PLAN_GATHER_MAP) ? take((size_t)p->red_cap * 4) : 0;
     }
+    L.io_pos = L.io_str = L.io_out = 0;
+    if (p->flags & P2P_PLAN_HOST_IO) {
+        const size_t per = (p->kind == P2P_GRAVITY) ? 4 : (size_t)8 * p->nrhs;   // strength bytes per particle
+        L.io_pos = take((size_t)n * 12);
+        L.io_str = take((size_t)n * per);
+        L.io_out = take((size_t)n * ((p->kind == P2P_GRAVITY) ? 16 : per));   // gravity: phi, then acc
+    }
     L.total = off;
 }
 
@@ -186,7 +193,7 @@ int plan_init(Plan* p, int kind, int64_t n, int level, const float* lo, float ed
     if (kind == P2P_GRAVITY && nrhs != 1) return P2P_ERR_INVALID_ARG;
     if (nrhs < 1 || nrhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
     if (flags & ~(P2P_PLAN_GATHER_MAP | P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING | P2P_PLAN_ADJOINT |
-                  P2P_PLAN_PERIODIC | P2P_PLAN_SYMMETRIC))
+                  P2P_PLAN_PERIODIC | P2P_PLAN_SYMMETRIC | P2P_PLAN_HOST_IO))
         return P2P_ERR_INVALID_ARG;
     if ((flags & P2P_PLAN_SYMMETRIC) &&
         (is_pairtask(layout) || (flags & P2P_PLAN_ADJOINT) || (kind == P2P_HELMHOLTZ && nrhs > 2)))
@@ -314,7 +321,11 @@ int p2p_plan_destroy(p2p_plan* h) {
     Plan* p = &h->p;
     if (p->timing)
         for (int ph = 0; ph < P2P_PHASE_COUNT; ++ph)
-            for (int e = 0; e < 2; ++e) cudaEventDestroy(p->ev[ph][e]);
+            for (int e = 0; e < 2; ++e)
+                if (p->ev[ph][e]) cudaEventDestroy(p->ev[ph][e]);
+    if (p->io_fork) cudaEventDestroy(p->io_fork);
+    if (p->io_join) cudaEventDestroy(p->io_join);
+    if (p->io_stream) cudaStreamDestroy(p->io_stream);
     delete h;
     return P2P_OK;
 }
@@ -462,6 +473,77 @@ int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void
         if (st) return st;
     }
     ev_end(p, P2P_PHASE_OPERATOR, s);
+    return P2P_OK;
+}
+
+// The transfer phase and the collect phase of a host-buffer step: the
+// strengths' copy is forked onto the plan's own stream (after the work already
+// queued on `s`) and joined before the restructuring, so it overlaps the
+// position copy and the tree build.
+static int host_inputs(p2p_plan* h, const float* pos, const void* str, size_t str_bytes, void* ws, size_t ws_bytes,
+                       cudaStream_t s) {
+    Plan* p = &h->p;
+    const Layout& L = p->L;
+    float* dpos = at<float>(ws, L.io_pos);
+    void* dstr = at<unsigned char>(ws, L.io_str);
+    if (!p->io_stream) {   // created on first use (on the current device)
+        P2P_CUDA_TRY(cudaStreamCreateWithFlags(&p->io_stream, cudaStreamNonBlocking));
+        P2P_CUDA_TRY(cudaEventCreateWithFlags(&p->io_fork, cudaEventDisableTiming));
+        P2P_CUDA_TRY(cudaEventCreateWithFlags(&p->io_join, cudaEventDisableTiming));
+    }
+    P2P_CUDA_TRY(cudaEventRecord(p->io_fork, s));
+    P2P_CUDA_TRY(cudaStreamWaitEvent(p->io_stream, p->io_fork, 0));
+    P2P_CUDA_TRY(cudaMemcpyAsync(dstr, str, str_bytes, cudaMemcpyHostToDevice, p->io_stream));
+    P2P_CUDA_TRY(cudaEventRecord(p->io_join, p->io_stream));
+    P2P_CUDA_TRY(cudaMemcpyAsync(dpos, pos, (size_t)p->n * 12, cudaMemcpyHostToDevice, s));
+    int st = p2p_tree_build(h, dpos, ws, ws_bytes, s);
+    // join the side stream even when the build failed, so it never outlives the call
+    const cudaError_t e = cudaStreamWaitEvent(s, p->io_join, 0);
+    if (st) return st;
+    if (e != cudaSuccess) return P2P_ERR_CUDA;
+    return p2p_restructure(h, dpos, dstr, ws, ws_bytes, s);
+}
+
+static int host_check(p2p_plan* h, int kind, const void* a, const void* b, const void* c, void* ws, size_t ws_bytes) {
+    if (!h || !a || !b || !c) return P2P_ERR_INVALID_ARG;
+    const Plan* p = &h->p;
+    if (p->kind != kind) return P2P_ERR_INVALID_ARG;
+    if (!(p->flags & P2P_PLAN_HOST_IO)) return P2P_ERR_UNSUPPORTED;
+    return check_ws(p, ws, ws_bytes);
+}
+
+int p2p_gravity_host(p2p_plan* h, float eps, const float* pos, const float* mass, float* phi, float* acc, void* ws,
+                     size_t ws_bytes, void* stream) {
+    int st = host_check(h, P2P_GRAVITY, pos, mass, phi, ws, ws_bytes);
+    if (st) return st;
+    if (!acc) return P2P_ERR_INVALID_ARG;
+    const Plan* p = &h->p;
+    const int64_t n = p->n;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = host_inputs(h, pos, mass, (size_t)n * 4, ws, ws_bytes, s);
+    if (st) return st;
+    float* dphi = at<float>(ws, p->L.io_out);
+    float* dacc = dphi + n;
+    st = p2p_gravity(h, eps, dphi, dacc, ws, ws_bytes, stream);
+    if (st) return st;
+    P2P_CUDA_TRY(cudaMemcpyAsync(phi, dphi, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    P2P_CUDA_TRY(cudaMemcpyAsync(acc, dacc, (size_t)n * 12, cudaMemcpyDeviceToHost, s));
+    return P2P_OK;
+}
+
+int p2p_helmholtz_host(p2p_plan* h, float k, const float* pos, const void* q, void* u, void* ws, size_t ws_bytes,
+                       void* stream) {
+    int st = host_check(h, P2P_HELMHOLTZ, pos, q, u, ws, ws_bytes);
+    if (st) return st;
+    const Plan* p = &h->p;
+    const size_t bytes = (size_t)p->n * 8 * p->nrhs;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = host_inputs(h, pos, q, bytes, ws, ws_bytes, s);
+    if (st) return st;
+    void* du = at<unsigned char>(ws, p->L.io_out);
+    st = p2p_helmholtz(h, k, du, ws, ws_bytes, stream);
+    if (st) return st;
+    P2P_CUDA_TRY(cudaMemcpyAsync(u, du, bytes, cudaMemcpyDeviceToHost, s));
     return P2P_OK;
 }
 

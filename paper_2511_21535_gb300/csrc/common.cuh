@@ -52,6 +52,7 @@ struct Layout {                        // byte offsets inside the workspace
         ent_box, pt_start, part_start, part,   // pair tasks (red_src/gather hold the task stream)
         task_kind, mirror,                      // symmetric tasks (layout or plan flag)
         bslot,                                  // plan flag: source-sum slots of mutual entries
+        io_pos, io_str, io_out,                 // P2P_PLAN_HOST_IO: device copies of inputs and outputs
         total;
 };
 
@@ -95,6 +96,9 @@ struct Plan {
     cudaEvent_t ev[P2P_PHASE_COUNT][2];
     int ev_valid[P2P_PHASE_COUNT];
     int timing;
+    // P2P_PLAN_HOST_IO: the stream that copies the strengths, and its fork / join events
+    cudaStream_t io_stream;
+    cudaEvent_t io_fork, io_join;
 };
 
 // launch accounting

@@ -18,6 +18,7 @@ GRAVITY, HELMHOLTZ = 0, 1
 LAYOUTS = {"indirect": 0, "redundant": 1, "auto": 2, "pairtask": 3, "symmetric": 4}
 PLAN_GATHER_MAP, PLAN_PLAIN_FP32, PLAN_TIMING, PLAN_ADJOINT, PLAN_PERIODIC = 0x1, 0x2, 0x4, 0x8, 0x10
 PLAN_SYMMETRIC = 0x20
+PLAN_HOST_IO = 0x40
 FLAG_DOMAIN, FLAG_TIMEOUT, FLAG_CAPACITY, FLAG_LATTICE = 0x1, 0x2, 0x4, 0x8
 
 ARRAYS = {"perm": (0, torch.int32), "box_key": (1, torch.int32), "box_start": (2, torch.int32),
@@ -37,7 +38,8 @@ EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_
            "p2p_batch_create", "p2p_batch_destroy", "p2p_batch_workspace_bytes", "p2p_batch_build",
            "p2p_batch_set_tuning", "p2p_batch_run", "p2p_batch_autotune", "p2p_batch_capture",
            "p2p_batch_launch", "p2p_batch_counters", "p2p_selftest_bounded_wait",
-           "p2p_plan_set_grid", "p2p_build_checked", "p2p_fail_host_allocs")
+           "p2p_plan_set_grid", "p2p_build_checked", "p2p_fail_host_allocs", "p2p_gravity_host",
+           "p2p_helmholtz_host")
 
 
 class P2PError(RuntimeError):
@@ -106,6 +108,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_plan_set_grid": (I, [P, F, I]),
         "p2p_build_checked": (I, []),
         "p2p_fail_host_allocs": (I, [I]),
+        "p2p_gravity_host": (I, [P, F, P, P, P, P, P, SZ, P]),
+        "p2p_helmholtz_host": (I, [P, F, P, P, P, P, SZ, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -166,7 +170,7 @@ class Plan:
     def __init__(self, kind: str, n: int, level: int, lo, edge: float, nrhs: int = 1,
                  layout: str = "redundant", gather_map: bool = False, plain_fp32: bool = False,
                  timing: bool = False, adjoint: bool = False, periodic: bool = False, symmetric: bool = False,
-                 device=None, workspace: torch.Tensor | None = None):
+                 host_io: bool = False, device=None, workspace: torch.Tensor | None = None):
         lib = load()
         self.kind = kind
         self.n = int(n)
@@ -178,7 +182,8 @@ class Plan:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         flags = (PLAN_GATHER_MAP if gather_map else 0) | (PLAN_PLAIN_FP32 if plain_fp32 else 0) | \
                 (PLAN_TIMING if timing else 0) | (PLAN_ADJOINT if adjoint else 0) | \
-                (PLAN_PERIODIC if periodic else 0) | (PLAN_SYMMETRIC if symmetric else 0)
+                (PLAN_PERIODIC if periodic else 0) | (PLAN_SYMMETRIC if symmetric else 0) | \
+                (PLAN_HOST_IO if host_io else 0)
         lo_arr = (ctypes.c_float * 3)(*[float(v) for v in lo])
         h = ctypes.c_void_p()
         kid = {"gravity": GRAVITY, "helmholtz": HELMHOLTZ}[kind]
@@ -284,6 +289,30 @@ class Plan:
                                           _ptr(grad_acc), _ptr(gm), _ptr(gx), w, b, _stream(stream)),
                "p2p_gravity_adjoint")
         return gm, gx
+
+    # -- one step from host buffers (host_io plans) ---------------------------
+    def gravity_host(self, eps: float, pos, mass, phi, acc, stream=None):
+        """Host tensors in and out (pinned for asynchronous copies): positions [n, 3],
+        masses [n] -> phi [n], acc [n, 3].  Asynchronous on the stream."""
+        cpu = torch.device("cpu")
+        _need(pos, torch.float32, (self.n, 3), cpu)
+        _need(mass, torch.float32, (self.n,), cpu)
+        _need(phi, torch.float32, (self.n,), cpu)
+        _need(acc, torch.float32, (self.n, 3), cpu)
+        w, b = self._wsp()
+        _check(load().p2p_gravity_host(self._h, float(eps), _ptr(pos), _ptr(mass), _ptr(phi), _ptr(acc), w, b,
+                                       _stream(stream)), "p2p_gravity_host")
+
+    def helmholtz_host(self, k: float, pos, q, u, stream=None):
+        """Host tensors in and out (pinned for asynchronous copies): positions [n, 3],
+        q [nrhs, n] complex64 -> u [nrhs, n].  Asynchronous on the stream."""
+        cpu = torch.device("cpu")
+        _need(pos, torch.float32, (self.n, 3), cpu)
+        _need(q, torch.complex64, (self.nrhs, self.n), cpu)
+        _need(u, torch.complex64, (self.nrhs, self.n), cpu)
+        w, b = self._wsp()
+        _check(load().p2p_helmholtz_host(self._h, float(k), _ptr(pos), _ptr(q), _ptr(u), w, b, _stream(stream)),
+               "p2p_helmholtz_host")
 
     # -- inspection ---------------------------------------------------------
     def counters(self, stream=None, check: bool = False) -> dict:

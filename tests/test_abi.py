@@ -90,6 +90,28 @@ def test_plan_argument_checks(lib):
     assert lib.p2p_plan_destroy(None) == 0
 
 
+def test_host_io_plan(lib):
+    """P2P_PLAN_HOST_IO: the workspace holds device copies of the inputs and outputs
+    (12 n + 4 n + 16 n bytes for gravity); the host entry points refuse plans
+    without it before any device work."""
+    lib.p2p_plan_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+    st, h0 = _create(lib, n=10000)
+    st1, h1 = _create(lib, n=10000, flags=0x40)
+    assert st == 0 and st1 == 0 and h1.value
+    b0, b1 = ctypes.c_size_t(), ctypes.c_size_t()
+    lib.p2p_plan_workspace_bytes(h0, ctypes.byref(b0))
+    lib.p2p_plan_workspace_bytes(h1, ctypes.byref(b1))
+    assert b1.value - b0.value >= 32 * 10000
+    P = ctypes.c_void_p
+    lib.p2p_gravity_host.argtypes = [P, ctypes.c_float, P, P, P, P, P, ctypes.c_size_t, P]
+    buf = (ctypes.c_float * 8)()
+    ptr = ctypes.cast(buf, P)
+    assert lib.p2p_gravity_host(h0, 1e-3, ptr, ptr, ptr, ptr, ptr, b0.value, None) == 5
+    assert lib.p2p_gravity_host(h1, 1e-3, None, ptr, ptr, ptr, ptr, b1.value, None) == 1
+    lib.p2p_plan_destroy.argtypes = [P]
+    lib.p2p_plan_destroy(h0)
+
+
 def test_workspace_layout_scales(lib):
     lib.p2p_plan_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
     sizes = {}
