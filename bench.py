@@ -478,6 +478,79 @@ def evaluation_variant(prob, layout: str, dev, steps: int, mufu_peak: float):
                          "unit": "G evaluations/s", "frac": evals_per_s / mufu_peak}}
 
 
+PIPE_COPIES = 32   # rotating input copies: 32 x (positions + strengths) > L2
+
+
+def pipelined_batches(prob, layout: str, dev, steps: int, ctas_per_sm: int = 3):
+    """Throughput of a stream of independent batches with two in flight: two
+    plans on two streams, each step a captured graph of the whole path (tree,
+    restructuring, P2P) on one of PIPE_COPIES rotating input copies, so the
+    collect phase of one batch runs while the other's P2P kernel does.  With
+    fewer P2P CTAs per SM (ctas_per_sm) the collect kernels find room on the SMs."""
+    import torch
+    from paper_2511_21535_gb300 import p2p
+    plans = []
+    for _ in range(2):
+        pl = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
+                      periodic=bool(prob.extra.get("periodic")), device=dev)
+        if ctas_per_sm and prob.kind == "helmholtz" and prob.nrhs <= 2:
+            pl.set_tuning(4, 64, ctas_per_sm, 4)   # the default tuning with fewer CTAs per SM
+        plans.append(pl)
+    pos0 = torch.from_numpy(prob.pos).to(dev)
+    str0 = torch.from_numpy(prob.strength).to(dev)
+    inputs = [(pos0.clone(), str0.clone()) for _ in range(PIPE_COPIES)]
+    if prob.kind == "gravity":
+        outs = [(torch.empty(prob.n, device=dev), torch.empty(prob.n, 3, device=dev)) for _ in range(2)]
+    else:
+        outs = [torch.empty(prob.nrhs, prob.n, dtype=torch.complex64, device=dev) for _ in range(2)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+
+    def step(pl, inp, out):
+        pl.tree_build(inp[0])
+        pl.restructure(inp[0], inp[1])
+        if prob.kind == "gravity":
+            pl.gravity(prob.eps, out[0], out[1])
+        else:
+            pl.helmholtz(prob.k, out)
+
+    for i in range(4):
+        with torch.cuda.stream(streams[i % 2]):
+            step(plans[i % 2], inputs[i], outs[i % 2])
+    torch.cuda.synchronize()
+    graphs = []
+    for c in range(PIPE_COPIES):   # copy c runs on plan / stream c % 2
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(streams[c % 2]):
+            with torch.cuda.graph(g, stream=streams[c % 2]):
+                step(plans[c % 2], inputs[c], outs[c % 2])
+        graphs.append(g)
+    torch.cuda.synchronize()
+
+    def run(n):
+        main = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        for st in streams:
+            st.wait_stream(main)
+        for i in range(n):
+            with torch.cuda.stream(streams[i % 2]):
+                graphs[i % PIPE_COPIES].replay()
+        for st in streams:
+            main.wait_stream(st)
+        b.record(main)
+        b.synchronize()
+        return a.elapsed_time(b) / n
+
+    run(min(steps, 20))
+    ms = run(steps)
+    c = plans[0].counters(check=True)
+    units = c["pairs"] * (prob.nrhs if prob.kind == "helmholtz" else 1)
+    return {"value": units / (ms * 1e-3), "unit": "pairs/s", "ms_per_step": ms, "steps": steps,
+            "batches_in_flight": 2, "streams": 2,
+            "ctas_per_sm": ctas_per_sm if (prob.kind == "helmholtz" and prob.nrhs <= 2) else "auto",
+            "inputs": f"{PIPE_COPIES} rotating input copies ({PIPE_COPIES * (prob.pos.nbytes + prob.strength.nbytes) >> 20} MiB > L2)"}
+
+
 def dbim_forward_adjoint(dev, steps: int, edge_points: int = 128):
     """Differentiable 128^3 configuration: L = ||P(chi u_inc) - d||^2 and dL/dchi through
     the autograd wrapper (forward P2P + hand-written adjoint P2P), per step."""
@@ -743,6 +816,8 @@ def main():
                 and args.layout in ("redundant", "indirect")):
             mufu_peak = res["roofline"]["peak"] * 1e9
             res["symmetric"] = evaluation_variant(prob, args.layout, dev, 100, mufu_peak)
+        if args.evaluation == "one-sided" and not args.pattern and args.layout in ("redundant", "indirect"):
+            res["pipelined"] = pipelined_batches(prob, args.layout, dev, min(max(args.steps, 20), 400))
     if rank == 0:
         if not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
