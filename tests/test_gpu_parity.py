@@ -244,6 +244,22 @@ def test_helmholtz_parity(dev, name, layout, tpl, tile, group):
     assert rel_l2(u, ou) <= TOL_COMPLEX
 
 
+@pytest.mark.parametrize("plain", [False, True])
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+def test_multi_rhs_equals_single_rhs_bitwise(dev, plain, layout):
+    """Several right-hand sides per pass accumulate each RHS with packed
+    (real, imaginary) FMAs in the scalar order: every RHS of an 8-RHS plan equals,
+    bit for bit, a one-RHS plan on that RHS with the same tuning (32-record tiles:
+    the tile wide 8-RHS records get, so the compensated sums fold at the same points)."""
+    prob = wl.grid_helmholtz(edge_points=24, nrhs=8, seed=4)
+    _, u8 = run_helmholtz(prob, dev, layout, 2, 32, plain=plain, group=4)
+    for r in (0, 3, 7):
+        one = wl.Problem(prob.name, prob.pos, prob.strength[r:r + 1].copy(), prob.level, prob.lo, prob.edge,
+                         "helmholtz", k=prob.k)
+        _, u1 = run_helmholtz(one, dev, layout, 2, 32, plain=plain, group=4)
+        np.testing.assert_array_equal(u8[r], u1[0])
+
+
 @pytest.mark.parametrize("group", [1, 4])
 def test_helmholtz_plain_fp32(dev, group):
     prob = wl.grid_helmholtz(edge_points=24, nrhs=3, seed=6)
