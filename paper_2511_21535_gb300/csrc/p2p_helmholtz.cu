@@ -80,8 +80,10 @@ int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* per
     while (r0 < p->nrhs) {
         const int left = p->nrhs - r0;
         const int R = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-        int st0 = fill32(&a.hdr->work_ctr, 0u, 1, s);
-        if (st0) return st0;
+        if (r0 > 0) {   // the first pass follows build_items, which zeroed the operator section
+            const int st0 = fill32(&a.hdr->work_ctr, 0u, 1, s);
+            if (st0) return st0;
+        }
         // symmetric tasks run only in the compensated hardware-sin/cos kernel
         if (a.task_kind && (precise || !comp)) return P2P_ERR_UNSUPPORTED;
         int st = precise ? launch_helm_precise(p, a, perm, k, r0, R, u, s)

@@ -186,8 +186,10 @@ int launch_helmholtz_pattern(const Plan* p, const LoopArgs& a, const int32_t* pe
     while (r0 < p->nrhs) {
         const int left = p->nrhs - r0;
         const int R = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-        int st0 = fill32(&a.hdr->work_ctr, 0u, 1, s);
-        if (st0) return st0;
+        if (r0 > 0) {   // the first pass follows build_items, which zeroed the operator section
+            const int st0 = fill32(&a.hdr->work_ctr, 0u, 1, s);
+            if (st0) return st0;
+        }
         int st;
         if (p->group >= 2)
             st = K == 2 ? pat_r<2, 4>(p, a, perm, table, r0, R, out, s) : pat_r<1, 4>(p, a, perm, table, r0, R, out, s);

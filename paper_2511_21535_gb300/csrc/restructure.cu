@@ -27,11 +27,13 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 
 __global__ void k_records_gravity(const float* __restrict__ pos, const float* __restrict__ mass,
                                   const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec,
-                                  unsigned long long* __restrict__ lb, int64_t lb_words, const Header* __restrict__ hdr) {
+                                  unsigned long long* __restrict__ lb, int64_t lb_words, Header* __restrict__ hdr) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
+    if (s < (int64_t)(kOpSectionOffset - kRestrSectionOffset) / 4)   // the restructuring's header counts
+        reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(hdr) + kRestrSectionOffset)[s] = 0u;
     if (s >= n || (hdr->flags & P2P_FLAG_CAPACITY)) return;   // an inconsistent imported structure
     const int64_t i = perm[s];
     rec[s] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass[i]);
@@ -91,6 +93,8 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
+    if (s < (int64_t)(kOpSectionOffset - kRestrSectionOffset) / 4)   // the restructuring's header counts
+        reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(hdr) + kRestrSectionOffset)[s] = 0u;
     if (s >= n || (hdr->flags & P2P_FLAG_CAPACITY)) return;   // an inconsistent imported structure
     const int64_t i = perm[s];
     float4* r = rec + s * words;
@@ -117,11 +121,13 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
 __global__ void k_records_helm_adjoint(const float* __restrict__ pos, const float2* __restrict__ q,
                                        const float2* __restrict__ gbar, const int32_t* __restrict__ perm, int64_t n,
                                        int nrhs, int words, float4* __restrict__ rec,
-                                  unsigned long long* __restrict__ lb, int64_t lb_words, const Header* __restrict__ hdr) {
+                                  unsigned long long* __restrict__ lb, int64_t lb_words, Header* __restrict__ hdr) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
+    if (s < (int64_t)(kOpSectionOffset - kRestrSectionOffset) / 4)   // the restructuring's header counts
+        reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(hdr) + kRestrSectionOffset)[s] = 0u;
     if (s >= n || (hdr->flags & P2P_FLAG_CAPACITY)) return;   // an inconsistent imported structure
     const int64_t i = perm[s];
     float4* r = rec + s * words;
@@ -141,11 +147,13 @@ __global__ void k_records_helm_adjoint(const float* __restrict__ pos, const floa
 __global__ void k_records_grav_adjoint(const float* __restrict__ pos, const float* __restrict__ mass,
                                        const float* __restrict__ gphi, const float* __restrict__ gacc,
                                        const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec,
-                                  unsigned long long* __restrict__ lb, int64_t lb_words, const Header* __restrict__ hdr) {
+                                  unsigned long long* __restrict__ lb, int64_t lb_words, Header* __restrict__ hdr) {
     pdl_wait();
     pdl_release();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < lb_words) lb[s] = 0ull;   // chained-scan scratch of the box statistics
+    if (s < (int64_t)(kOpSectionOffset - kRestrSectionOffset) / 4)   // the restructuring's header counts
+        reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(hdr) + kRestrSectionOffset)[s] = 0u;
     if (s >= n || (hdr->flags & P2P_FLAG_CAPACITY)) return;   // an inconsistent imported structure
     const int64_t i = perm[s];
     rec[2 * s] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], mass[i]);
@@ -472,9 +480,7 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
     float4* rec = at<float4>(ws, L.src);
     const bool red = p->layout == P2P_LAYOUT_REDUNDANT;
     int32_t* S = at<int32_t>(ws, L.box_S);
-    int st0 = fill32(reinterpret_cast<char*>(hdr) + kRestrSectionOffset, 0u,
-                     (kOpSectionOffset - kRestrSectionOffset) / 4, s);
-    if (st0) return st0;
+    // (the restructuring section of the header was zeroed by the records kernel)
     int32_t* red_start = red ? at<int32_t>(ws, L.red_start) : nullptr;
     unsigned long long* lb = at<unsigned long long>(ws, L.lookback) + lb_regions(p->n, bc).stats;   // stream bounds
     const LbRegions lr = lb_regions(p->n, bc);

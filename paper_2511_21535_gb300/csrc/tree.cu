@@ -27,11 +27,14 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // that follow (lb_words words; the grid always covers them).
 __global__ void k_keys(const float* __restrict__ pos, int64_t n, float lo0, float lo1, float lo2,
                        float scale, int level, uint32_t* __restrict__ keys, Header* hdr,
-                       unsigned long long* __restrict__ lb, int64_t lb_words) {
+                       unsigned long long* __restrict__ lb, int64_t lb_words, int32_t* __restrict__ table,
+                       int64_t table_words) {
     pdl_wait();
     pdl_release();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < lb_words) lb[i] = 0ull;
+    // the dense key -> box table starts empty (-1); the box CSR kernel fills it
+    for (int64_t t = i; t < table_words; t += (int64_t)gridDim.x * blockDim.x) table[t] = -1;
     if (i >= n) return;
     const float side = (float)(1 << level);
     const int32_t cmax = (1 << level) - 1;
@@ -331,8 +334,10 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
 
     const LbRegions lr = lb_regions(n, p->box_cap);
     unsigned long long* lb = at<unsigned long long>(ws, L.lookback);
+    int32_t* table = p->use_table ? at<int32_t>(ws, L.table) : nullptr;
+    const int64_t table_words = p->use_table ? ((int64_t)1 << (3 * p->level)) : 0;
     P2P_CUDA_TRY(launch_pdl(k_keys, blocks_for(n, 256), 256, 0, s, pos, n, p->lo[0], p->lo[1], p->lo[2], p->scale,
-                            p->level, ka, hdr, lb, lr.tree_words));
+                            p->level, ka, hdr, lb, lr.tree_words, table, table_words));
     P2P_LAUNCH_CHECK();
 
     // radix passes over 3*level key bits, equal digit widths <= 8 bits
@@ -364,15 +369,9 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
         P2P_CUDA_TRY(cudaMemcpyAsync(perm, vin, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
 
-    // box CSR (and the dense key -> box table, cleared first)
+    // box CSR (and the dense key -> box table, cleared by k_keys)
     uint32_t* box_key = at<uint32_t>(ws, L.box_key);
     int32_t* box_start = at<int32_t>(ws, L.box_start);
-    int32_t* table = nullptr;
-    if (p->use_table) {
-        table = at<int32_t>(ws, L.table);
-        const int st = fill32(table, 0xffffffffu, (int64_t)1 << (3 * p->level), s);
-        if (st) return st;
-    }
     P2P_CUDA_TRY(launch_pdl(k_box_csr, blocks_for(n, kCsrTile), kCsrThreads, 0, s, skey, n, box_key, box_start,
                             table, lb + lr.csr, hdr));
     P2P_LAUNCH_CHECK();
