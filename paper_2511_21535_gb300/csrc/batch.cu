@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "nvtx_range.cuh"
 #include "p2p_loop.cuh"
 
 namespace p2p {
@@ -190,6 +191,7 @@ int p2p_batch_workspace_bytes(const p2p_batch* h, size_t* bytes) {
 }
 
 int p2p_batch_build(p2p_batch* h, const float* pos, void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("p2p_batch_build");
     if (!h || !pos || (reinterpret_cast<uintptr_t>(pos) & 3u)) return P2P_ERR_INVALID_ARG;
     Batch& b = h->b;
     int st = batch_ws(b, ws, ws_bytes);
@@ -259,6 +261,7 @@ int p2p_batch_set_tuning(p2p_batch* h, int layout, int targets_per_lane, int til
 
 int p2p_batch_run(p2p_batch* h, float k, const float* pos, const void* q, const void* y, void* u, void* g, void* ws,
                   size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("p2p_batch_run");
     if (!h || !pos || !q || !u) return P2P_ERR_INVALID_ARG;
     Batch& b = h->b;
     if (b.pair && (!y || !g)) return P2P_ERR_INVALID_ARG;
@@ -274,6 +277,7 @@ int p2p_batch_run(p2p_batch* h, float k, const float* pos, const void* q, const 
 
 int p2p_batch_autotune(p2p_batch* h, float k, const float* pos, const void* q, const void* y, void* u, void* g,
                        void* ws, size_t ws_bytes, void* stream, int* best, float* best_ms) {
+    NvtxRange nvtx_range("p2p_batch_autotune");
     if (!h || !best || !best_ms) return P2P_ERR_INVALID_ARG;
     Batch& b = h->b;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -324,6 +328,7 @@ int p2p_batch_autotune(p2p_batch* h, float k, const float* pos, const void* q, c
 
 int p2p_batch_capture(p2p_batch* h, float k, const float* pos, const void* q, const void* y, void* u, void* g, void* ws,
                       size_t ws_bytes) {
+    NvtxRange nvtx_range("p2p_batch_capture");
     if (!h || !pos || !q || !u) return P2P_ERR_INVALID_ARG;
     Batch& b = h->b;
     if (b.pair && (!y || !g)) return P2P_ERR_INVALID_ARG;
@@ -360,6 +365,7 @@ int p2p_batch_capture(p2p_batch* h, float k, const float* pos, const void* q, co
 }
 
 int p2p_batch_launch(p2p_batch* h, void* stream) {
+    NvtxRange nvtx_range("p2p_batch_launch");
     if (!h) return P2P_ERR_INVALID_ARG;
     Batch& b = h->b;
     if (!b.exec) return P2P_ERR_STATE;

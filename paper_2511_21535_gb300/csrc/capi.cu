@@ -5,6 +5,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "nvtx_range.cuh"
 #include "p2p_loop.cuh"
 
 struct p2p_plan {
@@ -375,6 +376,7 @@ int p2p_plan_set_grid(p2p_plan* h, float grid_h, int points_per_box) {
 }
 
 int p2p_tree_build(p2p_plan* h, const float* pos, void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("p2p_tree_build");
     if (!h || !pos || (reinterpret_cast<uintptr_t>(pos) & 3u)) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     int st = check_ws(p, ws, ws_bytes);
@@ -389,6 +391,7 @@ int p2p_tree_build(p2p_plan* h, const float* pos, void* ws, size_t ws_bytes, voi
 int p2p_tree_import(p2p_plan* h, const int32_t* perm, const int32_t* box_start, int32_t n_boxes,
                     const int32_t* nbr_start, const int32_t* nbr_idx, int32_t n_nbr, void* ws, size_t ws_bytes,
                     void* stream) {
+    NvtxRange nvtx_range("p2p_tree_import");
     if (!h || !perm || !box_start || !nbr_start || !nbr_idx) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     int st = check_ws(p, ws, ws_bytes);
@@ -399,6 +402,7 @@ int p2p_tree_import(p2p_plan* h, const int32_t* perm, const int32_t* box_start, 
 }
 
 int p2p_restructure(p2p_plan* h, const float* pos, const void* strength, void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("p2p_restructure");
     if (!h || !pos || !strength || (reinterpret_cast<uintptr_t>(pos) & 3u)) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if ((reinterpret_cast<uintptr_t>(strength) & (p->kind == P2P_GRAVITY ? 3u : 7u)) != 0) return P2P_ERR_INVALID_ARG;
@@ -413,6 +417,7 @@ int p2p_restructure(p2p_plan* h, const float* pos, const void* strength, void* w
 }
 
 int p2p_gravity(p2p_plan* h, float eps, float* phi, float* acc, void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("p2p_gravity");
     if (!h || !phi || !acc) return P2P_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(phi) & 3u) || (reinterpret_cast<uintptr_t>(acc) & 3u)) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
@@ -440,6 +445,7 @@ int p2p_gravity(p2p_plan* h, float eps, float* phi, float* acc, void* ws, size_t
 }
 
 int p2p_helmholtz(p2p_plan* h, float k, void* u, void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("p2p_helmholtz");
     if (!h || !u || (reinterpret_cast<uintptr_t>(u) & 7u)) return P2P_ERR_INVALID_ARG;
     Plan* p = &h->p;
     if (p->kind != P2P_HELMHOLTZ || !(k == k) || !(fabsf(k) < 1.0e30f)) return P2P_ERR_INVALID_ARG;
@@ -514,6 +520,7 @@ static int host_check(p2p_plan* h, int kind, const void* a, const void* b, const
 
 int p2p_gravity_host(p2p_plan* h, float eps, const float* pos, const float* mass, float* phi, float* acc, void* ws,
                      size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("p2p_gravity_host");
     int st = host_check(h, P2P_GRAVITY, pos, mass, phi, ws, ws_bytes);
     if (st) return st;
     if (!acc) return P2P_ERR_INVALID_ARG;
@@ -533,6 +540,7 @@ int p2p_gravity_host(p2p_plan* h, float eps, const float* pos, const float* mass
 
 int p2p_helmholtz_host(p2p_plan* h, float k, const float* pos, const void* q, void* u, void* ws, size_t ws_bytes,
                        void* stream) {
+    NvtxRange nvtx_range("p2p_helmholtz_host");
     int st = host_check(h, P2P_HELMHOLTZ, pos, q, u, ws, ws_bytes);
     if (st) return st;
     const Plan* p = &h->p;
@@ -549,6 +557,7 @@ int p2p_helmholtz_host(p2p_plan* h, float k, const float* pos, const void* q, vo
 
 int p2p_helmholtz_adjoint(p2p_plan* h, float k, const float* pos, const void* q, const void* gbar, void* grad_q,
                           float* grad_pos, void* ws, size_t ws_bytes, void* stream) {
+    NvtxRange nvtx_range("p2p_helmholtz_adjoint");
     if (!h || !pos || !gbar || (!grad_q && !grad_pos)) return P2P_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(gbar) & 7u) || (reinterpret_cast<uintptr_t>(grad_q) & 7u) ||
         (reinterpret_cast<uintptr_t>(grad_pos) & 3u) || (reinterpret_cast<uintptr_t>(pos) & 3u))
@@ -593,6 +602,7 @@ int p2p_helmholtz_adjoint(p2p_plan* h, float k, const float* pos, const void* q,
 int p2p_gravity_adjoint(p2p_plan* h, float eps, const float* pos, const float* mass, const float* grad_phi,
                         const float* grad_acc, float* grad_mass, float* grad_pos, void* ws, size_t ws_bytes,
                         void* stream) {
+    NvtxRange nvtx_range("p2p_gravity_adjoint");
     if (!h || !pos || !mass || !grad_phi || !grad_acc || (!grad_mass && !grad_pos)) return P2P_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(pos) | reinterpret_cast<uintptr_t>(mass) | reinterpret_cast<uintptr_t>(grad_phi) |
          reinterpret_cast<uintptr_t>(grad_acc) | reinterpret_cast<uintptr_t>(grad_mass) |
