@@ -182,9 +182,9 @@ int p2p_plan_workspace_bytes(const p2p_plan* plan, size_t* bytes);
  * of one box.  Helmholtz items hold at most 64 targets: with 4, a lane holds
  * four of them and takes every other source of a tile (two source groups per
  * warp; one-sided compensated passes of one or two right-hand sides, others
- * run as with 2; symmetric plans take 2).  tile: source records per shared-memory stage (32, 64
- * or 128; records wider than 16 bytes halve it until a stage holds at most
- * 160 words, 32 at least).  ctas_per_sm: 0 = as many as fit.  warps_per_item: 1, 2 or 4 warps
+ * run as with 2; symmetric plans take 2).  tile: source records per shared-memory stage (32, 48,
+ * 64 or 128; records wider than 16 bytes reduce it until a stage holds at
+ * most 160 words, 32 at least).  ctas_per_sm: 0 = as many as fit.  warps_per_item: 1, 2 or 4 warps
  * share one item, splitting its source tiles and adding their partial sums
  * in warp order.  Returns P2P_ERR_INVALID_ARG on values outside these sets.
  */

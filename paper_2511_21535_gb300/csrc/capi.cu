@@ -137,7 +137,7 @@ LoopArgs loop_args(const Plan* p, void* ws, int words) {
     a.words = words;
     // wide records: halve the tile until a stage stays within ~2.5 KB (32 at least)
     int tile = p->tile;
-    while (tile > 32 && words * tile > 160) tile >>= 1;
+    while (tile > 32 && words * tile > 160) tile = tile > 64 ? tile / 2 : 32;
     a.tile = tile;
     a.box_start = at<int32_t>(ws, L.box_start);
     a.nbr_start = at<int32_t>(ws, L.nbr_start);
@@ -342,7 +342,8 @@ int p2p_plan_set_tuning(p2p_plan* h, int targets_per_lane, int tile, int ctas_pe
     Plan* p = &h->p;
     const bool tpl_ok = targets_per_lane == 1 || targets_per_lane == 2 || targets_per_lane == 4;
     const bool g_ok = warps_per_item == 1 || warps_per_item == 2 || warps_per_item == 4;
-    if (!tpl_ok || !g_ok || (tile != 32 && tile != 64 && tile != 128) || ctas_per_sm < 0 || ctas_per_sm > 32)
+    if (!tpl_ok || !g_ok || (tile != 32 && tile != 48 && tile != 64 && tile != 128) || ctas_per_sm < 0 ||
+        ctas_per_sm > 32)
         return P2P_ERR_INVALID_ARG;
     p->tpl = targets_per_lane;
     p->tile = tile;

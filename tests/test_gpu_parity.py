@@ -235,7 +235,7 @@ HELM_CASES = {
 @pytest.mark.parametrize("name", sorted(HELM_CASES))
 @pytest.mark.parametrize("layout", ["indirect", "redundant"])
 @pytest.mark.parametrize("tpl,tile,group", [(1, 32, 1), (2, 64, 2), (2, 64, 4), (1, 64, 4), (4, 64, 4), (4, 32, 1),
-                                            (4, 64, 2)])
+                                            (4, 64, 2), (4, 48, 4), (2, 48, 2)])
 def test_helmholtz_parity(dev, name, layout, tpl, tile, group):
     prob = HELM_CASES[name]()
     _, u = run_helmholtz(prob, dev, layout, tpl, tile, group=group)
