@@ -77,7 +77,9 @@ def test_plan_argument_checks(lib):
     assert nbp.value > nb.value + 27 * 1000 * 16   # task stream (54 n records) and partial results
     lib.p2p_plan_set_tuning.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
     assert lib.p2p_plan_set_tuning(h, 3, 64, 0, 1) == 1
-    assert lib.p2p_plan_set_tuning(h, 2, 48, 0, 1) == 1
+    assert lib.p2p_plan_set_tuning(h, 2, 40, 0, 1) == 1
+    assert lib.p2p_plan_set_tuning(h, 2, 256, 0, 1) == 1
+    assert lib.p2p_plan_set_tuning(h, 2, 48, 0, 1) == 0
     assert lib.p2p_plan_set_tuning(h, 2, 64, 0, 3) == 1
     assert lib.p2p_plan_set_tuning(h, 4, 32, 2, 4) == 0
     # operator before the tree: state error is checked before any device work
