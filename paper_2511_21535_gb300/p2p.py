@@ -163,8 +163,23 @@ def _stream(stream=None):
 class Plan:
     """One problem shape (n, level, domain, kernel, layout) and its workspace.
 
-    The workspace is one torch uint8 tensor on the plan's device; every
-    intermediate array of the pipeline lives inside it.
+    kind: "gravity" (softened 1/r: potential and acceleration) or "helmholtz"
+    (e^{ikr}/(4 pi r) on complex sources, nrhs right-hand sides).  n particles
+    in the cube [lo, lo + edge)^3, uniform octree of 2^level boxes per edge.
+    layout: "redundant" (per-box contiguous source streams, the paper's data
+    redundancy), "indirect" (per-neighbour ranges of the box-ordered records),
+    "pairtask" (one task per (box, neighbour) with partial results reduced
+    afterwards) or "symmetric" (pair tasks evaluated once for both particles).
+    Flags: gather_map (keep the restructuring's source index map), plain_fp32
+    (no compensated sums), timing (CUDA-event phase timers, see timing()),
+    adjoint (room for the adjoint records), periodic (toroidal boundaries),
+    symmetric (each pair of a small box pair evaluated once on a target-owned
+    layout), host_io (device copies of inputs and outputs for the *_host calls).
+
+    The workspace is one torch uint8 tensor on the plan's device (allocated
+    here unless given); every intermediate array of the pipeline lives inside
+    it.  Calls are asynchronous on the current (or given) stream; device-side
+    errors are reported by counters().
     """
 
     def __init__(self, kind: str, n: int, level: int, lo, edge: float, nrhs: int = 1,
@@ -207,6 +222,8 @@ class Plan:
 
     # -- knobs --------------------------------------------------------------
     def set_tuning(self, targets_per_lane: int, tile: int, ctas_per_sm: int = 0, warps_per_item: int = 4):
+        """Targets per lane (1, 2, 4), source records per shared-memory stage (32, 48, 64,
+        128), CTAs per SM (0: as many as fit), warps cooperating on one work item (1, 2, 4)."""
         _check(load().p2p_plan_set_tuning(self._h, targets_per_lane, tile, ctas_per_sm, warps_per_item),
                "p2p_plan_set_tuning")
 
