@@ -321,6 +321,19 @@ def _sample_targets(prob, plan, count, seed):
     return np.unique(np.concatenate([rng.choice(prob.n, count, replace=False), heavy]))
 
 
+@pytest.mark.parametrize("name", ["grid_helmholtz_64", "plummer_gravity_4m"])
+def test_structures_bit_exact_full_size(dev, name):
+    """The bench workloads at full size: keys, permutation, boxes, neighbour lists,
+    redundant stream bounds, self offsets, gather map and pair count equal the
+    oracle's, bit for bit (4,194,304 particles, 605,596 boxes, 102 M stream records)."""
+    prob = wl.grid_helmholtz() if name == "grid_helmholtz_64" else wl.plummer_gravity()
+    if prob.kind == "gravity":
+        plan, _, _ = run_gravity(prob, dev, "redundant", gather=True)
+    else:
+        plan, _ = run_helmholtz(prob, dev, "redundant")
+    check_structures(plan, prob, "redundant")
+
+
 def test_plummer_gravity_full_sampled(dev):
     prob = wl.plummer_gravity()
     for layout in ("indirect", "redundant"):
