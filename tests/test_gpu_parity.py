@@ -321,12 +321,13 @@ def _sample_targets(prob, plan, count, seed):
     return np.unique(np.concatenate([rng.choice(prob.n, count, replace=False), heavy]))
 
 
-@pytest.mark.parametrize("name", ["grid_helmholtz_64", "plummer_gravity_4m"])
+@pytest.mark.parametrize("name", ["grid_helmholtz_64", "grid_helmholtz_128", "plummer_gravity_4m"])
 def test_structures_bit_exact_full_size(dev, name):
     """The bench workloads at full size: keys, permutation, boxes, neighbour lists,
     redundant stream bounds, self offsets, gather map and pair count equal the
-    oracle's, bit for bit (4,194,304 particles, 605,596 boxes, 102 M stream records)."""
-    prob = wl.grid_helmholtz() if name == "grid_helmholtz_64" else wl.plummer_gravity()
+    oracle's, bit for bit (up to 4,194,304 particles, 605,596 boxes, 102 M stream records)."""
+    prob = {"grid_helmholtz_64": wl.grid_helmholtz, "grid_helmholtz_128": lambda: wl.grid_helmholtz(edge_points=128),
+            "plummer_gravity_4m": wl.plummer_gravity}[name]()
     if prob.kind == "gravity":
         plan, _, _ = run_gravity(prob, dev, "redundant", gather=True)
     else:
