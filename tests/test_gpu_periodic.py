@@ -100,6 +100,22 @@ def check_structures(plan, prob, layout):
                                       r["gather_idx"])
 
 
+@pytest.mark.parametrize("layout,symmetric", [("redundant", False), ("indirect", False), ("indirect", True)])
+def test_periodic_grid_helmholtz_64_full(dev, layout, symmetric):
+    """The bench's --periodic Helmholtz workload at full size (452,722,688 pairs
+    through 27 images) against the FP64 periodic oracle, one-sided and symmetric."""
+    prob = wl.grid_helmholtz()
+    plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, layout=layout, periodic=True,
+                    symmetric=symmetric, device=dev)
+    pos = torch.from_numpy(prob.pos).to(dev)
+    plan.tree_build(pos)
+    plan.restructure(pos, torch.from_numpy(prob.strength).to(dev))
+    u = plan.helmholtz(prob.k).cpu().numpy()
+    ou, pairs = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k, periodic=True)
+    assert plan.counters(check=True)["pairs"] == pairs == 452_722_688
+    assert rel_l2(u, ou) <= TOL_COMPLEX
+
+
 def test_periodic_structures_bit_exact_full_size(dev):
     """The 4.2 M-point Plummer sphere with toroidal boundaries (the bench's
     --periodic gravity workload): wrapped neighbour lists, image codes,
