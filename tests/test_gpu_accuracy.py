@@ -59,10 +59,12 @@ def test_accuracy_plummer_gravity(dev, plain):
     assert ep <= (1e-5 if not plain else 1e-4) and ea <= (1e-5 if not plain else 1e-4)
 
 
-@pytest.mark.parametrize("mode", ["symmetric", "pattern", "indirect", "pairtask", "four_per_lane"])
+@pytest.mark.parametrize("mode", ["symmetric", "pattern", "indirect", "pairtask", "four_per_lane",
+                                  "symmetric_pairtask"])
 def test_accuracy_grid_helmholtz_64_variants(dev, mode):
     prob = wl.grid_helmholtz()
-    kw = dict(layout="indirect") if mode == "indirect" else dict(layout="pairtask") if mode == "pairtask" else {}
+    kw = {"indirect": dict(layout="indirect"), "pairtask": dict(layout="pairtask"),
+          "symmetric_pairtask": dict(layout="symmetric")}.get(mode, {})
     plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, symmetric=(mode == "symmetric"),
                     device=dev, **kw)
     if mode == "four_per_lane":
