@@ -285,13 +285,15 @@ static void orc_ctx_free(orc_ctx* c) {
     free(c->nbr_start); free(c->nbr_idx); free(c->nbr_img); free(c->box_of);
 }
 
-static int orc_periodic = 0;   /* set by the *_periodic entry points around a call */
-
-static int orc_ctx_build(orc_ctx* c, const float* pos, int64_t n, int level, const float* lo, float edge) {
+/* Tree context of one call; periodic != 0 wraps the neighbour cells and
+ * records an image code per neighbour entry.  Every call builds its own
+ * context, so concurrent calls (open or periodic) do not interact. */
+static int orc_ctx_build(orc_ctx* c, const float* pos, int64_t n, int level, const float* lo, float edge,
+                         int periodic) {
     memset(c, 0, sizeof(*c));
     c->n = n;
     c->edge = (double)edge;
-    if (orc_periodic) {
+    if (periodic) {
         c->nbr_img = (int32_t*)malloc((size_t)n * 27 * sizeof(int32_t));
         if (!c->nbr_img) return ORC_ERR_NOMEM;
     }
@@ -306,7 +308,7 @@ static int orc_ctx_build(orc_ctx* c, const float* pos, int64_t n, int level, con
         return ORC_ERR_NOMEM;
     }
     int64_t e;
-    int st = orc_tree_ex(pos, n, level, lo, edge, orc_periodic, c->perm, c->box_key, c->box_start, &c->nb,
+    int st = orc_tree_ex(pos, n, level, lo, edge, periodic, c->perm, c->box_key, c->box_start, &c->nb,
                          c->nbr_start, c->nbr_idx, c->nbr_img, &e);
     if (st != ORC_OK) { orc_ctx_free(c); return st; }
     for (int32_t b = 0; b < c->nb; ++b)
@@ -319,11 +321,11 @@ static int orc_ctx_build(orc_ctx* c, const float* pos, int64_t n, int level, con
  * phi[nt], acc[nt*3] in double.  eps is the float32 softening widened.
  * Optionally counts the ordered pairs visited into *pairs.
  */
-int orc_gravity(const float* pos, const float* mass, int64_t n, int level, const float* lo,
-                float edge, float eps, const int64_t* targets, int64_t nt,
-                double* phi, double* acc, int64_t* pairs) {
+static int orc_gravity_ex(const float* pos, const float* mass, int64_t n, int level, const float* lo,
+                          float edge, float eps, const int64_t* targets, int64_t nt,
+                          double* phi, double* acc, int64_t* pairs, int periodic) {
     orc_ctx c;
-    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge, periodic);
     if (st != ORC_OK) return st;
     if (!targets) nt = n;
     const double e2 = (double)eps * (double)eps;
@@ -366,12 +368,12 @@ int orc_gravity(const float* pos, const float* mass, int64_t n, int level, const
  * q: complex64 sources laid out [nrhs][n][re,im] (float32); u: [nrhs][nt][re,im]
  * in double.  k is the float32 wavenumber widened.
  */
-int orc_helmholtz(const float* pos, const float* q, int nrhs, int64_t n, int level,
-                  const float* lo, float edge, float k, const int64_t* targets, int64_t nt,
-                  double* u, int64_t* pairs) {
+static int orc_helmholtz_ex(const float* pos, const float* q, int nrhs, int64_t n, int level,
+                            const float* lo, float edge, float k, const int64_t* targets, int64_t nt,
+                            double* u, int64_t* pairs, int periodic) {
     if (nrhs < 1) return ORC_ERR_ARG;
     orc_ctx c;
-    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge, periodic);
     if (st != ORC_OK) return st;
     if (!targets) nt = n;
     const double kk = (double)k;
@@ -410,11 +412,23 @@ int orc_helmholtz(const float* pos, const float* q, int nrhs, int64_t n, int lev
     return ORC_OK;
 }
 
+int orc_gravity(const float* pos, const float* mass, int64_t n, int level, const float* lo,
+                float edge, float eps, const int64_t* targets, int64_t nt,
+                double* phi, double* acc, int64_t* pairs) {
+    return orc_gravity_ex(pos, mass, n, level, lo, edge, eps, targets, nt, phi, acc, pairs, 0);
+}
+
+int orc_helmholtz(const float* pos, const float* q, int nrhs, int64_t n, int level,
+                  const float* lo, float edge, float k, const int64_t* targets, int64_t nt,
+                  double* u, int64_t* pairs) {
+    return orc_helmholtz_ex(pos, q, nrhs, n, level, lo, edge, k, targets, nt, u, pairs, 0);
+}
+
 /* Number of ordered pairs P = sum_b n_b S_b - n (self pairs excluded). */
 int orc_pair_count(const float* pos, int64_t n, int level, const float* lo, float edge,
                    int64_t* pairs) {
     orc_ctx c;
-    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge, 0);
     if (st != ORC_OK) return st;
     int64_t p = 0;
     for (int32_t b = 0; b < c.nb; ++b) {
@@ -451,7 +465,7 @@ int orc_helmholtz_adjoint(const float* pos, const float* q, const float* gbar, i
                           double* grad_x) {
     if (nrhs < 1) return ORC_ERR_ARG;
     orc_ctx c;
-    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge, 0);
     if (st != ORC_OK) return st;
     const double kk = (double)k;
     const double inv4pi = 1.0 / (4.0 * ORC_PI);
@@ -508,7 +522,7 @@ int orc_gravity_adjoint(const float* pos, const float* mass, const float* gphi, 
                         int64_t n, int level, const float* lo, float edge, float eps,
                         double* grad_m, double* grad_x) {
     orc_ctx c;
-    int st = orc_ctx_build(&c, pos, n, level, lo, edge);
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge, 0);
     if (st != ORC_OK) return st;
     const double e2 = (double)eps * (double)eps;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -561,18 +575,12 @@ int orc_gravity_periodic(const float* pos, const float* mass, int64_t n, int lev
                          float edge, float eps, const int64_t* targets, int64_t nt,
                          double* phi, double* acc, int64_t* pairs) {
     if (level < 2) return ORC_ERR_ARG;
-    orc_periodic = 1;
-    int st = orc_gravity(pos, mass, n, level, lo, edge, eps, targets, nt, phi, acc, pairs);
-    orc_periodic = 0;
-    return st;
+    return orc_gravity_ex(pos, mass, n, level, lo, edge, eps, targets, nt, phi, acc, pairs, 1);
 }
 
 int orc_helmholtz_periodic(const float* pos, const float* q, int nrhs, int64_t n, int level,
                            const float* lo, float edge, float k, const int64_t* targets, int64_t nt,
                            double* u, int64_t* pairs) {
     if (level < 2) return ORC_ERR_ARG;
-    orc_periodic = 1;
-    int st = orc_helmholtz(pos, q, nrhs, n, level, lo, edge, k, targets, nt, u, pairs);
-    orc_periodic = 0;
-    return st;
+    return orc_helmholtz_ex(pos, q, nrhs, n, level, lo, edge, k, targets, nt, u, pairs, 1);
 }

@@ -171,6 +171,124 @@ def test_redundant_identities():
     assert oracle.pair_count(p.pos, p.level, p.lo, p.edge) == int((occ * S).sum()) - 3000
 
 
+def decode_morton(keys, level):
+    """Cells of Morton keys, de-interleaved bit by bit (x from key bit 3b, y 3b+1, z 3b+2)."""
+    keys = np.asarray(keys, np.int64)
+    c = np.zeros((keys.size, 3), np.int64)
+    for b in range(level):
+        for a in range(3):
+            c[:, a] |= ((keys >> (3 * b + a)) & 1) << b
+    return c
+
+
+@pytest.mark.parametrize("n,level,seed", [(3000, 3, 1), (4000, 4, 2)])
+def test_redundant_stream_order_bruteforce(n, level, seed):
+    """The redundant stream of each target box, rebuilt from the box keys alone:
+    the sorted particles of every box at Chebyshev cell distance <= 1 (found by
+    testing all box pairs), boxes in ascending Morton key, each box's particles
+    in sorted order; red_self is the offset of the box's own block.  Uneven
+    occupancies (a clustered sphere) so that a wrong neighbour order changes
+    the stream."""
+    p = wl.plummer_gravity(n=n, level=level, eps=1e-3, seed=seed)
+    t = oracle.tree(p.pos, p.level, p.lo, p.edge)
+    r = oracle.redundant(t)
+    keys, bs = t["box_key"].astype(np.int64), t["box_start"]
+    assert np.all(np.diff(keys) > 0)
+    cell = decode_morton(keys, level)
+    occ = np.diff(bs)
+    assert len(np.unique(occ)) > 3
+    pos = 0
+    for b in range(t["n_boxes"]):
+        near = np.nonzero(np.abs(cell - cell[b]).max(axis=1) <= 1)[0]     # ascending index = ascending key
+        expect = np.concatenate([np.arange(bs[c], bs[c + 1]) for c in near])
+        assert r["red_start"][b] == pos
+        np.testing.assert_array_equal(r["gather_idx"][pos:pos + expect.size], expect)
+        own = int(np.nonzero(near == b)[0][0])
+        assert r["red_self"][b] == occ[near[:own]].sum()
+        pos += expect.size
+    assert r["total"] == pos == r["red_start"][-1]
+
+
+def f32_cells(pos, level, lo, edge):
+    """The boxing rule in numpy float32 (each operation rounded to float32):
+    s = 2^L / edge, u = (x - lo) * s, cell = min(floor(u), 2^L - 1)."""
+    f = np.float32
+    s = f(f(1 << level) / f(edge))
+    u = (np.asarray(pos, f) - np.asarray(lo, f)) * s
+    assert u.dtype == np.float32
+    return np.minimum(np.floor(u).astype(np.int64), (1 << level) - 1), u
+
+
+def test_cells_offset_domain_near_faces():
+    """A shifted domain with a non-dyadic edge (lo != 0, edge = 2.7): points on
+    and within a few float32 ulps of every cell face, plus random points; the
+    oracle's cells equal the float32 rule evaluated by numpy, and the points
+    sit close enough to the faces that evaluating the same rule in float64
+    would box some of them differently."""
+    level, edge = 5, 2.7
+    lo = np.array([-0.37, 1.25, 3.1], np.float32)
+    side = 1 << level
+    f = np.float32
+    pts = []
+    for a in range(3):
+        faces = lo[a].astype(np.float64) + np.arange(side + 1) * (float(f(edge)) / side)
+        x = faces.astype(np.float32)
+        for k in range(-3, 4):
+            y = x.copy()
+            for _ in range(abs(k)):
+                y = np.nextafter(y, np.float32(np.inf if k > 0 else -np.inf))
+            pts.append((a, y))
+    rng = np.random.default_rng(17)
+    base = (lo + rng.random((1, 3), dtype=np.float32) * f(edge)).astype(np.float32)
+    rows = []
+    for a, y in pts:
+        blk = np.repeat(base, y.size, axis=0)
+        blk[:, a] = y
+        rows.append(blk)
+    rows.append((lo + rng.random((5000, 3), dtype=np.float32) * f(edge * 0.999)).astype(np.float32))
+    pos = np.concatenate(rows)
+    ref, u = f32_cells(pos, level, lo, edge)
+    ok = np.all((u >= 0) & (u <= side), axis=1)
+    assert ok.sum() > 5000 and (~ok).sum() > 0
+    cell, key = oracle.cells(pos[ok], level, lo, edge)
+    np.testing.assert_array_equal(cell, ref[ok])
+    np.testing.assert_array_equal(decode_morton(key, level), ref[ok])
+    u64 = (pos[ok].astype(np.float64) - lo.astype(np.float64)) * (side / float(f(edge)))
+    c64 = np.minimum(np.floor(u64).astype(np.int64), side - 1)
+    assert np.any(c64 != ref[ok])
+    for bad in pos[~ok][:20]:
+        with pytest.raises(RuntimeError):
+            oracle.cells(bad[None], level, lo, edge)
+
+
+def test_oracle_calls_are_reentrant():
+    """Open and periodic calls running at the same time in two host threads
+    (ctypes releases the interpreter lock) give the results of sequential calls."""
+    import threading
+    p = wl.uniform_gravity(n=6000, level=3, seed=12)
+    seq_open = oracle.gravity(p.pos, p.strength, p.level, p.lo, p.edge, p.eps)
+    seq_per = oracle.gravity(p.pos, p.strength, p.level, p.lo, p.edge, p.eps, periodic=True)
+    out = {}
+
+    def work(name, periodic):
+        res = []
+        for _ in range(4):
+            res.append(oracle.gravity(p.pos, p.strength, p.level, p.lo, p.edge, p.eps, periodic=periodic))
+        out[name] = res
+
+    th = [threading.Thread(target=work, args=("open", False)), threading.Thread(target=work, args=("per", True))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for name, ref in (("open", seq_open), ("per", seq_per)):
+        for res in out[name]:
+            np.testing.assert_array_equal(res[0], ref[0])
+            np.testing.assert_array_equal(res[1], ref[1])
+            assert res[2] == ref[2]
+    assert seq_per[2] > seq_open[2]
+
+
 # ---------------------------------------------------------------------------
 # sums
 # ---------------------------------------------------------------------------
