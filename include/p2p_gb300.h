@@ -264,10 +264,12 @@ int p2p_gravity(p2p_plan* plan, float eps, float* phi, float* acc, void* ws, siz
 
 /*
  * Compute + update -- Helmholtz.  Writes u complex64 [nrhs][n] in original
- * order.  k is the float32 wavenumber.  When k times the largest in-box
- * distance stays below 100 pi the sine and cosine use the hardware
- * approximation (absolute error below 1e-6 there); otherwise the accurate
- * library routines.  Pair-task plans reduce partial results as p2p_gravity.
+ * order.  k is the float32 wavenumber.  When |k| * r_max <= 32, with
+ * r_max = 2 sqrt(3) x box edge (the largest distance between points of
+ * neighbouring boxes), the sine and cosine use the hardware approximation
+ * (its error grows with the phase; the parity tests cover phases up to 31.6
+ * at the complex64 tolerance); otherwise the accurate library routines.
+ * Pair-task plans reduce partial results as p2p_gravity.
  * Symmetric plans need the hardware sine/cosine range and compensated
  * accumulation (otherwise P2P_ERR_UNSUPPORTED).
  */
