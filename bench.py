@@ -6,12 +6,19 @@ restructuring (box-ordered records, redundant per-box streams) -> P2P kernel
 (outputs written in original order).  The step is captured once in a CUDA
 graph and replayed (--no-graph launches it kernel by kernel); phase times come
 from CUDA events the library records on the launching stream (external event
-nodes inside the graph).  Default workload: the Helmholtz near
-field on a 64^3 grid at lambda/10 spacing, 4^3-point leaf boxes, one complex
-right-hand side, redundant layout.
+nodes inside the graph).
+
+Default workload: the clustered gravity case, 4,194,304 particles (a Plummer
+sphere of scale radius 0.05 plus a 10 % uniform background) on a level-7
+octree with eps = 1e-4, redundant layout; the indirect layout on the same
+workload is reported beside it (`indirect`, `layouts_compared`), and the
+64^3 Helmholtz grid (both layouts, the symmetric evaluation, two batches in
+flight) as the `grid_helmholtz_64` object.  The batched forward + adjoint of
+64 uneven grids x 8 right-hand sides against per-instance launches is the
+`batched` object, the differentiable 128^3 step the `adjoint` object.
 
 `e2e` is the same step from pinned host buffers through the library's
-host-buffer call (p2p_helmholtz_host / p2p_gravity_host): the positions' and
+host-buffer call (p2p_gravity_host / p2p_helmholtz_host): the positions' and
 strengths' copies to the device and the results' copy back are inside the
 timed region.
 
@@ -203,22 +210,43 @@ class ClockSampler:
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def run_gpu(args, rank, world, local_rank):
+def roofline_of(prob, kern_ms: float, evals: int, pipes: dict, f_mhz: float, sms: int, pattern: bool = False):
+    """Pipe roofline of the P2P kernel: pipe lanes per SM per clock (measured by
+    p2p_measure_pipes) x SMs x sampled SM clock / operations per pair evaluation."""
+    mufu_rate = min(pipes["mufu_rsqrt"], pipes["mufu_sin"])
+    if prob.kind == "helmholtz" and pattern:
+        # table lookups: one 8-byte shared load per lane and pair; 128 B/clk/SM of shared bandwidth
+        pipe, per_pair, rate = "smem", 8.0, 128.0
+    elif prob.kind == "helmholtz" and prob.nrhs <= 2:
+        pipe, per_pair, rate = "mufu", 3.0, mufu_rate      # rsqrt, sin, cos per geometric pair
+    elif prob.kind == "helmholtz":
+        pipe, per_pair, rate = "fp32", 12.0 + 4.0 * prob.nrhs, pipes["fp32"]
+    else:
+        pipe, per_pair, rate = "fp32", 13.0, pipes["fp32"]
+    peak = rate * sms * f_mhz * 1e6 / per_pair
+    achieved = evals / (kern_ms * 1e-3)
+    return {"bound": "alu", "pipe": pipe, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+            "frac": achieved / peak, "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms,
+            "evaluations_per_launch": evals,
+            "peak_source": "pipe rates measured by p2p_measure_pipes x SMs x sampled SM clock"}
+
+
+def measure_arm(prob, layout: str, args, dev, pipes: dict, clk, steps: int, warmup: int, symmetric: bool = False,
+                pattern: bool = False, e2e: bool = True):
+    """One layout of one workload: the whole step (tree, restructuring, P2P
+    kernel with the update to original order) captured in one CUDA graph and
+    replayed `steps` times (L2 flushed between steps), phase times from the
+    plan's events, and the same step end to end from pinned host buffers
+    through p2p_*_host.  Returns the arm's record (the plan is released)."""
     import torch
     from paper_2511_21535_gb300 import p2p
 
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    prob = make_problem(args.workload, args.periodic)
-    layout = args.layout
-    # symmetric evaluation applies to the target-owned layouts in direct mode with <= 2 right-hand sides
-    symmetric = (args.evaluation == "symmetric" and not args.pattern and layout in ("redundant", "indirect")
-                 and (prob.kind == "gravity" or prob.nrhs <= 2))
     plan = p2p.Plan(prob.kind, prob.n, prob.level, prob.lo, prob.edge, nrhs=prob.nrhs, layout=layout,
-                    timing=True, periodic=args.periodic, symmetric=symmetric, host_io=True, device=dev)
+                    timing=True, periodic=bool(prob.extra.get("periodic")), symmetric=symmetric, host_io=e2e,
+                    device=dev)
     if args.tpl:
         plan.set_tuning(args.tpl, args.tile, args.ctas, args.group)
-    if args.pattern:
+    if pattern:
         plan.set_grid(wl.SPACING, wl.LEAF_EDGE_POINTS)
     pos = torch.from_numpy(prob.pos).to(dev)
     strength = torch.from_numpy(prob.strength).to(dev)
@@ -228,33 +256,26 @@ def run_gpu(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def make_step(pl):
-        def step():
-            pl.tree_build(pos)
-            pl.restructure(pos, strength)
-            if prob.kind == "gravity":
-                pl.gravity(prob.eps, out_a, out_b)
-            else:
-                pl.helmholtz(prob.k, out_u)
-        return step
+    def step():
+        plan.tree_build(pos)
+        plan.restructure(pos, strength)
+        if prob.kind == "gravity":
+            plan.gravity(prob.eps, out_a, out_b)
+        else:
+            plan.helmholtz(prob.k, out_u)
 
-    step = make_step(plan)
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    smi_id = vis.split(",")[local_rank].strip() if vis else str(local_rank)
-    clk = ClockSampler(smi_id).__enter__()
-    time.sleep(0.5)
-    pipes = p2p.measure_pipes()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
     cnt = plan.counters(check=True)
-    pairs = cnt["pairs"] * (prob.nrhs if prob.kind == "helmholtz" else 1)
     geo_pairs = cnt["pairs"]
+    pairs = geo_pairs * (prob.nrhs if prob.kind == "helmholtz" else 1)
+    sym = symmetric or layout == "symmetric"
+    evals = cnt.get("evals", geo_pairs) if sym else geo_pairs
 
-    # optionally capture the whole step (tree, restructuring, operator) in one CUDA graph
-    run, graph, graph_note, launches_per_replay = step, None, None, None
-    graph_events = False
+    # capture the whole step (tree, restructuring, operator) in one CUDA graph
+    run, graph, graph_note, launches_per_replay, graph_events = step, None, None, None, False
     if args.graph:
         try:
             side = torch.cuda.Stream(device=dev)
@@ -268,7 +289,8 @@ def run_gpu(args, rank, world, local_rank):
             with torch.cuda.graph(graph):
                 step()
             launches_per_replay = p2p.launch_count() - l0
-            for _ in range(args.warmup):
+            for _ in range(warmup):
+                flush.zero_()
                 graph.replay()
             torch.cuda.synchronize()
             run = graph.replay
@@ -283,106 +305,147 @@ def run_gpu(args, rank, world, local_rank):
             graph, run = None, step
             graph_note = f"graph capture failed: {type(e).__name__}: {e}"[:200]
 
-    dist = world > 1
-    if dist:
+    if dist_active():
         import torch.distributed as td
         td.barrier()
     torch.cuda.synchronize()
     launches0 = p2p.launch_count()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     phases = {k: [] for k in p2p.PHASES}
     t_start = time.time()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.zero_()
         ev[i][0].record(stream)
         run()
         ev[i][1].record(stream)
         if graph is None or graph_events:
-            t = plan.timing()      # waits for this step's events (external event nodes in a graph)
-            for k, v in t.items():
+            for k, v in plan.timing().items():   # waits for this step's events
                 phases[k].append(v)
     torch.cuda.synchronize()
+    t_end = time.time()
     if graph is not None and not graph_events:
         # event timing inside a graph replay is not available: phase times
         # come from the same step launched on the stream, right after
-        for _ in range(min(args.steps, 50)):
+        for _ in range(min(steps, 50)):
             flush.zero_()
             step()
             for k, v in plan.timing().items():
                 phases[k].append(v)
         torch.cuda.synchronize()
-    t_end = time.time()
-    time.sleep(0.3)
-    clk.__exit__(None, None, None)
     launches = p2p.launch_count() - launches0
     if graph is not None:
-        launches = launches_per_replay * args.steps
+        launches = launches_per_replay * steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
-    value, ms, _ = replica_throughput(pairs, ms, dist, dev)
-
-    # end to end through the C ABI's host-buffer step (p2p_*_host) from pinned
-    # host buffers: H2D of positions and strengths (the strengths' copy
-    # overlapped with the tree build), full step, D2H of the results
-    hpos = torch.from_numpy(prob.pos).pin_memory()
-    hstr = torch.from_numpy(prob.strength).pin_memory()
-    if prob.kind == "gravity":
-        hout = (torch.empty(prob.n, dtype=torch.float32).pin_memory(),
-                torch.empty(prob.n, 3, dtype=torch.float32).pin_memory())
-    else:
-        hout = (torch.empty(prob.nrhs, prob.n, dtype=torch.complex64).pin_memory(),)
-
-    def e2e_step():
-        if prob.kind == "gravity":
-            plan.gravity_host(prob.eps, hpos, hstr, hout[0], hout[1])
-        else:
-            plan.helmholtz_host(prob.k, hpos, hstr, hout[0])
-
-    for _ in range(max(1, args.warmup)):
-        flush.zero_()
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_ms = []
-    for i in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e2e_step()
-        b.record(stream)
-        b.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    h2d = prob.pos.nbytes + prob.strength.nbytes
-    d2h = sum(t.numel() * t.element_size() for t in hout)
-    e2e_mean = sum(e2e_ms) / len(e2e_ms)
-    e2e_value, e2e_mean, _ = replica_throughput(pairs, e2e_mean, dist, dev)
-
-    kern_ms = sum(phases["kernel"]) / len(phases["kernel"])
     csum = clk.summary(t_start, t_end)
-    f_mhz = csum["sm_mhz"] or pipes["sm_mhz"] or 2070.0
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    mufu_rate = min(pipes["mufu_rsqrt"], pipes["mufu_sin"])
-    if prob.kind == "helmholtz" and args.pattern:
-        # table lookups: one 8-byte shared load per lane and pair; 128 B/clk/SM of shared bandwidth
-        pipe, per_pair = "smem", 8.0
-        peak = 128.0 * sms * f_mhz * 1e6 / per_pair
-    elif prob.kind == "helmholtz" and prob.nrhs <= 2:
-        pipe, per_pair = "mufu", 3.0        # rsqrt, sin, cos per geometric pair
-        peak = mufu_rate * sms * f_mhz * 1e6 / per_pair
-    elif prob.kind == "helmholtz":
-        pipe, per_pair = "fp32", 12.0 + 4.0 * prob.nrhs
-        peak = pipes["fp32"] * sms * f_mhz * 1e6 / per_pair
-    else:
-        pipe, per_pair = "fp32", 13.0
-        peak = pipes["fp32"] * sms * f_mhz * 1e6 / per_pair
-    # the default Helmholtz tuning for one or two right-hand sides, one-sided: four targets per lane
+    phases_ms = {k: (sum(v) / len(v) if v else None) for k, v in phases.items()}
+    rec = {"layout": layout, "evaluation": "symmetric" if sym else "one-sided", "ms_per_step": ms,
+           "pairs_per_step": pairs, "geometric_pairs": geo_pairs, "phases_ms": phases_ms,
+           "kernel_ms": phases_ms["kernel"], "gpu_launches": launches, "graph": graph_note, "clocks": csum,
+           "n_boxes": cnt["n_boxes"], "redundant_records": cnt["total_src"] if layout != "indirect" else 0}
+    rec["evaluations_per_launch"] = evals
+
+    if e2e:
+        # end to end through the C ABI's host-buffer step (p2p_*_host) from pinned
+        # host buffers: H2D of positions and strengths (the strengths' copy
+        # overlapped with the tree build), full step, D2H of the results
+        hpos = torch.from_numpy(prob.pos).pin_memory()
+        hstr = torch.from_numpy(prob.strength).pin_memory()
+        if prob.kind == "gravity":
+            hout = (torch.empty(prob.n, dtype=torch.float32).pin_memory(),
+                    torch.empty(prob.n, 3, dtype=torch.float32).pin_memory())
+        else:
+            hout = (torch.empty(prob.nrhs, prob.n, dtype=torch.complex64).pin_memory(),)
+
+        def e2e_step():
+            if prob.kind == "gravity":
+                plan.gravity_host(prob.eps, hpos, hstr, hout[0], hout[1])
+            else:
+                plan.helmholtz_host(prob.k, hpos, hstr, hout[0])
+
+        for _ in range(max(1, warmup)):
+            flush.zero_()
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for i in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        e2e_mean = sum(e2e_ms) / len(e2e_ms)
+        rec["e2e"] = {"value": pairs / (e2e_mean * 1e-3), "unit": "pairs/s",
+                      "h2d_bytes_per_step": prob.pos.nbytes + prob.strength.nbytes,
+                      "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in hout), "ms_per_step": e2e_mean}
+    rec["value"] = pairs / (ms * 1e-3)
+    rec["unit"] = "pairs/s"
+    del plan, pos, strength, flush
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return rec
+
+
+def kernel_of(prob, layout: str, args, symmetric: bool, pattern: bool):
+    """The dominant kernel of an arm, by the library's default tuning."""
     if prob.kind == "helmholtz":
         tile2d = not symmetric and layout != "symmetric" and prob.nrhs <= 2 and args.tpl in (0, 4)
     else:
         tile2d = not symmetric and layout != "symmetric" and args.tpl in (0, 2, 4)
-    kname = kernel_name(prob.kind, symmetric or layout == "symmetric", args.pattern, tile2d)
-    # pair evaluations the kernel performs (a symmetric plan's mutual evaluation serves two ordered pairs)
-    evals = cnt.get("evals", geo_pairs) if (symmetric or layout == "symmetric") else geo_pairs
-    achieved = evals / (kern_ms * 1e-3)
+    return kernel_name(prob.kind, symmetric or layout == "symmetric", pattern, tile2d)
+
+
+def arm_with_roofline(prob, layout, args, dev, pipes, clk, steps, warmup, symmetric=False, pattern=False):
+    import torch
+    rec = measure_arm(prob, layout, args, dev, pipes, clk, steps, warmup, symmetric, pattern)
+    f_mhz = rec["clocks"]["sm_mhz"] or pipes["sm_mhz"] or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    kname = kernel_of(prob, layout, args, symmetric, pattern)
+    roof = roofline_of(prob, rec["kernel_ms"], rec["evaluations_per_launch"], pipes, f_mhz, sms, pattern)
+    roof["kernel"] = kname
+    roof["traffic"] = (None if prob.extra.get("periodic") else
+                       kernel_traffic(kname, prob.name, layout, prob.n, symmetric or layout == "symmetric"))
+    roof["work_unit"] = ("pair evaluation (a mutual one serves two ordered pairs)"
+                         if rec["evaluations_per_launch"] != rec["geometric_pairs"] else "ordered pair")
+    rec["roofline"] = roof
+    return rec
+
+
+_DIST = {"on": False}
+
+
+def dist_active() -> bool:
+    return _DIST["on"]
+
+
+def run_gpu(args, rank, world, local_rank):
+    """The bench line: the selected workload and layout (default: the 4.2 M
+    Plummer sphere, redundant layout), the other target-owned layout on the
+    same workload beside it, and (for the default) the 64^3 Helmholtz grid
+    with both layouts as a secondary object."""
+    import torch
+    from paper_2511_21535_gb300 import p2p
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    _DIST["on"] = world > 1
+    prob = make_problem(args.workload, args.periodic)
+    layout = args.layout
+    # symmetric evaluation applies to the target-owned layouts in direct mode with <= 2 right-hand sides
+    symmetric = (args.evaluation == "symmetric" and not args.pattern and layout in ("redundant", "indirect")
+                 and (prob.kind == "gravity" or prob.nrhs <= 2))
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_id = vis.split(",")[local_rank].strip() if vis else str(local_rank)
+    clk = ClockSampler(smi_id).__enter__()
+    time.sleep(0.5)
+    pipes = p2p.measure_pipes()
+    main = arm_with_roofline(prob, layout, args, dev, pipes, clk, args.steps, args.warmup, symmetric, args.pattern)
+    value, ms, _ = replica_throughput(main["pairs_per_step"], main["ms_per_step"], world > 1, dev)
+    e2e = dict(main["e2e"])
+    e2e["value"], e2e["ms_per_step"], _ = replica_throughput(main["pairs_per_step"], e2e["ms_per_step"],
+                                                             world > 1, dev)
     result = {
         "metric": METRIC,
         "value": value,
@@ -397,26 +460,42 @@ def run_gpu(args, rank, world, local_rank):
         "dtype": "f32",
         "data": "synthetic",
         "config": workload_config(prob, layout, args.pattern, symmetric),
-        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
-        "roofline": {"bound": "alu", "pipe": pipe, "kernel": kname,
-                     "achieved": achieved / 1e9,
-                     "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak,
-                     "traffic": None if args.periodic else kernel_traffic(kname, prob.name, layout, prob.n,
-                                                                          symmetric),
-                     "ops_per_pair": per_pair, "sm_mhz": f_mhz, "sms": sms,
-                     "evaluations_per_launch": evals,
-                     "work_unit": ("pair evaluation (a mutual one serves two ordered pairs)"
-                                   if evals != geo_pairs else "ordered pair"),
-                     "peak_source": "pipe rates measured by p2p_measure_pipes x SMs x sampled SM clock",
-                     "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in pipes.items()}},
-        "phases_ms": {k: (sum(v) / len(v) if v else None) for k, v in phases.items()},
-        "pairs_per_step": pairs,
-        "gpu_launches": launches,
-        "graph": graph_note,
-        "clocks": csum,
+        "e2e": e2e,
+        "roofline": dict(main["roofline"], pipe_rates_per_sm_clk={k: round(v, 3) for k, v in pipes.items()}),
+        "phases_ms": main["phases_ms"],
+        "pairs_per_step": main["pairs_per_step"],
+        "gpu_launches": main["gpu_launches"],
+        "graph": main["graph"],
+        "clocks": main["clocks"],
     }
-    return result, prob
+    if not args.no_arms and not args.pattern and layout in ("redundant", "indirect"):
+        other = "indirect" if layout == "redundant" else "redundant"
+        arm = arm_with_roofline(prob, other, args, dev, pipes, clk, args.steps, args.warmup, symmetric)
+        result[other] = {k: arm[k] for k in ("value", "unit", "ms_per_step", "kernel_ms", "phases_ms", "e2e",
+                                             "roofline", "gpu_launches", "clocks")}
+        result["layouts_compared"] = {
+            "workload": prob.name, "unit": "pairs/s",
+            layout: {"step": value, "kernel": main["pairs_per_step"] / (main["kernel_ms"] * 1e-3),
+                     "e2e": e2e["value"], "restructure_ms": main["phases_ms"]["restructure"]},
+            other: {"step": arm["value"], "kernel": arm["pairs_per_step"] / (arm["kernel_ms"] * 1e-3),
+                    "e2e": arm["e2e"]["value"], "restructure_ms": arm["phases_ms"]["restructure"]}}
+    return result, prob, pipes, clk
+
+
+def grid_secondary(args, dev, pipes, clk, steps: int):
+    """The 64^3 Helmholtz grid (262,144 points at lambda/10, 4^3-point leaves,
+    one right-hand side): redundant and indirect arms with their rooflines,
+    the symmetric evaluation, and two batches in flight."""
+    prob = make_problem("grid_helmholtz", args.periodic)
+    out = {"workload": "grid_helmholtz_64", "config": workload_config(prob, "redundant")}
+    for layout in ("redundant", "indirect"):
+        rec = arm_with_roofline(prob, layout, args, dev, pipes, clk, steps, args.warmup)
+        out[layout] = {k: rec[k] for k in ("value", "unit", "ms_per_step", "kernel_ms", "phases_ms", "e2e",
+                                           "roofline", "gpu_launches", "clocks")}
+    mufu_peak = out["redundant"]["roofline"]["peak"] * 1e9
+    out["symmetric"] = evaluation_variant(prob, "redundant", dev, steps, mufu_peak)
+    out["pipelined"] = pipelined_batches(prob, "redundant", dev, min(max(steps, 20), 400))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -594,17 +673,20 @@ def dbim_forward_adjoint(dev, steps: int, edge_points: int = 128):
 # batched forward + adjoint (64 uneven grid instances x 8 RHS) vs plain launches
 # ---------------------------------------------------------------------------
 
-def batched_vs_plain(dev, steps: int, layout: str = "auto"):
+def batched_vs_plain(dev, steps: int, pipes: dict, f_mhz: float, layout: str = "auto"):
     """One CUDA-graph launch computing u = P q and g = conj(P) y for all 64
     instances, against per-instance plans doing restructure + forward +
-    adjoint with their own launches; both compensated FP32."""
+    adjoint with their own launches; both compensated FP32, and the plain
+    plans given the batch's autotuned layout and tuning, so that the ratio
+    isolates batching and the graph launch."""
     import torch
     from paper_2511_21535_gb300 import p2p
     probs = wl.batched_helmholtz()
     nrhs = probs[0].nrhs
     k = probs[0].k
     rng = np.random.default_rng(123)
-    batch = p2p.Batch([(p.n, p.level, p.lo, p.edge) for p in probs], nrhs, k, pair=True, layout=layout, device=dev)
+    batch = p2p.Batch([(p.n, p.level, p.lo, p.edge) for p in probs], nrhs, k, pair=True, layout=layout,
+                      timing=True, device=dev)
     pos = torch.from_numpy(np.concatenate([p.pos for p in probs])).to(dev)
     q = torch.from_numpy(np.concatenate([p.strength for p in probs], axis=1)).to(dev)
     y = torch.from_numpy(wl.complex_normal((nrhs, batch.N), rng)).to(dev)
@@ -627,12 +709,26 @@ def batched_vs_plain(dev, steps: int, layout: str = "auto"):
     batched_ms = a.elapsed_time(b) / steps
     batched_kernels = (p2p.launch_count() - lb) // steps
     pairs = batch.counters()["pairs"]
+    # the P2P kernel's share of a replay: phase events inside the graph
+    kern, restr = [], []
+    for _ in range(steps):
+        batch.launch()
+        t = batch.timing()
+        kern.append(t["kernel"])
+        restr.append(t["restructure"])
+    kernel_ms = sum(kern) / len(kern)
+    passes = -(-2 * nrhs // 8)                 # right-hand-side passes of at most 8 (forward and adjoint)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    per_pass = 12.0 + 4.0 * min(8, 2 * nrhs)
+    peak = pipes["fp32"] * sms * f_mhz * 1e6 / per_pass
+    achieved = pairs * passes / (kernel_ms * 1e-3)
 
-    # plain: one plan per instance, three calls per product
+    # plain: one plan per instance, three calls per product, the batch's tuning
     plans, per = [], []
     for i, pr in enumerate(probs):
         o0, o1 = batch.offsets[i], batch.offsets[i + 1]
-        pl = p2p.Plan("helmholtz", pr.n, pr.level, pr.lo, pr.edge, nrhs=nrhs, layout="indirect", device=dev)
+        pl = p2p.Plan("helmholtz", pr.n, pr.level, pr.lo, pr.edge, nrhs=nrhs, layout=best["layout"], device=dev)
+        pl.set_tuning(best["targets_per_lane"], best["tile"], 0, best["warps_per_item"])
         pp = pos[o0:o1].contiguous()
         pl.tree_build(pp)
         per.append((pp, q[:, o0:o1].contiguous(), y[:, o0:o1].contiguous(),
@@ -671,7 +767,19 @@ def batched_vs_plain(dev, steps: int, layout: str = "auto"):
             "plain_pairs_per_s": pairs * nrhs * 2 / (plain_ms * 1e-3),
             "batched_graph_launches_per_step": 1, "batched_kernels_per_step": int(batched_kernels),
             "plain_kernels_per_step": int(plain_launches),
+            "batched_phases_ms": {"restructure": sum(restr) / len(restr), "kernel": kernel_ms},
+            "roofline": {"bound": "alu", "pipe": "fp32", "kernel": "k_helmholtz (8 right-hand sides per pass)",
+                         "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G geometric pair-passes/s",
+                         "frac": achieved / peak, "ops_per_pair_pass": per_pass, "passes": passes,
+                         "sm_mhz": f_mhz, "sms": sms,
+                         "peak_source": "FP32 lanes per SM per clock measured by p2p_measure_pipes x SMs x "
+                                        "sampled SM clock"},
             "rel_l2_batched_vs_plain": {"u": diff_u, "g": diff_g}, "autotune": best,
+            "plain_arm": {"plans": len(plans), "layout": best["layout"],
+                          "tuning": {"targets_per_lane": best["targets_per_lane"], "tile": best["tile"],
+                                     "warps_per_item": best["warps_per_item"]},
+                          "calls_per_instance": "restructure, forward, adjoint (strengths only)",
+                          "tuned": "the batch's autotuned choice"},
             "build_s": build_s}
 
 
@@ -679,70 +787,95 @@ def batched_vs_plain(dev, steps: int, layout: str = "auto"):
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(prob, target_seconds: float, seed: int = 0):
-    """Time the FP64 oracle on a random sample of targets sized for ~target_seconds."""
+def oracle_context(prob):
+    """The oracle's tree of the whole workload, and the seconds its build took."""
     import oracle
-    rng = np.random.default_rng(seed)
+    oracle.build()
+    t0 = time.perf_counter()
+    ctx = oracle.Context(prob.pos, prob.level, prob.lo, prob.edge, periodic=bool(prob.extra.get("periodic")))
+    return ctx, time.perf_counter() - t0
+
+
+def oracle_sums(ctx, prob, tg) -> int:
+    """The oracle's sums at targets tg; returns the pair interactions (per right-hand side)."""
+    if prob.kind == "gravity":
+        return ctx.gravity(prob.strength, prob.eps, targets=tg)[2]
+    _, pairs = ctx.helmholtz(prob.strength, prob.k, targets=tg)
+    return pairs * prob.nrhs
+
+
+def oracle_target_count(ctx, prob, seconds: float, rng) -> int:
+    """Random targets per call for about `seconds` of the oracle's sums."""
     nt = 256
     while True:
         tg = rng.choice(prob.n, min(nt, prob.n), replace=False)
         t0 = time.perf_counter()
-        _, pairs = _oracle_eval(oracle, prob, tg)
+        oracle_sums(ctx, prob, tg)
         dt = time.perf_counter() - t0
-        if dt >= 0.25 * target_seconds or nt >= prob.n:
-            return pairs, dt, len(tg)
-        nt = min(prob.n, int(nt * max(2.0, 0.5 * target_seconds / max(dt, 1e-3))))
+        if dt >= 0.25 * seconds or nt >= prob.n:
+            return max(64, min(prob.n, int(nt * seconds / max(dt, 1e-6))))
+        nt = min(prob.n, int(nt * max(2.0, 0.5 * seconds / max(dt, 1e-3))))
 
 
-def _oracle_eval(oracle, prob, tg):
-    per = bool(prob.extra.get("periodic"))
-    if prob.kind == "gravity":
-        _, _, pairs = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps, targets=tg,
-                                     periodic=per)
-        return None, pairs
-    u, pairs = oracle.helmholtz(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.k, targets=tg,
-                                periodic=per)
-    return u, pairs * prob.nrhs
+def oracle_timed(ctx, tree_s, prob, seconds: float, seed: int, calls: int = 4):
+    """The oracle's sums at random target samples for about `seconds` (split over
+    `calls` calls), with the tree build charged in proportion to the targets
+    sampled (tree seconds x targets / n): the throughput of the oracle's whole
+    path on this workload, estimated from a bounded sample."""
+    rng = np.random.default_rng(seed)
+    nt = oracle_target_count(ctx, prob, seconds / calls, rng)
+    pairs, t, targets = 0, 0.0, 0
+    while t < seconds:
+        tg = rng.choice(prob.n, nt, replace=False)
+        t0 = time.perf_counter()
+        pairs += oracle_sums(ctx, prob, tg)
+        t += time.perf_counter() - t0
+        targets += nt
+    charged = t + tree_s * targets / prob.n
+    return pairs, charged, targets, nt
 
 
 def cpu_baseline(prob, seconds):
-    """The oracle as it stands, on random target samples, repeated until ~`seconds` of CPU work."""
+    """The oracle as it stands, on all host cores and on one core, on random
+    target samples of the workload (about `seconds` of sums each)."""
     import oracle
-    pairs, dt, nt = oracle_sample(prob, seconds)
-    rng = np.random.default_rng(7)
-    reps = 1
-    while dt < seconds:
-        tg = rng.choice(prob.n, nt, replace=False)
-        t0 = time.perf_counter()
-        _, p = _oracle_eval(oracle, prob, tg)
-        dt += time.perf_counter() - t0
-        pairs += p
-        reps += 1
-    return {"value": pairs / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle, {reps} x {nt} random targets of the same workload "
-                      f"({pairs} pairs in {dt:.1f} s)"}
+    ctx, tree_s = oracle_context(prob)
+    pairs, t, targets, nt = oracle_timed(ctx, tree_s, prob, seconds, 7)
+    cores = oracle.num_threads()
+    prev = oracle.set_num_threads(1)
+    try:
+        p1, t1, tg1, nt1 = oracle_timed(ctx, tree_s, prob, 0.5 * seconds, 8, calls=2)
+    finally:
+        oracle.set_num_threads(prev)
+    sample = ("FP64 oracle sums at {tg} random targets ({calls} calls of {nt}; {p} pairs) of the full workload, "
+              "plus its tree build of all {n} particles ({tree:.2f} s, charged x targets/n)")
+    return {"value": pairs / t, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "sample": sample.format(tg=targets, calls=targets // nt, nt=nt, p=pairs, n=prob.n, tree=tree_s),
+            "single_core": {"value": p1 / t1, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                            "sample": sample.format(tg=tg1, calls=tg1 // nt1, nt=nt1, p=p1, n=prob.n, tree=tree_s)}}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, each step the
+    oracle's sums at a random target sample of the workload sized so that the
+    whole run takes about two minutes, with the tree build of the whole
+    workload charged in proportion to the targets of the step."""
     if rank != 0:
         return None
     import oracle
     prob = make_problem(args.workload, args.periodic)
-    oracle.build()
+    ctx, tree_s = oracle_context(prob)
     rng = np.random.default_rng(1)
-    # size one step to ~2 s of oracle work
-    pairs1, dt1, nt1 = oracle_sample(prob, 2.0)
-    per_target = dt1 / nt1
-    nt = max(64, min(prob.n, int(2.0 / max(per_target, 1e-9))))
+    per_step = min(4.0, max(0.5, 120.0 / (args.warmup + args.steps)))
+    nt = oracle_target_count(ctx, prob, per_step, rng)
     samples = [rng.choice(prob.n, nt, replace=False) for _ in range(args.warmup + args.steps)]
     for tg in samples[:args.warmup]:
-        _oracle_eval(oracle, prob, tg)
+        oracle_sums(ctx, prob, tg)
     tot_pairs, tot_t = 0, 0.0
     for tg in samples[args.warmup:]:
         t0 = time.perf_counter()
-        _, p = _oracle_eval(oracle, prob, tg)
-        tot_t += time.perf_counter() - t0
-        tot_pairs += p
+        tot_pairs += oracle_sums(ctx, prob, tg)
+        tot_t += time.perf_counter() - t0 + tree_s * nt / prob.n
     value = tot_pairs / tot_t
     ms = 1e3 * tot_t / max(1, args.steps)
     return {
@@ -751,7 +884,8 @@ def run_reference(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(prob, args.layout),
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"each step: FP64 oracle on {nt} random targets of the workload"},
+                         "sample": f"each step: FP64 oracle sums at {nt} random targets of the workload, plus its "
+                                   f"tree build of all {prob.n} particles ({tree_s:.2f} s) charged x {nt}/{prob.n}"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -759,10 +893,12 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="grid_helmholtz")
+    ap.add_argument("--workload", default="plummer_gravity",
+                    help="plummer_gravity (default: 4,194,304 particles, level 7), grid_helmholtz (64^3), "
+                         "uniform_gravity (8,192), grid_helmholtz_128, plummer_gravity_1m, grid_helmholtz_r8")
     ap.add_argument("--layout", default="redundant", choices=["redundant", "indirect", "pairtask", "symmetric"])
     ap.add_argument("--tpl", type=int, default=0)
     ap.add_argument("--tile", type=int, default=64)
@@ -781,6 +917,11 @@ def main():
                          "also reports the symmetric evaluation of a Helmholtz workload")
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-arms", action="store_true",
+                    help="skip the other target-owned layout on the same workload")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 64^3 Helmholtz object (and, for a Helmholtz workload, the symmetric and "
+                         "pipelined objects)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -795,29 +936,32 @@ def main():
             print(json.dumps(res))
         return
 
-    # the oracle's process pool is created before any GPU work
     import torch
     if world > 1:
         import torch.distributed as td
         td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     from paper_2511_21535_gb300 import build as cuda_build
     cuda_build.build()
+    dev = torch.device("cuda", local_rank)
     if args.batched_only:
-        import torch as _t
-        print(json.dumps(batched_vs_plain(_t.device("cuda", local_rank), 10)))
+        from paper_2511_21535_gb300 import p2p
+        pipes = p2p.measure_pipes()
+        print(json.dumps(batched_vs_plain(dev, 10, pipes, pipes["sm_mhz"] or 2070.0)))
         return
-    res, prob = run_gpu(args, rank, world, local_rank)
-    if not args.no_batched:
-        import torch as _t
-        dev = _t.device("cuda", local_rank)
-        res["batched"] = batched_vs_plain(dev, 10)
-        res["adjoint"] = dbim_forward_adjoint(dev, 10)
-        if (prob.kind == "helmholtz" and prob.nrhs <= 2 and args.evaluation == "one-sided" and not args.pattern
-                and args.layout in ("redundant", "indirect")):
-            mufu_peak = res["roofline"]["peak"] * 1e9
-            res["symmetric"] = evaluation_variant(prob, args.layout, dev, 100, mufu_peak)
-        if args.evaluation == "one-sided" and not args.pattern and args.layout in ("redundant", "indirect"):
+    res, prob, pipes, clk = run_gpu(args, rank, world, local_rank)
+    f_mhz = res["clocks"]["sm_mhz"] or pipes["sm_mhz"] or 2070.0
+    try:
+        if not args.no_secondary and prob.name != "grid_helmholtz" and not args.pattern:
+            res["grid_helmholtz_64"] = grid_secondary(args, dev, pipes, clk, min(max(args.steps, 50), 300))
+        elif (prob.kind == "helmholtz" and prob.nrhs <= 2 and args.evaluation == "one-sided" and not args.pattern
+              and args.layout in ("redundant", "indirect") and not args.no_secondary):
+            res["symmetric"] = evaluation_variant(prob, args.layout, dev, 100, res["roofline"]["peak"] * 1e9)
             res["pipelined"] = pipelined_batches(prob, args.layout, dev, min(max(args.steps, 20), 400))
+        if not args.no_batched:
+            res["batched"] = batched_vs_plain(dev, 10, pipes, f_mhz)
+            res["adjoint"] = dbim_forward_adjoint(dev, 10)
+    finally:
+        clk.__exit__(None, None, None)
     if rank == 0:
         if not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)

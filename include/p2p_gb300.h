@@ -330,8 +330,9 @@ int p2p_gravity_adjoint(p2p_plan* plan, float eps, const float* pos, const float
  *                      right-hand sides, since conj(P) y = conj(P conj y)).
  *                      layout: INDIRECT, REDUNDANT or AUTO (the workspace
  *                      holds redundant streams; p2p_batch_autotune chooses).
- *                      flags: 0 or P2P_PLAN_PLAIN_FP32.  Helmholtz only
- *                      (P2P_ERR_UNSUPPORTED otherwise).
+ *                      flags: 0, P2P_PLAN_PLAIN_FP32 and/or
+ *                      P2P_PLAN_TIMING (phase events, p2p_batch_timing).
+ *                      Helmholtz only (P2P_ERR_UNSUPPORTED otherwise).
  *   p2p_batch_build    builds every instance's tree and merges them into one
  *                      box structure; synchronises the stream once per
  *                      instance (set-up, not the hot path).
@@ -365,6 +366,13 @@ int p2p_batch_capture(p2p_batch* batch, float k, const float* pos, const void* q
 int p2p_batch_launch(p2p_batch* batch, void* stream);
 /* counters of the combined structure (as p2p_read_counters; pairs are geometric) */
 int p2p_batch_counters(const p2p_batch* batch, const void* ws, int64_t* out, void* stream);
+/* Milliseconds of the last run's phases (batches created with
+ * P2P_PLAN_TIMING), as p2p_plan_timing: RESTRUCTURE, KERNEL (every
+ * right-hand-side pass of the P2P kernel) and OPERATOR (work list + kernel);
+ * TREE is -1 (the trees are built once, by p2p_batch_build).  Inside a
+ * captured graph the events are external event nodes, so a replay records
+ * them.  Host float ms_out[P2P_PHASE_COUNT]; waits for the events. */
+int p2p_batch_timing(p2p_batch* batch, float* ms_out);
 
 /*
  * Self-test of the bounded device waits (a library check; the paper has no

@@ -41,6 +41,8 @@ def load():
         I = ctypes.c_int
         F = ctypes.c_float
         lib.orc_num_threads.restype = I
+        lib.orc_set_num_threads.restype = I
+        lib.orc_set_num_threads.argtypes = [I]
         lib.orc_morton.restype = ctypes.c_uint32
         lib.orc_morton.argtypes = [ctypes.c_int32] * 3 + [I]
         lib.orc_unmorton.argtypes = [ctypes.c_uint32, I, P, P, P]
@@ -55,6 +57,13 @@ def load():
         lib.orc_gravity_periodic.argtypes = [P, P, I64, I, P, F, F, P, I64, P, P, P]
         lib.orc_helmholtz_periodic.argtypes = [P, P, I, I64, I, P, F, F, P, I64, P, P]
         lib.orc_gravity_adjoint.argtypes = [P, P, P, P, I64, I, P, F, F, P, P]
+        lib.orc_context_new.restype = P
+        lib.orc_context_new.argtypes = [P, I64, I, P, F, I, ctypes.POINTER(I)]
+        lib.orc_context_free.argtypes = [P]
+        lib.orc_gravity_ctx.argtypes = [P, P, P, F, P, I64, P, P, P]
+        lib.orc_helmholtz_ctx.argtypes = [P, P, P, I, F, P, I64, P, P]
+        lib.orc_gravity_ctx.restype = I
+        lib.orc_helmholtz_ctx.restype = I
         for f in ("orc_cells", "orc_tree", "orc_redundant", "orc_gravity", "orc_helmholtz",
                   "orc_pair_count", "orc_helmholtz_adjoint", "orc_gravity_adjoint", "orc_tree_periodic",
                   "orc_gravity_periodic", "orc_helmholtz_periodic"):
@@ -78,6 +87,11 @@ def _check(st, what):
 
 def num_threads() -> int:
     return int(load().orc_num_threads())
+
+
+def set_num_threads(t: int) -> int:
+    """Threads of the oracle's parallel loops on the calling thread from now on; returns the previous count."""
+    return int(load().orc_set_num_threads(int(t)))
 
 
 def morton(cx: int, cy: int, cz: int, level: int) -> int:
@@ -189,6 +203,51 @@ def helmholtz(pos, q, level, lo, edge, k, targets=None, periodic: bool = False):
               float(edge), float(k), _p(tg), nt, _p(u), ctypes.byref(pairs)),
            "helmholtz")
     return u[..., 0] + 1j * u[..., 1], pairs.value
+
+
+class Context:
+    """The oracle's tree of one workload, kept across calls so that sums at
+    several target samples share one tree build (the benchmark's CPU baseline
+    times the two apart).  Same results as gravity() / helmholtz()."""
+
+    def __init__(self, pos, level, lo, edge, periodic: bool = False):
+        self.pos = np.ascontiguousarray(pos, np.float32)
+        self.n = self.pos.shape[0]
+        st = ctypes.c_int()
+        self._h = load().orc_context_new(_p(self.pos), self.n, level, _p(_lo(lo)), float(edge),
+                                         1 if periodic else 0, ctypes.byref(st))
+        _check(st.value, "context")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_context_free(h)
+            self._h = None
+
+    def gravity(self, mass, eps, targets=None):
+        mass = np.ascontiguousarray(mass, np.float32)
+        tg = None if targets is None else np.ascontiguousarray(targets, np.int64)
+        nt = self.n if tg is None else tg.shape[0]
+        phi = np.zeros(nt, np.float64)
+        acc = np.zeros((nt, 3), np.float64)
+        pairs = ctypes.c_int64()
+        _check(load().orc_gravity_ctx(self._h, _p(self.pos), _p(mass), float(eps), _p(tg), nt, _p(phi), _p(acc),
+                                      ctypes.byref(pairs)), "gravity_ctx")
+        return phi, acc, pairs.value
+
+    def helmholtz(self, q, k, targets=None):
+        q = np.asarray(q)
+        if q.ndim == 1:
+            q = q[None, :]
+        q = np.ascontiguousarray(q, np.complex64)
+        nrhs = q.shape[0]
+        tg = None if targets is None else np.ascontiguousarray(targets, np.int64)
+        nt = self.n if tg is None else tg.shape[0]
+        u = np.zeros((nrhs, nt, 2), np.float64)
+        pairs = ctypes.c_int64()
+        _check(load().orc_helmholtz_ctx(self._h, _p(self.pos), _p(q.view(np.float32)), nrhs, float(k), _p(tg), nt,
+                                        _p(u), ctypes.byref(pairs)), "helmholtz_ctx")
+        return u[..., 0] + 1j * u[..., 1], pairs.value
 
 
 def pair_count(pos, level, lo, edge) -> int:

@@ -60,6 +60,20 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the sums' parallel loops started by the calling host thread from
+ * now on (OpenMP); returns the previous count.  Used to time the oracle on one
+ * core and on all cores. */
+int orc_set_num_threads(int t) {
+#ifdef _OPENMP
+    const int old = omp_get_max_threads();
+    if (t > 0) omp_set_num_threads(t);
+    return old;
+#else
+    (void)t;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------- */
 /* boxing                                                                     */
 /* ------------------------------------------------------------------------- */
@@ -321,13 +335,10 @@ static int orc_ctx_build(orc_ctx* c, const float* pos, int64_t n, int level, con
  * phi[nt], acc[nt*3] in double.  eps is the float32 softening widened.
  * Optionally counts the ordered pairs visited into *pairs.
  */
-static int orc_gravity_ex(const float* pos, const float* mass, int64_t n, int level, const float* lo,
-                          float edge, float eps, const int64_t* targets, int64_t nt,
-                          double* phi, double* acc, int64_t* pairs, int periodic) {
-    orc_ctx c;
-    int st = orc_ctx_build(&c, pos, n, level, lo, edge, periodic);
-    if (st != ORC_OK) return st;
-    if (!targets) nt = n;
+static void orc_gravity_sum(const orc_ctx* cp, const float* pos, const float* mass, float eps,
+                            const int64_t* targets, int64_t nt, double* phi, double* acc, int64_t* pairs) {
+    const orc_ctx c = *cp;
+    if (!targets) nt = c.n;
     const double e2 = (double)eps * (double)eps;
     int64_t count = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : count)
@@ -359,6 +370,15 @@ static int orc_gravity_ex(const float* pos, const float* mass, int64_t n, int le
         acc[3 * t] = ax; acc[3 * t + 1] = ay; acc[3 * t + 2] = az;
     }
     if (pairs) *pairs = count;
+}
+
+static int orc_gravity_ex(const float* pos, const float* mass, int64_t n, int level, const float* lo,
+                          float edge, float eps, const int64_t* targets, int64_t nt,
+                          double* phi, double* acc, int64_t* pairs, int periodic) {
+    orc_ctx c;
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge, periodic);
+    if (st != ORC_OK) return st;
+    orc_gravity_sum(&c, pos, mass, eps, targets, nt, phi, acc, pairs);
     orc_ctx_free(&c);
     return ORC_OK;
 }
@@ -368,13 +388,10 @@ static int orc_gravity_ex(const float* pos, const float* mass, int64_t n, int le
  * q: complex64 sources laid out [nrhs][n][re,im] (float32); u: [nrhs][nt][re,im]
  * in double.  k is the float32 wavenumber widened.
  */
-static int orc_helmholtz_ex(const float* pos, const float* q, int nrhs, int64_t n, int level,
-                            const float* lo, float edge, float k, const int64_t* targets, int64_t nt,
-                            double* u, int64_t* pairs, int periodic) {
-    if (nrhs < 1) return ORC_ERR_ARG;
-    orc_ctx c;
-    int st = orc_ctx_build(&c, pos, n, level, lo, edge, periodic);
-    if (st != ORC_OK) return st;
+static void orc_helmholtz_sum(const orc_ctx* cp, const float* pos, const float* q, int nrhs, float k,
+                              const int64_t* targets, int64_t nt, double* u, int64_t* pairs) {
+    const orc_ctx c = *cp;
+    const int64_t n = c.n;
     if (!targets) nt = n;
     const double kk = (double)k;
     const double inv4pi = 1.0 / (4.0 * ORC_PI);
@@ -408,6 +425,16 @@ static int orc_helmholtz_ex(const float* pos, const float* q, int nrhs, int64_t 
         }
     }
     if (pairs) *pairs = count;
+}
+
+static int orc_helmholtz_ex(const float* pos, const float* q, int nrhs, int64_t n, int level,
+                            const float* lo, float edge, float k, const int64_t* targets, int64_t nt,
+                            double* u, int64_t* pairs, int periodic) {
+    if (nrhs < 1) return ORC_ERR_ARG;
+    orc_ctx c;
+    int st = orc_ctx_build(&c, pos, n, level, lo, edge, periodic);
+    if (st != ORC_OK) return st;
+    orc_helmholtz_sum(&c, pos, q, nrhs, k, targets, nt, u, pairs);
     orc_ctx_free(&c);
     return ORC_OK;
 }
@@ -422,6 +449,44 @@ int orc_helmholtz(const float* pos, const float* q, int nrhs, int64_t n, int lev
                   const float* lo, float edge, float k, const int64_t* targets, int64_t nt,
                   double* u, int64_t* pairs) {
     return orc_helmholtz_ex(pos, q, nrhs, n, level, lo, edge, k, targets, nt, u, pairs, 0);
+}
+
+/*
+ * A tree context kept across calls: the same sums as orc_gravity /
+ * orc_helmholtz (periodic != 0: as the *_periodic calls) at several target
+ * samples on one tree, so that a caller can time the tree build and the sums
+ * apart.  pos must be the positions the context was built from.
+ * orc_context_new returns NULL on failure and the status in *status.
+ */
+void* orc_context_new(const float* pos, int64_t n, int level, const float* lo, float edge, int periodic,
+                      int* status) {
+    orc_ctx* c = (orc_ctx*)malloc(sizeof(orc_ctx));
+    int st = c ? ORC_OK : ORC_ERR_NOMEM;
+    if (c && periodic && level < 2) st = ORC_ERR_ARG;
+    if (st == ORC_OK) st = orc_ctx_build(c, pos, n, level, lo, edge, periodic);
+    if (status) *status = st;
+    if (st != ORC_OK) { free(c); return NULL; }
+    return c;
+}
+
+void orc_context_free(void* h) {
+    if (!h) return;
+    orc_ctx_free((orc_ctx*)h);
+    free(h);
+}
+
+int orc_gravity_ctx(const void* h, const float* pos, const float* mass, float eps, const int64_t* targets,
+                    int64_t nt, double* phi, double* acc, int64_t* pairs) {
+    if (!h) return ORC_ERR_ARG;
+    orc_gravity_sum((const orc_ctx*)h, pos, mass, eps, targets, nt, phi, acc, pairs);
+    return ORC_OK;
+}
+
+int orc_helmholtz_ctx(const void* h, const float* pos, const float* q, int nrhs, float k, const int64_t* targets,
+                      int64_t nt, double* u, int64_t* pairs) {
+    if (!h || nrhs < 1) return ORC_ERR_ARG;
+    orc_helmholtz_sum((const orc_ctx*)h, pos, q, nrhs, k, targets, nt, u, pairs);
+    return ORC_OK;
 }
 
 /* Number of ordered pairs P = sum_b n_b S_b - n (self pairs excluded). */

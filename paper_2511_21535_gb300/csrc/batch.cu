@@ -91,12 +91,29 @@ static int batch_run(Batch& b, float k, const float* pos, const void* q, const v
                      cudaStream_t s) {
     void* cws = static_cast<char*>(ws) + b.comb_off;
     Plan* p = &b.comb;
+    ev_begin(p, P2P_PHASE_RESTRUCTURE, s);
     int st = restructure(p, pos, q, cws, s, b.pair ? y : nullptr);
     if (st) return st;
+    ev_end(p, P2P_PHASE_RESTRUCTURE, s);
+    ev_begin(p, P2P_PHASE_OPERATOR, s);
     st = build_items(p, cws, 32 * helmholtz_targets_per_lane(p, k), s);
     if (st) return st;
-    return launch_helmholtz_kernel(p, loop_args(p, cws, p->rec_words), at<int32_t>(cws, p->L.perm), k,
-                                   HelmOut{static_cast<float2*>(u), static_cast<float2*>(g), p->split}, s);
+    ev_begin(p, P2P_PHASE_KERNEL, s);
+    st = launch_helmholtz_kernel(p, loop_args(p, cws, p->rec_words), at<int32_t>(cws, p->L.perm), k,
+                                 HelmOut{static_cast<float2*>(u), static_cast<float2*>(g), p->split}, s);
+    if (st) return st;
+    ev_end(p, P2P_PHASE_KERNEL, s);
+    ev_end(p, P2P_PHASE_OPERATOR, s);
+    return P2P_OK;
+}
+
+static void batch_events_destroy(Batch& b) {
+    for (int ph = 0; ph < P2P_PHASE_COUNT; ++ph)
+        for (int e = 0; e < 2; ++e)
+            if (b.comb.ev[ph][e]) {
+                cudaEventDestroy(b.comb.ev[ph][e]);
+                b.comb.ev[ph][e] = nullptr;
+            }
 }
 
 extern "C" {
@@ -109,7 +126,7 @@ int p2p_batch_create(p2p_batch** out, int kind, int n_instances, const int64_t* 
     if (n_instances < 1 || !n || !level || !lo || !edge) return P2P_ERR_INVALID_ARG;
     if (layout != P2P_LAYOUT_INDIRECT && layout != P2P_LAYOUT_REDUNDANT && layout != P2P_LAYOUT_AUTO)
         return P2P_ERR_INVALID_ARG;
-    if (flags & ~(P2P_PLAN_PLAIN_FP32)) return P2P_ERR_INVALID_ARG;
+    if (flags & ~(P2P_PLAN_PLAIN_FP32 | P2P_PLAN_TIMING)) return P2P_ERR_INVALID_ARG;
     const int total_rhs = pair ? 2 * nrhs : nrhs;
     if (nrhs < 1 || total_rhs > P2P_MAX_NRHS) return P2P_ERR_INVALID_ARG;
     p2p_batch* h = host_alloc_should_fail() ? nullptr : new (std::nothrow) p2p_batch;
@@ -161,6 +178,19 @@ int p2p_batch_create(p2p_batch** out, int kind, int n_instances, const int64_t* 
     }
     b.comb.split = nrhs;
     b.comb.rmax = rmax;
+    b.comb.timing = (flags & P2P_PLAN_TIMING) ? 1 : 0;
+    for (int ph = 0; ph < P2P_PHASE_COUNT; ++ph) {
+        b.comb.ev_valid[ph] = 0;
+        b.comb.ev[ph][0] = b.comb.ev[ph][1] = nullptr;
+    }
+    if (b.comb.timing)
+        for (int ph = 0; ph < P2P_PHASE_COUNT; ++ph)
+            for (int e = 0; e < 2; ++e)
+                if (cudaEventCreate(&b.comb.ev[ph][e]) != cudaSuccess) {
+                    batch_events_destroy(b);
+                    delete h;
+                    return P2P_ERR_CUDA;
+                }
     if (layout == P2P_LAYOUT_AUTO) b.comb.layout = P2P_LAYOUT_INDIRECT;  // until the autotuner decides
     b.tmp_off = 0;
     b.comb_off = (b.tmp.L.total + 255) / 256 * 256;
@@ -180,6 +210,7 @@ int p2p_batch_destroy(p2p_batch* h) {
     if (b.exec) cudaGraphExecDestroy(b.exec);
     if (b.graph) cudaGraphDestroy(b.graph);
     if (b.cap_stream) cudaStreamDestroy(b.cap_stream);
+    batch_events_destroy(b);
     delete h;
     return P2P_OK;
 }
@@ -371,6 +402,20 @@ int p2p_batch_launch(p2p_batch* h, void* stream) {
     if (!b.exec) return P2P_ERR_STATE;
     P2P_CUDA_TRY(cudaGraphLaunch(b.exec, static_cast<cudaStream_t>(stream)));
     count_launch((int)b.graph_launches);
+    return P2P_OK;
+}
+
+int p2p_batch_timing(p2p_batch* h, float* ms_out) {
+    if (!h || !ms_out) return P2P_ERR_INVALID_ARG;
+    Plan* p = &h->b.comb;
+    for (int ph = 0; ph < P2P_PHASE_COUNT; ++ph) {
+        ms_out[ph] = -1.0f;
+        if (!p->timing || !p->ev_valid[ph]) continue;
+        if (cudaEventSynchronize(p->ev[ph][1]) != cudaSuccess) return P2P_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->ev[ph][0], p->ev[ph][1]) != cudaSuccess) return P2P_ERR_CUDA;
+        ms_out[ph] = ms;
+    }
     return P2P_OK;
 }
 

@@ -119,10 +119,10 @@ static void ev_record(cudaEvent_t ev, cudaStream_t s) {
     else
         cudaEventRecord(ev, s);
 }
-static void ev_begin(Plan* p, int ph, cudaStream_t s) {
+void ev_begin(Plan* p, int ph, cudaStream_t s) {
     if (p->timing) ev_record(p->ev[ph][0], s);
 }
-static void ev_end(Plan* p, int ph, cudaStream_t s) {
+void ev_end(Plan* p, int ph, cudaStream_t s) {
     if (p->timing) {
         ev_record(p->ev[ph][1], s);
         p->ev_valid[ph] = 1;

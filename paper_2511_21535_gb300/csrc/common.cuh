@@ -104,6 +104,11 @@ struct Plan {
 // launch accounting
 void count_launch(int k = 1);
 
+// phase timing of plans with P2P_PLAN_TIMING: CUDA events on the launching
+// stream (external event nodes while the stream is being captured)
+void ev_begin(Plan* p, int phase, cudaStream_t s);
+void ev_end(Plan* p, int phase, cudaStream_t s);
+
 // host allocation failure injection (testing): true while failures are pending
 bool host_alloc_should_fail();
 

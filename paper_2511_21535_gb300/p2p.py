@@ -39,7 +39,7 @@ EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_
            "p2p_batch_set_tuning", "p2p_batch_run", "p2p_batch_autotune", "p2p_batch_capture",
            "p2p_batch_launch", "p2p_batch_counters", "p2p_selftest_bounded_wait",
            "p2p_plan_set_grid", "p2p_build_checked", "p2p_fail_host_allocs", "p2p_gravity_host",
-           "p2p_helmholtz_host")
+           "p2p_helmholtz_host", "p2p_batch_timing")
 
 
 class P2PError(RuntimeError):
@@ -104,6 +104,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_batch_capture": (I, [P, F, P, P, P, P, P, P, SZ]),
         "p2p_batch_launch": (I, [P, P]),
         "p2p_batch_counters": (I, [P, P, ctypes.POINTER(I64), P]),
+        "p2p_batch_timing": (I, [P, ctypes.POINTER(F)]),
         "p2p_selftest_bounded_wait": (I, [ctypes.c_uint64, P, P]),
         "p2p_plan_set_grid": (I, [P, F, I]),
         "p2p_build_checked": (I, []),
@@ -474,7 +475,7 @@ class Batch:
     """
 
     def __init__(self, instances, nrhs: int, k: float, pair: bool = False, layout: str = "auto",
-                 plain_fp32: bool = False, device=None):
+                 plain_fp32: bool = False, timing: bool = False, device=None):
         lib = load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nrhs, self.k, self.pair = int(nrhs), float(k), bool(pair)
@@ -490,7 +491,8 @@ class Batch:
         self.N = self.offsets[-1]
         h = ctypes.c_void_p()
         _check(lib.p2p_batch_create(ctypes.byref(h), HELMHOLTZ, I, n, lv, lo, ed, self.nrhs, 1 if pair else 0,
-                                    LAYOUTS[layout], PLAN_PLAIN_FP32 if plain_fp32 else 0), "p2p_batch_create")
+                                    LAYOUTS[layout], (PLAN_PLAIN_FP32 if plain_fp32 else 0) |
+                                    (PLAN_TIMING if timing else 0)), "p2p_batch_create")
         self._h = h
         nb = ctypes.c_size_t()
         _check(lib.p2p_batch_workspace_bytes(h, ctypes.byref(nb)), "p2p_batch_workspace_bytes")
@@ -576,6 +578,13 @@ class Batch:
 
     def launch(self, stream=None):
         _check(load().p2p_batch_launch(self._h, _stream(stream)), "p2p_batch_launch")
+
+    def timing(self) -> dict:
+        """Milliseconds of the last run's phases (batches created with timing=True);
+        "tree" is -1 (trees are built once by build())."""
+        out = (ctypes.c_float * len(PHASES))()
+        _check(load().p2p_batch_timing(self._h, out), "p2p_batch_timing")
+        return {k_: float(v) for k_, v in zip(PHASES, out)}
 
     def counters(self, stream=None) -> dict:
         out = (ctypes.c_int64 * len(COUNTERS))()

@@ -590,3 +590,23 @@ def test_periodic_translation_by_a_box():
     assert rel_l2(phi2, phi) < 1e-14 and rel_l2(acc2, acc) < 1e-14
     f = mass.astype(np.float64)[:, None] * acc
     assert np.abs(f.sum(axis=0)).max() < 1e-12 * np.abs(f).sum()
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_context_sums_equal_one_call_sums(periodic):
+    """A tree context kept across calls gives the one-call results bit for bit
+    (the same tree and the same loops), at any target sample."""
+    p = wl.uniform_gravity(n=5000, level=3, seed=21)
+    ctx = oracle.Context(p.pos, p.level, p.lo, p.edge, periodic=periodic)
+    tg = np.random.default_rng(2).choice(p.n, 700, replace=False)
+    for targets in (None, tg):
+        a = oracle.gravity(p.pos, p.strength, p.level, p.lo, p.edge, p.eps, targets=targets, periodic=periodic)
+        b = ctx.gravity(p.strength, p.eps, targets=targets)
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+        assert a[2] == b[2]
+        q = wl.complex_normal((2, p.n), np.random.default_rng(3))
+        u1, n1 = oracle.helmholtz(p.pos, q, p.level, p.lo, p.edge, 9.0, targets=targets, periodic=periodic)
+        u2, n2 = ctx.helmholtz(q, 9.0, targets=targets)
+        np.testing.assert_array_equal(u1, u2)
+        assert n1 == n2
