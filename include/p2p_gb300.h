@@ -520,17 +520,38 @@ int p2p_measure_pipes(double* out, void* stream);
  * requests return P2P_ERR_UNSUPPORTED without touching the device.  The
  * scratch (P2P_NOALLOC_SCRATCH_BYTES) exists on every GPU that loads the
  * library, until the process exits.
- * The first call on a device looks up the scratch array's device address
- * (one cudaGetSymbolAddress per device); make that first call before any
+ * The set-up, workspace layout and kernels are those of a plan created
+ * with the same arguments and flags 0 (default tuning), so the results equal
+ * the workspace path's bit for bit; the scratch needed is that plan's
+ * p2p_plan_workspace_bytes, which for every n, level and layout within the
+ * limits is at most P2P_NOALLOC_SCRATCH_BYTES.
+ * Every call looks up the scratch array's device address with
+ * cudaGetSymbolAddress in the current context; the first call on a device
+ * also loads the library's module there, so make that first call before any
  * stream capture.  Every call shares the one array and leaves its contents
  * behind; the call clears what it needs.  Calls whose GPU work overlaps
  * (different streams or host threads) race on the scratch.
+ * Errors the device detects (a position outside the boxing domain or NaN, an
+ * expired bounded wait) are not in the return value: the call only queues
+ * the work.  Read them with p2p_gravity_noalloc_status.
  */
 #define P2P_NOALLOC_MAX_N 8192
 #define P2P_NOALLOC_MAX_LEVEL 4
 #define P2P_NOALLOC_SCRATCH_BYTES (4718592)  /* 4.5 MiB */
 int p2p_gravity_noalloc(const float* pos, const float* mass, int64_t n, int level, const float* lo,
                         float edge, float eps, int layout, float* phi, float* acc, void* stream);
+
+/*
+ * Status of the last p2p_gravity_noalloc call on the current device: waits
+ * for `stream`, reads the device flag word that call left in the library's
+ * scratch array (allocating nothing) and returns the status it maps to, as
+ * p2p_read_counters does: P2P_ERR_DOMAIN for a position outside the boxing
+ * domain (or NaN; phi and acc are then not meaningful), P2P_ERR_TIMEOUT for
+ * an expired bounded wait, P2P_ERR_BOUNDS (checked builds), else P2P_OK.
+ * flags: host uint32, nullable; receives the raw P2P_FLAG_* bits.
+ * The paper has no counterpart.
+ */
+int p2p_gravity_noalloc_status(uint32_t* flags, void* stream);
 
 #ifdef __cplusplus
 }

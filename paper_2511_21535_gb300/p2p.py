@@ -39,7 +39,7 @@ EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_
            "p2p_batch_set_tuning", "p2p_batch_run", "p2p_batch_autotune", "p2p_batch_capture",
            "p2p_batch_launch", "p2p_batch_counters", "p2p_selftest_bounded_wait",
            "p2p_plan_set_grid", "p2p_build_checked", "p2p_fail_host_allocs", "p2p_gravity_host",
-           "p2p_helmholtz_host", "p2p_batch_timing")
+           "p2p_helmholtz_host", "p2p_batch_timing", "p2p_gravity_noalloc_status")
 
 
 class P2PError(RuntimeError):
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_batch_launch": (I, [P, P]),
         "p2p_batch_counters": (I, [P, P, ctypes.POINTER(I64), P]),
         "p2p_batch_timing": (I, [P, ctypes.POINTER(F)]),
+        "p2p_gravity_noalloc_status": (I, [ctypes.POINTER(U), P]),
         "p2p_selftest_bounded_wait": (I, [ctypes.c_uint64, P, P]),
         "p2p_plan_set_grid": (I, [P, F, I]),
         "p2p_build_checked": (I, []),
