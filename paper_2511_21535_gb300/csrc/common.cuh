@@ -273,5 +273,9 @@ int launch_helmholtz_pattern(const Plan* p, const LoopArgs& a, const int32_t* pe
 
 // records
 inline int helmholtz_rec_words(int nrhs) { return 1 + (nrhs + 1) / 2; }
+// Helmholtz records of plans with four or more right-hand sides (direct
+// evaluation) hold each pair of right-hand sides planar in its word,
+// [Re q_a, Re q_b, Im q_a, Im q_b]; otherwise interleaved, [Re q_a, Im q_a, Re q_b, Im q_b]
+inline bool helmholtz_planar(const Plan* p) { return p->kind == P2P_HELMHOLTZ && p->nrhs >= 4 && !p->pattern; }
 
 }  // namespace p2p

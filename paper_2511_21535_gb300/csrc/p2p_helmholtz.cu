@@ -75,20 +75,23 @@ int launch_helmholtz_kernel(const Plan* p, const LoopArgs& a, const int32_t* per
                             cudaStream_t s) {
     const bool comp = !(p->flags & P2P_PLAN_PLAIN_FP32);
     const bool precise = helmholtz_needs_precise(p, k);
+    const bool planar = helmholtz_planar(p);
     // passes of 8, 4, 2, 1 right-hand sides; every pass but the last starts at an even index
+    // (planar records: 8, 4 or 2, the last pair of an odd count half empty)
     int r0 = 0;
     while (r0 < p->nrhs) {
         const int left = p->nrhs - r0;
-        const int R = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        const int R = left >= 8 ? 8 : left >= 4 ? 4 : (left >= 2 || planar) ? 2 : 1;
         if (r0 > 0) {   // the first pass follows build_items, which zeroed the operator section
             const int st0 = fill32(&a.hdr->work_ctr, 0u, 1, s);
             if (st0) return st0;
         }
         // symmetric tasks run only in the compensated hardware-sin/cos kernel
         if (a.task_kind && (precise || !comp)) return P2P_ERR_UNSUPPORTED;
-        int st = precise ? launch_helm_precise(p, a, perm, k, r0, R, u, s)
-                 : comp  ? launch_helm_fast(p, a, perm, k, r0, R, u, s)
-                         : launch_helm_plain(p, a, perm, k, r0, R, u, s);
+        int st = planar  ? launch_helm_planar(p, a, perm, k, r0, R, left < R ? left : R, comp, precise, u, s)
+                 : precise ? launch_helm_precise(p, a, perm, k, r0, R, u, s)
+                 : comp    ? launch_helm_fast(p, a, perm, k, r0, R, u, s)
+                           : launch_helm_plain(p, a, perm, k, r0, R, u, s);
         if (st) return st;
         r0 += R;
     }

@@ -242,5 +242,9 @@ int launch_helm_plain(const Plan* p, const LoopArgs& a, const int32_t* perm, flo
                       cudaStream_t s);
 int launch_helm_precise(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, HelmOut u,
                         cudaStream_t s);
+// records with the right-hand sides planar per word (plans of four or more): passes of 2, 4 or 8 values,
+// nval of them valid
+int launch_helm_planar(const Plan* p, const LoopArgs& a, const int32_t* perm, float kk, int r0, int R, int nval,
+                       bool comp, bool precise, HelmOut u, cudaStream_t s);
 
 }  // namespace p2p

@@ -12,7 +12,10 @@
 //
 // Source record formats (16-byte words):
 //   gravity    [x, y, z, m]
-//   Helmholtz  [x, y, z, 0] then nrhs complex q values packed two per word
+//   Helmholtz  [x, y, z, 0] then nrhs complex q values packed two per word,
+//              [Re q_a, Im q_a, Re q_b, Im q_b]; plans of four or more
+//              right-hand sides (direct evaluation) hold each pair planar,
+//              [Re q_a, Re q_b, Im q_a, Im q_b]
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -86,7 +89,7 @@ __device__ __forceinline__ bool lattice_code(const float* x, const LatticeArgs& 
 
 __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2* __restrict__ q,
                                     const float2* __restrict__ q2, int split, const int32_t* __restrict__ perm,
-                                    int64_t n, int nrhs, int words, LatticeArgs lat, Header* hdr,
+                                    int64_t n, int nrhs, int words, int planar, LatticeArgs lat, Header* hdr,
                                     float4* __restrict__ rec,
                                   unsigned long long* __restrict__ lb, int64_t lb_words) {
     pdl_wait();
@@ -114,7 +117,7 @@ __global__ void k_records_helmholtz(const float* __restrict__ pos, const float2*
         const int r0 = 2 * (w - 1), r1 = r0 + 1;
         const float2 a = rhs_value(q, q2, split, n, r0, i);
         const float2 b = (r1 < nrhs) ? rhs_value(q, q2, split, n, r1, i) : make_float2(0.0f, 0.0f);
-        r[w] = make_float4(a.x, a.y, b.x, b.y);
+        r[w] = planar ? make_float4(a.x, b.x, a.y, b.y) : make_float4(a.x, a.y, b.x, b.y);
     }
 }
 
@@ -537,7 +540,8 @@ int restructure(Plan* p, const float* pos, const void* strength, void* ws, cudaS
         }
         P2P_CUDA_TRY(launch_pdl(k_records_helmholtz, blocks_for(n, 256), 256, 0, s, pos, static_cast<const float2*>(strength),
                                                               static_cast<const float2*>(strength2), split, perm, n,
-                                                              p->nrhs, p->rec_words, lat, at<Header>(ws, L.header),
+                                                              p->nrhs, p->rec_words, helmholtz_planar(p) ? 1 : 0, lat,
+                                                              at<Header>(ws, L.header),
                                                               rec, lbc, lbc_words));
     }
     P2P_LAUNCH_CHECK();
