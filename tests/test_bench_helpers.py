@@ -10,6 +10,8 @@ import bench
 def test_kernel_names():
     assert bench.kernel_name("helmholtz", False, tile2d=True) == "k_helmtile"
     assert bench.kernel_name("helmholtz", False) == "k_helmholtz"
+    assert bench.kernel_name("helmholtz", False, tile2d=True, nrhs=8) == "k_helmplanar"
+    assert bench.kernel_name("helmholtz", False, tile2d=False, nrhs=4) == "k_helmplanar"
     assert bench.kernel_name("helmholtz", True, tile2d=True) == "k_helmsym"
     assert bench.kernel_name("helmholtz", False, pattern=True, tile2d=True) == "k_helmholtz_pattern"
     assert bench.kernel_name("gravity", False, tile2d=True) == "k_gravity_pk"

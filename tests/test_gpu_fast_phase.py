@@ -43,9 +43,27 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+# pairs of points near opposite corners of two diagonally adjacent level-3 boxes
+# (cells c and c + (1, 1, 1)): their distance is 0.9993 r_max, so every case
+# evaluates phases up to k * 0.9993 r_max
+FAR_CELLS = ((0, 0, 0), (3, 2, 5), (6, 6, 6), (1, 5, 2))
+
+
+def far_pairs(level=LEVEL):
+    h = 1.0 / (1 << level)
+    d = 1e-4
+    pts = []
+    for c in FAR_CELLS:
+        lo = np.array(c, np.float64) * h
+        pts.append(lo + d)
+        pts.append(lo + 2 * h - d)
+    return np.array(pts, np.float32)
+
+
 def problem(n, nrhs, seed, k=K_FAST, level=LEVEL):
     rng = np.random.default_rng(seed)
     pos = rng.random((n, 3), dtype=np.float32)
+    pos[:2 * len(FAR_CELLS)] = far_pairs(level)
     q = wl.complex_normal((nrhs, n), rng)
     return wl.Problem("fast_phase", pos, q, level, (0.0, 0.0, 0.0), 1.0, "helmholtz", k=k)
 
@@ -72,13 +90,14 @@ def oracle_u(prob, periodic=False):
 def test_phase_range_is_just_below_the_switch():
     assert 31.0 < K_FAST * rmax(LEVEL) <= 32.0
     assert K_ABOVE * rmax(LEVEL) > 32.0
-    # the generated points reach the top of the range: some neighbouring pair is within 10 % of r_max
+    # every case holds neighbouring pairs at the top of the range (boxes at Chebyshev distance 1)
     prob = problem(8000, 1, 1)
     cells, _ = oracle.cells(prob.pos, LEVEL, prob.lo, prob.edge)
-    corner = np.all(cells == 0, axis=1)
-    far = np.all(cells == 1, axis=1)
-    d = np.linalg.norm(prob.pos[corner][:, None, :].astype(np.float64) - prob.pos[far][None, :, :], axis=2)
-    assert d.max() > 0.9 * rmax(LEVEL)
+    for i in range(len(FAR_CELLS)):
+        a, b = 2 * i, 2 * i + 1
+        assert np.abs(cells[a] - cells[b]).max() == 1
+        d = np.linalg.norm(prob.pos[a].astype(np.float64) - prob.pos[b])
+        assert K_FAST * d > 31.5
 
 
 @pytest.mark.parametrize("layout", ["indirect", "redundant"])
