@@ -417,13 +417,19 @@ __global__ void __launch_bounds__(256) k_items_fill(Units U, Header* hdr, int tt
 }
 
 constexpr int kGatherParts = 4;
+constexpr int kGatherLight = 512;   // streams of at most this many records: one lane per neighbour entry
 
-// Redundant gather: kGatherParts warps per target box copy the records of each
-// neighbour box, in neighbour order, into the box's stream (16-byte words,
-// coalesced), and optionally the sorted index of every copied record.  With
-// periodic boundaries a wrapped neighbour's records are copied with their
-// positions moved to the image the box meets (word 0 holds x, y, z), so the
-// kernel needs no image logic.
+// Redundant gather: each target box's stream is the records of its neighbour
+// boxes, in neighbour order (16-byte words), optionally with the sorted index
+// of every copied record.  A light stream (<= kGatherLight records: sparse
+// boxes, e.g. the background of a clustered distribution) is copied by one
+// warp with one lane per neighbour entry, all entries at once (the offsets are
+// a warp scan of the entries' counts); a heavy stream by kGatherParts warps,
+// each copying a contiguous chunk of the entries one entry at a time with the
+// whole warp (coalesced, eight loads in flight per lane).  With periodic
+// boundaries a wrapped neighbour's records are copied with their positions
+// moved to the image the box meets (word 0 holds x, y, z), so the kernel
+// needs no image logic.
 __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ rec, int words,
                                                    const int32_t* __restrict__ box_start,
                                                    const int32_t* __restrict__ nbr_start,
@@ -449,6 +455,22 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
         const int64_t b = w / kGatherParts;
         const int part = (int)(w % kGatherParts);
         const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+        const int32_t rs0 = red_start[b];
+        if (red_start[b + 1] - rs0 <= kGatherLight) {
+            if (part != 0) continue;
+            int32_t s0 = 0, cnt = 0, code = 13;
+            if (lane < ne && !(task_kind && task_kind[e0 + lane] == kTaskNone)) {
+                const int32_t c = nbr_idx[e0 + lane];
+                s0 = box_start[c];
+                cnt = box_start[c + 1] - s0;
+                if (nbr_img) code = nbr_img[e0 + lane];
+            }
+            const int64_t out = (int64_t)rs0 + warp_incl_scan(cnt) - cnt;
+            lane_copy_records(rec + (int64_t)s0 * words, red + out * words, cnt, words, code, edge);
+            if (gather)
+                for (int32_t l = 0; l < cnt; ++l) gather[out + l] = (uint32_t)(s0 + l);
+            continue;
+        }
         const int32_t lo = part * ne / kGatherParts, hi = (part + 1) * ne / kGatherParts;
         // the chunk's offset in the stream: the streamed counts of the entries before it
         int32_t before = 0;
@@ -458,7 +480,7 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(FULL, before, o);
-        int64_t out = (int64_t)red_start[b] + before;
+        int64_t out = (int64_t)rs0 + before;
         for (int32_t e = e0 + lo; e < e0 + hi; ++e) {
             if (task_kind && task_kind[e] == kTaskNone) continue;   // symmetric: the mirror's mutual item covers it
             const int32_t c = nbr_idx[e];
