@@ -173,16 +173,38 @@ def test_gravity_layouts_agree_bitwise(dev):
 
 @pytest.mark.parametrize("layout", ["indirect", "redundant"])
 def test_gravity_packed_kernels_agree(dev, layout):
-    """Two and four targets per lane run the packed two-wide kernel: the same
-    per-target operation order, so bitwise equal; one per lane is the scalar
-    kernel (the compiler may contract its products into FMAs): equal to rounding."""
+    """Two and four targets per lane run the packed two-wide kernel: targets of
+    items of more than 32 targets sum their sources in the same order (bitwise
+    equal between the two); an item of at most 32 targets with two per lane runs
+    source-split (even and odd sources in the two halves, added at the end), and
+    one per lane is the scalar kernel: equal to rounding."""
     prob = wl.plummer_gravity(n=40000, level=5, eps=1e-3, seed=2)
-    _, p1, a1 = run_gravity(prob, dev, layout, 1, 64, group=4)
+    plan, p1, a1 = run_gravity(prob, dev, layout, 1, 64, group=4)
     _, p2, a2 = run_gravity(prob, dev, layout, 2, 64, group=4)
     _, p4, a4 = run_gravity(prob, dev, layout, 4, 64, group=4)
-    np.testing.assert_array_equal(p2, p4)
-    np.testing.assert_array_equal(a2, a4)
     assert rel_l2(p1, p2) < 1e-6 and rel_l2(a1, a2) < 1e-6
+    assert rel_l2(p4, p2) < 1e-6 and rel_l2(a4, a2) < 1e-6
+    # targets in whole 64-target items of two per lane are summed as with four per lane
+    bs = plan.array("box_start", plan.counters()["n_boxes"] + 1).cpu().numpy()
+    perm = plan.array("perm", prob.n).cpu().numpy()
+    occ = np.diff(bs)
+    full = np.concatenate([perm[bs[b]:bs[b] + (occ[b] // 128) * 128] for b in range(len(occ)) if occ[b] >= 128])
+    assert full.size > 1000
+    np.testing.assert_array_equal(p2[full], p4[full])
+    np.testing.assert_array_equal(a2[full], a4[full])
+
+
+@pytest.mark.parametrize("layout", ["indirect", "redundant"])
+@pytest.mark.parametrize("n,level", [(3000, 3), (24000, 3), (20000, 2)])
+def test_gravity_source_split_items(dev, layout, n, level):
+    """Boxes of at most 32 particles (every item source-split), of 33-64 (packed
+    targets), and larger boxes whose last item holds <= 32 targets; odd and even
+    tile counts; against the FP64 oracle."""
+    prob = wl.uniform_gravity(n=n, level=level, seed=n)
+    for tile in (64, 128):
+        _, phi, acc = run_gravity(prob, dev, layout, 2, tile, group=1)
+        ophi, oacc, _ = oracle.gravity(prob.pos, prob.strength, prob.level, prob.lo, prob.edge, prob.eps)
+        assert rel_l2(phi, ophi) <= TOL_REAL and rel_l2(acc, oacc) <= TOL_REAL
 
 
 def test_gravity_deterministic(dev):
