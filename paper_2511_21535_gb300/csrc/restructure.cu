@@ -204,123 +204,131 @@ __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ b
     __shared__ int32_t pre_s[kBoxTile + 1], bpre_s[kBoxTile + 1];
     __shared__ unsigned long long pairs_s, evals_s;
     if (threadIdx.x == 0) {
-        // a rejected structure: the block takes no tile (later tiles wait only on taken ones);
-        // one thread reads the flag, which other blocks of this launch may be setting
-        tile_s = (hdr->flags & P2P_FLAG_CAPACITY) ? -1 : lb_ticket(lb);
         pairs_s = 0ull;
         evals_s = 0ull;
     }
-    __syncthreads();
-    const int tile = tile_s;
-    if (tile < 0) return;
     const int32_t nb = hdr->n_boxes;
-    const int64_t b0 = (int64_t)tile * kBoxTile;
-    if (b0 >= nb) return;   // past the last box (whole block): no later tile waits on it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long pairs = 0ull, evals = 0ull;
-    int32_t cbx[kStatsPerWarp];   // symmetric: this lane's offset among its box's mutual source slots
-#pragma unroll
-    for (int q = 0; q < kStatsPerWarp; ++q) {
-        const int64_t b = b0 + warp * kStatsPerWarp + q;
-        int32_t all = 0, cnt = 0, lower = 0, cb = 0;
-        if (b < nb) {
-            const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
-            if (lane < ne) {
-                const int32_t e = e0 + lane;
-                const int32_t c = nbr_idx[e];
-                const int32_t nc = box_start[c + 1] - box_start[c];
-                all = nc;
-                int32_t kind = kTaskOneSided;
-                if (task_kind) {
-                    kind = entry_kind((int32_t)b, c, box_start[b + 1] - box_start[b], nc);
-                    int32_t mir = -1;
-                    if (kind == kTaskNone) {
-                        // b's position in c's ascending list: independent loads, one latency
-                        const int32_t c0 = nbr_start[c], cn = nbr_start[c + 1] - c0;
-                        int32_t below = 0;
-                        bool found = false;
-#pragma unroll
-                        for (int i = 0; i < 27; ++i) {
-                            const int32_t v = i < cn ? nbr_idx[c0 + i] : INT32_MAX;
-                            below += v < b ? 1 : 0;
-                            found |= v == b;
-                        }
-                        if (found && cn <= 27) mir = c0 + below;
-                        else atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);   // inconsistent (imported) relation
-                    }
-                    task_kind[e] = kind;
-                    mirror[e] = mir;
-                }
-                cnt = kind == kTaskNone ? 0 : nc;
-                lower = (c < b) ? cnt : 0;
-                cb = kind == kTaskMutual ? nc : 0;
-            }
+    unsigned long long pairs = 0ull, evals = 0ull;   // this warp's share over all its tiles
+    // a few blocks per SM take tiles of kBoxTile boxes by ticket until the boxes run out
+    for (;;) {
+        if (threadIdx.x == 0) {
+            // a rejected structure: the block takes no tile (later tiles wait only on taken ones);
+            // one thread reads the flag, which other blocks of this launch may be setting
+            tile_s = (hdr->flags & P2P_FLAG_CAPACITY) ? -1 : lb_ticket(lb);
         }
-        const int32_t cbi = warp_incl_scan(cb);
-        cbx[q] = cbi - cb;
+        __syncthreads();
+        const int tile = tile_s;
+        if (tile < 0) break;
+        const int64_t b0 = (int64_t)tile * kBoxTile;
+        if (b0 >= nb) break;   // past the last box (whole block): no later tile waits on it
+        int32_t cbx[kStatsPerWarp];   // symmetric: this lane's offset among its box's mutual source slots
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            all += __shfl_xor_sync(FULL, all, o);
-            cnt += __shfl_xor_sync(FULL, cnt, o);
-            lower += __shfl_xor_sync(FULL, lower, o);
-        }
-        const int32_t cbt = __shfl_sync(FULL, cbi, 31);
-        if (lane == 0) {
-            s_s[warp * kStatsPerWarp + q] = cnt;
-            b_s[warp * kStatsPerWarp + q] = cbt;
+        for (int q = 0; q < kStatsPerWarp; ++q) {
+            const int64_t b = b0 + warp * kStatsPerWarp + q;
+            int32_t all = 0, cnt = 0, lower = 0, cb = 0;
             if (b < nb) {
-                S[b] = cnt;
-                if (self_off) self_off[b] = lower;
-                pairs += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)all;
-                evals += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)cnt;
+                const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+                if (lane < ne) {
+                    const int32_t e = e0 + lane;
+                    const int32_t c = nbr_idx[e];
+                    const int32_t nc = box_start[c + 1] - box_start[c];
+                    all = nc;
+                    int32_t kind = kTaskOneSided;
+                    if (task_kind) {
+                        kind = entry_kind((int32_t)b, c, box_start[b + 1] - box_start[b], nc);
+                        int32_t mir = -1;
+                        if (kind == kTaskNone) {
+                            // b's position in c's ascending list: independent loads, one latency
+                            const int32_t c0 = nbr_start[c], cn = nbr_start[c + 1] - c0;
+                            int32_t below = 0;
+                            bool found = false;
+#pragma unroll
+                            for (int i = 0; i < 27; ++i) {
+                                const int32_t v = i < cn ? nbr_idx[c0 + i] : INT32_MAX;
+                                below += v < b ? 1 : 0;
+                                found |= v == b;
+                            }
+                            if (found && cn <= 27) mir = c0 + below;
+                            else atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);   // inconsistent (imported) relation
+                        }
+                        task_kind[e] = kind;
+                        mirror[e] = mir;
+                    }
+                    cnt = kind == kTaskNone ? 0 : nc;
+                    lower = (c < b) ? cnt : 0;
+                    cb = kind == kTaskMutual ? nc : 0;
+                }
+            }
+            const int32_t cbi = warp_incl_scan(cb);
+            cbx[q] = cbi - cb;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                all += __shfl_xor_sync(FULL, all, o);
+                cnt += __shfl_xor_sync(FULL, cnt, o);
+                lower += __shfl_xor_sync(FULL, lower, o);
+            }
+            const int32_t cbt = __shfl_sync(FULL, cbi, 31);
+            if (lane == 0) {
+                s_s[warp * kStatsPerWarp + q] = cnt;
+                b_s[warp * kStatsPerWarp + q] = cbt;
+                if (b < nb) {
+                    S[b] = cnt;
+                    if (self_off) self_off[b] = lower;
+                    pairs += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)all;
+                    evals += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)cnt;
+                }
             }
         }
+        __syncthreads();
+        const bool last = nb - 1 >= b0 && nb - 1 < b0 + kBoxTile;
+        if (red_start) {
+            if (warp == 0) {
+                const int32_t v = s_s[lane];
+                const int32_t inc = warp_incl_scan(v);
+                const int32_t agg = __shfl_sync(FULL, inc, 31);
+                const int32_t ex = lb_exclusive(lb, tile, agg, hdr);
+                pre_s[lane] = ex + inc - v;
+                if (lane == 31) pre_s[kBoxTile] = ex + inc;
+            }
+            __syncthreads();
+            if (threadIdx.x < kBoxTile && b0 + threadIdx.x < nb) red_start[b0 + threadIdx.x] = pre_s[threadIdx.x];
+            if (threadIdx.x == 0 && last) {
+                red_start[nb] = pre_s[kBoxTile];
+                hdr->total_src = pre_s[kBoxTile];
+            }
+        }
+        if (bslot) {
+            if (warp == 0) {
+                const int32_t v = b_s[lane];
+                const int32_t inc = warp_incl_scan(v);
+                const int32_t agg = __shfl_sync(FULL, inc, 31);
+                const int32_t ex = lb_exclusive(lb2, tile, agg, hdr);
+                bpre_s[lane] = ex + inc - v;
+                if (lane == 31) bpre_s[kBoxTile] = ex + inc;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kStatsPerWarp; ++q) {
+                const int64_t b = b0 + warp * kStatsPerWarp + q;
+                if (b < nb) {
+                    const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+                    if (lane < ne) bslot[e0 + lane] = bpre_s[warp * kStatsPerWarp + q] + cbx[q];
+                }
+            }
+            if (threadIdx.x == 0 && last) {
+                hdr->part_total = bpre_s[kBoxTile];
+                if ((int64_t)bpre_s[kBoxTile] > part_cap) atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);
+            }
+        }
+        __syncthreads();   // the shared tile state is reused by the next tile
     }
+    // the pair counts of this block's tiles
     if (lane == 0 && pairs) atomicAdd(&pairs_s, pairs);
     if (lane == 0 && evals) atomicAdd(&evals_s, evals);
     __syncthreads();
     if (threadIdx.x == 0 && pairs_s) atomicAdd(&hdr->pairs_nS, pairs_s);
     if (threadIdx.x == 0 && evals_s) atomicAdd(&hdr->evals_nS, evals_s);
-    const bool last = nb - 1 >= b0 && nb - 1 < b0 + kBoxTile;
-    if (red_start) {
-        if (warp == 0) {
-            const int32_t v = s_s[lane];
-            const int32_t inc = warp_incl_scan(v);
-            const int32_t agg = __shfl_sync(FULL, inc, 31);
-            const int32_t ex = lb_exclusive(lb, tile, agg, hdr);
-            pre_s[lane] = ex + inc - v;
-            if (lane == 31) pre_s[kBoxTile] = ex + inc;
-        }
-        __syncthreads();
-        if (threadIdx.x < kBoxTile && b0 + threadIdx.x < nb) red_start[b0 + threadIdx.x] = pre_s[threadIdx.x];
-        if (threadIdx.x == 0 && last) {
-            red_start[nb] = pre_s[kBoxTile];
-            hdr->total_src = pre_s[kBoxTile];
-        }
-    }
-    if (bslot) {
-        if (warp == 0) {
-            const int32_t v = b_s[lane];
-            const int32_t inc = warp_incl_scan(v);
-            const int32_t agg = __shfl_sync(FULL, inc, 31);
-            const int32_t ex = lb_exclusive(lb2, tile, agg, hdr);
-            bpre_s[lane] = ex + inc - v;
-            if (lane == 31) bpre_s[kBoxTile] = ex + inc;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kStatsPerWarp; ++q) {
-            const int64_t b = b0 + warp * kStatsPerWarp + q;
-            if (b < nb) {
-                const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
-                if (lane < ne) bslot[e0 + lane] = bpre_s[warp * kStatsPerWarp + q] + cbx[q];
-            }
-        }
-        if (threadIdx.x == 0 && last) {
-            hdr->part_total = bpre_s[kBoxTile];
-            if ((int64_t)bpre_s[kBoxTile] > part_cap) atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);
-        }
-    }
 }
 
 __device__ __forceinline__ int cost_class(int32_t nt, int32_t sb) {
@@ -511,7 +519,8 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
     const LbRegions lr = lb_regions(p->n, bc);
     unsigned long long* lb2 = at<unsigned long long>(ws, L.lookback) + lr.stats2;
     int32_t* kinds = p->sym ? at<int32_t>(ws, L.task_kind) : nullptr;
-    P2P_CUDA_TRY(launch_pdl(k_box_stats, blocks_for(bc, kBoxTile), 256, 0, s, at<int32_t>(ws, L.box_start),
+    const unsigned stats_blocks = (unsigned)std::min<int64_t>(blocks_for(bc, kBoxTile), (int64_t)num_sms() * 8);
+    P2P_CUDA_TRY(launch_pdl(k_box_stats, stats_blocks, 256, 0, s, at<int32_t>(ws, L.box_start),
                             at<int32_t>(ws, L.nbr_start), at<int32_t>(ws, L.nbr_idx), hdr, S,
                             red ? at<int32_t>(ws, L.red_self) : nullptr, red_start, lb, kinds,
                             p->sym ? at<int32_t>(ws, L.mirror) : nullptr, p->sym ? at<int32_t>(ws, L.bslot) : nullptr,
