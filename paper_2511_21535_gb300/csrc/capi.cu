@@ -69,12 +69,13 @@ void compute_layout(Plan* p) {
     L.box_S = take((bc + 1) * 4);
     L.items = take((size_t)p->items_cap * 8);
     L.pattern = (p->kind == P2P_HELMHOLTZ) ? take((size_t)kPatternMaxEntries * 8) : 0;
-    L.red_start = L.red_self = L.red_src = L.gather = 0;
+    L.red_start = L.red_self = L.red_src = L.gather = L.heavy = 0;
     L.ent_box = L.pt_start = L.part_start = L.part = 0;
     L.task_kind = L.mirror = L.bslot = 0;
     if (p->layout == P2P_LAYOUT_REDUNDANT) {
         L.red_start = take((bc + 1) * 4);
         L.red_self = take(bc * 4);
+        L.heavy = take(bc * 4);
     } else if (pt) {
         L.ent_box = take((size_t)27 * bc * 4);
         L.pt_start = take(((size_t)27 * bc + 1) * 4);
@@ -572,32 +573,51 @@ int p2p_helmholtz_adjoint(p2p_plan* h, float k, const float* pos, const void* q,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (!grad_pos) {
         // grad_q = conj(P) gbar = P(-k) gbar: the forward operator on gbar
+        ev_begin(p, P2P_PHASE_RESTRUCTURE, s);
         st = restructure(p, pos, gbar, ws, s);
         if (st) return st;
+        ev_end(p, P2P_PHASE_RESTRUCTURE, s);
+        ev_begin(p, P2P_PHASE_OPERATOR, s);
         if (p->pattern) {
             st = build_items(p, ws, 32 * (p->tpl >= 2 ? 2 : 1), s);
             if (st) return st;
+            ev_begin(p, P2P_PHASE_KERNEL, s);
             st = launch_helmholtz_pattern(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), -k,
                                           at<float2>(ws, p->L.pattern),
                                           HelmOut{static_cast<float2*>(grad_q), nullptr, p->nrhs}, s);
             p->src_ready = 0;
-            return st;
+            if (st) return st;
+            ev_end(p, P2P_PHASE_KERNEL, s);
+            ev_end(p, P2P_PHASE_OPERATOR, s);
+            return P2P_OK;
         }
         st = build_items(p, ws, 32 * helmholtz_targets_per_lane(p, -k), s);
         if (st) return st;
+        ev_begin(p, P2P_PHASE_KERNEL, s);
         st = launch_helmholtz_kernel(p, loop_args(p, ws, p->rec_words), at<int32_t>(ws, p->L.perm), -k,
                                      HelmOut{static_cast<float2*>(grad_q), nullptr, p->nrhs}, s);
         p->src_ready = 0;   // the records hold gbar, not the forward sources
-        return st;
+        if (st) return st;
+        ev_end(p, P2P_PHASE_KERNEL, s);
+        ev_end(p, P2P_PHASE_OPERATOR, s);
+        return P2P_OK;
     }
     if (!q || (reinterpret_cast<uintptr_t>(q) & 7u)) return P2P_ERR_INVALID_ARG;
     int words = 0;
+    ev_begin(p, P2P_PHASE_RESTRUCTURE, s);
     st = restructure_adjoint(p, pos, q, gbar, nullptr, ws, &words, s);
     if (st) return st;
+    ev_end(p, P2P_PHASE_RESTRUCTURE, s);
+    ev_begin(p, P2P_PHASE_OPERATOR, s);
     st = build_items(p, ws, 32, s);
     if (st) return st;
-    return launch_helmholtz_adjoint_kernel(p, loop_args(p, ws, words), at<int32_t>(ws, p->L.perm), k,
-                                           helmholtz_needs_precise(p, k), static_cast<float2*>(grad_q), grad_pos, s);
+    ev_begin(p, P2P_PHASE_KERNEL, s);
+    st = launch_helmholtz_adjoint_kernel(p, loop_args(p, ws, words), at<int32_t>(ws, p->L.perm), k,
+                                         helmholtz_needs_precise(p, k), static_cast<float2*>(grad_q), grad_pos, s);
+    if (st) return st;
+    ev_end(p, P2P_PHASE_KERNEL, s);
+    ev_end(p, P2P_PHASE_OPERATOR, s);
+    return P2P_OK;
 }
 
 int p2p_gravity_adjoint(p2p_plan* h, float eps, const float* pos, const float* mass, const float* grad_phi,
@@ -617,12 +637,20 @@ int p2p_gravity_adjoint(p2p_plan* h, float eps, const float* pos, const float* m
     if (!p->tree_ready) return P2P_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int words = 0;
+    ev_begin(p, P2P_PHASE_RESTRUCTURE, s);
     st = restructure_adjoint(p, pos, mass, grad_phi, grad_acc, ws, &words, s);
     if (st) return st;
+    ev_end(p, P2P_PHASE_RESTRUCTURE, s);
+    ev_begin(p, P2P_PHASE_OPERATOR, s);
     st = build_items(p, ws, 32 * gravity_adjoint_targets_per_lane(p), s);
     if (st) return st;
-    return launch_gravity_adjoint_kernel(p, loop_args(p, ws, words), at<int32_t>(ws, p->L.perm), eps, grad_mass,
-                                         grad_pos, s);
+    ev_begin(p, P2P_PHASE_KERNEL, s);
+    st = launch_gravity_adjoint_kernel(p, loop_args(p, ws, words), at<int32_t>(ws, p->L.perm), eps, grad_mass,
+                                       grad_pos, s);
+    if (st) return st;
+    ev_end(p, P2P_PHASE_KERNEL, s);
+    ev_end(p, P2P_PHASE_OPERATOR, s);
+    return P2P_OK;
 }
 
 int p2p_plan_array(const p2p_plan* h, int which, int64_t* offset_bytes, int64_t* capacity) {

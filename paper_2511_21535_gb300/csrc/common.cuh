@@ -28,7 +28,8 @@ struct Header {
     int32_t total_src;                 // sum_b S_b (redundant records; pair tasks: task-stream records)
     int32_t part_total;                // pair tasks: partial-result slots, sum_e n_b(e)
     unsigned long long evals_nS;       // sum over streamed pairs (symmetric: mutual pairs once), self included
-    int32_t restr_pad[10];
+    int32_t n_heavy;                   // redundant gather: boxes whose streams exceed kGatherLight records
+    int32_t restr_pad[9];
     // operator section (zeroed at the start of each operator call), offset 128
     int32_t n_items;
     uint32_t work_ctr;
@@ -48,7 +49,7 @@ static_assert(offsetof(Header, n_items) == kOpSectionOffset, "header layout");
 struct Layout {                        // byte offsets inside the workspace
     size_t header, keys_a, keys_b, vals_a, perm, sorted_key, hist, scan_tmp, lookback,
         box_key, box_start, table, nbr_start, nbr_idx, src, box_S, red_start,
-        red_self, red_src, gather, items, pattern, nbr_img,
+        red_self, red_src, gather, items, pattern, nbr_img, heavy,
         ent_box, pt_start, part_start, part,   // pair tasks (red_src/gather hold the task stream)
         task_kind, mirror,                      // symmetric tasks (layout or plan flag)
         bslot,                                  // plan flag: source-sum slots of mutual entries
@@ -169,6 +170,17 @@ inline cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, si
 // clears the first two, the record kernels of the restructuring the others.
 constexpr int kCsrTileElems = 2048;
 constexpr int kBoxTile = 32;
+// redundant gather: a stream of at most kGatherLight records is copied by one
+// warp, one lane per neighbour entry; longer streams by kGatherParts warps
+constexpr int kGatherLight = 512;
+constexpr int kGatherParts = 4;
+// Radix sort of 3 * level key bits: equal digit widths of at most 8 bits.
+inline void sort_digits(int level, int* passes, int* dbits) {
+    const int bits = 3 * level;
+    *passes = (bits + 7) / 8;
+    *dbits = (bits + *passes - 1) / *passes;
+}
+
 struct LbRegions {
     int64_t csr, nbr, stats, stats2, tree_words, words;   // offsets and sizes in 8-byte words
 };

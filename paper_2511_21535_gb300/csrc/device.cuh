@@ -199,6 +199,7 @@ __device__ __forceinline__ void lane_copy_records(const float4* __restrict__ src
     const float sx = (float)(code % 3 - 1) * edge, sy = (float)((code / 3) % 3 - 1) * edge,
                 sz = (float)(code / 9 - 1) * edge;
     const bool shift = code != 13;
+#pragma unroll 4
     for (int32_t l = 0; l < cnt; ++l) {
         float4 v = __ldg(src + (int64_t)l * words);
         if (shift) {

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ b
                                                   int32_t* __restrict__ red_start, unsigned long long* lb,
                                                   int32_t* __restrict__ task_kind, int32_t* __restrict__ mirror,
                                                   int32_t* __restrict__ bslot, unsigned long long* lb2,
-                                                  int64_t part_cap) {
+                                                  int64_t part_cap, int32_t* __restrict__ heavy) {
     pdl_wait();
     pdl_release();
     __shared__ int tile_s;
@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(256) k_box_stats(const int32_t* __restrict__ b
                 b_s[warp * kStatsPerWarp + q] = cbt;
                 if (b < nb) {
                     S[b] = cnt;
+                    if (heavy && cnt > kGatherLight) heavy[atomicAdd(&hdr->n_heavy, 1)] = (int32_t)b;
                     if (self_off) self_off[b] = lower;
                     pairs += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)all;
                     evals += (unsigned long long)(box_start[b + 1] - box_start[b]) * (unsigned long long)cnt;
@@ -424,20 +425,72 @@ __global__ void __launch_bounds__(256) k_items_fill(Units U, Header* hdr, int tt
     }
 }
 
-constexpr int kGatherParts = 4;
-constexpr int kGatherLight = 512;   // streams of at most this many records: one lane per neighbour entry
-
 // Redundant gather: each target box's stream is the records of its neighbour
 // boxes, in neighbour order (16-byte words), optionally with the sorted index
 // of every copied record.  A light stream (<= kGatherLight records: sparse
 // boxes, e.g. the background of a clustered distribution) is copied by one
 // warp with one lane per neighbour entry, all entries at once (the offsets are
-// a warp scan of the entries' counts); a heavy stream by kGatherParts warps,
-// each copying a contiguous chunk of the entries one entry at a time with the
-// whole warp (coalesced, eight loads in flight per lane).  With periodic
-// boundaries a wrapped neighbour's records are copied with their positions
-// moved to the image the box meets (word 0 holds x, y, z), so the kernel
-// needs no image logic.
+// a warp scan of the entries' counts); a heavy stream (listed by the box
+// statistics) by kGatherParts warps, each copying a contiguous chunk of the
+// entries one entry at a time with the whole warp (coalesced, eight loads in
+// flight per lane).  The warps first take every box (a light box whole, a
+// heavy box's first part), then the other parts of the heavy boxes.  With
+// periodic boundaries a wrapped neighbour's records are copied with their
+// positions moved to the image the box meets (word 0 holds x, y, z), so the
+// kernel needs no image logic.
+__device__ __forceinline__ void gather_light(int64_t b, const float4* __restrict__ rec, int words,
+                                             const int32_t* __restrict__ box_start,
+                                             const int32_t* __restrict__ nbr_start,
+                                             const int32_t* __restrict__ nbr_idx,
+                                             const int32_t* __restrict__ nbr_img, float edge, int32_t rs0,
+                                             float4* __restrict__ red, uint32_t* __restrict__ gather,
+                                             const int32_t* __restrict__ task_kind, int lane) {
+    const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+    int32_t s0 = 0, cnt = 0, code = 13;
+    if (lane < ne && !(task_kind && task_kind[e0 + lane] == kTaskNone)) {
+        const int32_t c = nbr_idx[e0 + lane];
+        s0 = box_start[c];
+        cnt = box_start[c + 1] - s0;
+        if (nbr_img) code = nbr_img[e0 + lane];
+    }
+    const int64_t out = (int64_t)rs0 + warp_incl_scan(cnt) - cnt;
+    lane_copy_records(rec + (int64_t)s0 * words, red + out * words, cnt, words, code, edge);
+    if (gather)
+        for (int32_t l = 0; l < cnt; ++l) gather[out + l] = (uint32_t)(s0 + l);
+}
+
+__device__ __forceinline__ void gather_part(int64_t b, int part, const float4* __restrict__ rec, int words,
+                                            const int32_t* __restrict__ box_start,
+                                            const int32_t* __restrict__ nbr_start,
+                                            const int32_t* __restrict__ nbr_idx,
+                                            const int32_t* __restrict__ nbr_img, float edge, int32_t rs0,
+                                            float4* __restrict__ red, uint32_t* __restrict__ gather,
+                                            const int32_t* __restrict__ task_kind, int lane) {
+    const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+    const int32_t lo = part * ne / kGatherParts, hi = (part + 1) * ne / kGatherParts;
+    // the chunk's offset in the stream: the streamed counts of the entries before it
+    int32_t before = 0;
+    if (lane < lo && !(task_kind && task_kind[e0 + lane] == kTaskNone)) {
+        const int32_t c = nbr_idx[e0 + lane];
+        before = box_start[c + 1] - box_start[c];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(FULL, before, o);
+    int64_t out = (int64_t)rs0 + before;
+    for (int32_t e = e0 + lo; e < e0 + hi; ++e) {
+        if (task_kind && task_kind[e] == kTaskNone) continue;   // symmetric: the mirror's mutual item covers it
+        const int32_t c = nbr_idx[e];
+        const int32_t s0 = box_start[c];
+        const int32_t cnt = box_start[c + 1] - s0;
+        const float4* src = rec + (int64_t)s0 * words;
+        float4* dst = red + out * words;
+        warp_copy_records(src, dst, cnt, words, lane, nbr_img ? nbr_img[e] : 13, edge);
+        if (gather)
+            for (int32_t l = lane; l < cnt; l += 32) gather[out + l] = (uint32_t)(s0 + l);
+        out += cnt;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ rec, int words,
                                                    const int32_t* __restrict__ box_start,
                                                    const int32_t* __restrict__ nbr_start,
@@ -446,7 +499,8 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
                                                    const int32_t* __restrict__ red_start, Header* hdr,
                                                    int64_t red_cap, float4* __restrict__ red,
                                                    uint32_t* __restrict__ gather,
-                                                   const int32_t* __restrict__ task_kind) {
+                                                   const int32_t* __restrict__ task_kind,
+                                                   const int32_t* __restrict__ heavy, int64_t heavy_cap) {
     pdl_wait();
     pdl_release();
     const int lane = threadIdx.x & 31;
@@ -458,49 +512,23 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t nb = hdr->n_boxes;
-    // kGatherParts warps per box, each copying a contiguous chunk of its entries
-    for (int64_t w = warp; w < (int64_t)nb * kGatherParts; w += nwarps) {
-        const int64_t b = w / kGatherParts;
-        const int part = (int)(w % kGatherParts);
-        const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
+    // every box: a light stream whole, a heavy stream's first part
+    for (int64_t b = warp; b < nb; b += nwarps) {
         const int32_t rs0 = red_start[b];
-        if (red_start[b + 1] - rs0 <= kGatherLight) {
-            if (part != 0) continue;
-            int32_t s0 = 0, cnt = 0, code = 13;
-            if (lane < ne && !(task_kind && task_kind[e0 + lane] == kTaskNone)) {
-                const int32_t c = nbr_idx[e0 + lane];
-                s0 = box_start[c];
-                cnt = box_start[c + 1] - s0;
-                if (nbr_img) code = nbr_img[e0 + lane];
-            }
-            const int64_t out = (int64_t)rs0 + warp_incl_scan(cnt) - cnt;
-            lane_copy_records(rec + (int64_t)s0 * words, red + out * words, cnt, words, code, edge);
-            if (gather)
-                for (int32_t l = 0; l < cnt; ++l) gather[out + l] = (uint32_t)(s0 + l);
-            continue;
-        }
-        const int32_t lo = part * ne / kGatherParts, hi = (part + 1) * ne / kGatherParts;
-        // the chunk's offset in the stream: the streamed counts of the entries before it
-        int32_t before = 0;
-        if (lane < lo && !(task_kind && task_kind[e0 + lane] == kTaskNone)) {
-            const int32_t c = nbr_idx[e0 + lane];
-            before = box_start[c + 1] - box_start[c];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(FULL, before, o);
-        int64_t out = (int64_t)rs0 + before;
-        for (int32_t e = e0 + lo; e < e0 + hi; ++e) {
-            if (task_kind && task_kind[e] == kTaskNone) continue;   // symmetric: the mirror's mutual item covers it
-            const int32_t c = nbr_idx[e];
-            const int32_t s0 = box_start[c];
-            const int32_t cnt = box_start[c + 1] - s0;
-            const float4* src = rec + (int64_t)s0 * words;
-            float4* dst = red + out * words;
-            warp_copy_records(src, dst, cnt, words, lane, nbr_img ? nbr_img[e] : 13, edge);
-            if (gather)
-                for (int32_t l = lane; l < cnt; l += 32) gather[out + l] = (uint32_t)(s0 + l);
-            out += cnt;
-        }
+        if (red_start[b + 1] - rs0 <= kGatherLight)
+            gather_light(b, rec, words, box_start, nbr_start, nbr_idx, nbr_img, edge, rs0, red, gather, task_kind,
+                         lane);
+        else
+            gather_part(b, 0, rec, words, box_start, nbr_start, nbr_idx, nbr_img, edge, rs0, red, gather, task_kind,
+                        lane);
+    }
+    // the other parts of the heavy streams
+    const int64_t nh = min((int64_t)hdr->n_heavy, heavy_cap);
+    for (int64_t w = warp; w < nh * (kGatherParts - 1); w += nwarps) {
+        const int32_t b = heavy[w / (kGatherParts - 1)];
+        const int part = 1 + (int)(w % (kGatherParts - 1));
+        gather_part(b, part, rec, words, box_start, nbr_start, nbr_idx, nbr_img, edge, red_start[b], red, gather,
+                    task_kind, lane);
     }
 }
 
@@ -524,7 +552,7 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
                             at<int32_t>(ws, L.nbr_start), at<int32_t>(ws, L.nbr_idx), hdr, S,
                             red ? at<int32_t>(ws, L.red_self) : nullptr, red_start, lb, kinds,
                             p->sym ? at<int32_t>(ws, L.mirror) : nullptr, p->sym ? at<int32_t>(ws, L.bslot) : nullptr,
-                            lb2, p->part_cap));
+                            lb2, p->part_cap, red ? at<int32_t>(ws, L.heavy) : nullptr));
     P2P_LAUNCH_CHECK();
     if (red) {
         const int sms = num_sms();
@@ -534,7 +562,7 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
                                             hdr, p->red_cap,
                                             at<float4>(ws, L.red_src),
                                             (p->flags & P2P_PLAN_GATHER_MAP) ? at<uint32_t>(ws, L.gather) : nullptr,
-                                            kinds));
+                                            kinds, at<int32_t>(ws, L.heavy), bc));
         P2P_LAUNCH_CHECK();
     } else if (is_pairtask(p->layout)) {
         return pairtask_restructure(p, ws, words, s);

@@ -21,51 +21,87 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
 // ---------------------------------------------------------------------------
-// 1. keys
+// 1. keys (with the first radix pass's digit counts)
 // ---------------------------------------------------------------------------
-// Also clears the chained-scan scratch of the box and neighbour CSR kernels
-// that follow (lb_words words; the grid always covers them).
-__global__ void k_keys(const float* __restrict__ pos, int64_t n, float lo0, float lo1, float lo2,
-                       float scale, int level, uint32_t* __restrict__ keys, Header* hdr,
-                       unsigned long long* __restrict__ lb, int64_t lb_words, int32_t* __restrict__ table,
-                       int64_t table_words) {
+// Digit histograms: hist[d * tiles + t] = the count of digit d in sort tile t
+// (kSortTile keys); the scan kernels then turn it into the scatter's offsets
+// (digit-major exclusive scan).  (Scanning a small histogram in the last
+// block of the counting kernel instead, to save the scan launch, measured
+// slower on the 64^3 grid: 0.060 vs 0.048 ms for the tree build.)
+__device__ __forceinline__ void hist_publish(const int32_t* cnt, int radix, int tiles, int32_t* hist) {
+    __syncthreads();
+    for (int d = threadIdx.x; d < radix; d += kSortThreads) hist[(int64_t)d * tiles + blockIdx.x] = cnt[d];
+}
+
+// One sort tile per block: the box key of each particle and the tile's counts
+// of the first pass's digits.  Also clears the chained-scan scratch of the box
+// and neighbour CSR kernels that follow (lb_words words) and the dense
+// key -> box table (-1).
+__global__ void __launch_bounds__(kSortThreads) k_keys(const float* __restrict__ pos, int64_t n, float lo0,
+                                                      float lo1, float lo2, float scale, int level,
+                                                      uint32_t* __restrict__ keys, Header* hdr,
+                                                      unsigned long long* __restrict__ lb, int64_t lb_words,
+                                                      int32_t* __restrict__ table, int64_t table_words,
+                                                      uint32_t mask, int32_t* __restrict__ hist) {
     pdl_wait();
     pdl_release();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < lb_words) lb[i] = 0ull;
+    __shared__ int32_t cnt[256];
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = gid; t < lb_words; t += gstride) lb[t] = 0ull;
     // the dense key -> box table starts empty (-1); the box CSR kernel fills it
-    for (int64_t t = i; t < table_words; t += (int64_t)gridDim.x * blockDim.x) table[t] = -1;
-    if (i >= n) return;
+    for (int64_t t = gid; t < table_words; t += gstride) table[t] = -1;
+    const int radix = (int)mask + 1;
+    if (threadIdx.x < radix) cnt[threadIdx.x] = 0;
+    __syncthreads();
     const float side = (float)(1 << level);
     const int32_t cmax = (1 << level) - 1;
     const float lo[3] = {lo0, lo1, lo2};
-    uint32_t c[3];
     bool bad = false;
+    // all of the thread's positions are loaded before any is used (independent loads in flight)
+    float x[kSortItems][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        // exactly one float32 subtraction and one float32 product, no contraction
-        float u = __fmul_rn(__fsub_rn(pos[3 * i + a], lo[a]), scale);
-        if (!(u >= 0.0f && u <= side)) {
-            bad = true;
-            u = 0.0f;
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = (int64_t)blockIdx.x * kSortTile + r * kSortThreads + threadIdx.x;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) x[r][a] = i < n ? pos[3 * i + a] : lo[a];
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = (int64_t)blockIdx.x * kSortTile + r * kSortThreads + threadIdx.x;
+        if (i < n) {
+            uint32_t c[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                // exactly one float32 subtraction and one float32 product, no contraction
+                float u = __fmul_rn(__fsub_rn(x[r][a], lo[a]), scale);
+                if (!(u >= 0.0f && u <= side)) {
+                    bad = true;
+                    u = 0.0f;
+                }
+                int32_t ci = (int32_t)floorf(u);
+                c[a] = (uint32_t)(ci > cmax ? cmax : ci);
+            }
+            const uint32_t key = morton3(c[0], c[1], c[2]);
+            keys[i] = key;
+            atomicAdd(&cnt[key & mask], 1);
         }
-        int32_t ci = (int32_t)floorf(u);
-        c[a] = (uint32_t)(ci > cmax ? cmax : ci);
     }
     if (bad) atomicOr(&hdr->flags, P2P_FLAG_DOMAIN);
-    keys[i] = morton3(c[0], c[1], c[2]);
+    hist_publish(cnt, radix, gridDim.x, hist);
 }
 
 // ---------------------------------------------------------------------------
 // 2. stable radix sort
 // ---------------------------------------------------------------------------
+// Digit counts of a later pass, one sort tile per block.
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n,
-                                                            int shift, uint32_t mask, int32_t* hist, int tiles) {
+                                                            int shift, uint32_t mask, int32_t* hist) {
     pdl_wait();
     pdl_release();
     __shared__ int32_t cnt[256];
     const int radix = (int)mask + 1;
-    for (int d = threadIdx.x; d < radix; d += kSortThreads) cnt[d] = 0;
+    if (threadIdx.x < radix) cnt[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
 #pragma unroll
@@ -73,8 +109,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
         int64_t i = base + r * kSortThreads + threadIdx.x;
         if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & mask], 1);
     }
-    __syncthreads();
-    for (int d = threadIdx.x; d < radix; d += kSortThreads) hist[(int64_t)d * tiles + blockIdx.x] = cnt[d];
+    hist_publish(cnt, radix, gridDim.x, hist);
 }
 
 // Stable scatter.  Within a tile, keys are taken in index order: round-major,
@@ -244,10 +279,13 @@ __device__ __forceinline__ int32_t neighbour_cell(int64_t b, const uint32_t* __r
     return c;
 }
 
-// Neighbour CSR in one pass: a block holds a tile of kNbrTile boxes, four per
-// warp; the list lengths are scanned across tiles (lookback.cuh) and each
-// list is written ascending (a found box's rank = how many found indices are
-// smaller; they are distinct).  The tile holding the last box closes the CSR.
+// Neighbour CSR in one pass: a tile of kNbrTile boxes, four per warp; the list
+// lengths are scanned across tiles (lookback.cuh) and each list is written
+// ascending (a found box's rank = how many found indices are smaller; they
+// are distinct).  The tile holding the last box closes the CSR.  A grid of a
+// few blocks per SM takes tiles by ticket until the boxes run out (the box
+// count is known on the device only; a grid sized for the capacity would
+// launch mostly empty blocks on sparse distributions).
 constexpr int kNbrPerWarp = 4;
 constexpr int kNbrTile = 8 * kNbrPerWarp;
 static_assert(kNbrTile == kBoxTile, "neighbour CSR tile");
@@ -261,53 +299,56 @@ __global__ void __launch_bounds__(256) k_nbr_csr(const uint32_t* __restrict__ bo
     __shared__ int tile_s;
     __shared__ int32_t cnt_s[kNbrTile];
     __shared__ int32_t pre_s[kNbrTile + 1];
-    if (threadIdx.x == 0) tile_s = lb_ticket(lb);
-    __syncthreads();
-    const int tile = tile_s;
     const int32_t nb = hdr->n_boxes;
-    const int64_t b0 = (int64_t)tile * kNbrTile;
-    if (b0 >= nb) return;   // past the last box (whole block): no later tile waits on it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t c[kNbrPerWarp], code[kNbrPerWarp];
+    for (;;) {
+        if (threadIdx.x == 0) tile_s = lb_ticket(lb);
+        __syncthreads();
+        const int tile = tile_s;
+        const int64_t b0 = (int64_t)tile * kNbrTile;
+        if (b0 >= nb) return;   // past the last box (whole block): no later tile waits on it
+        int32_t c[kNbrPerWarp], code[kNbrPerWarp];
 #pragma unroll
-    for (int q = 0; q < kNbrPerWarp; ++q) {
-        const int64_t b = b0 + warp * kNbrPerWarp + q;
-        c[q] = -1;
-        code[q] = 13;
-        if (b < nb) c[q] = neighbour_cell(b, box_key, nb, level, table, periodic, lane, &code[q]);
-        const int32_t found = __popc(__ballot_sync(FULL, c[q] >= 0));
-        if (lane == 0) cnt_s[warp * kNbrPerWarp + q] = found;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int32_t v = cnt_s[lane];
-        const int32_t inc = warp_incl_scan(v);
-        const int32_t agg = __shfl_sync(FULL, inc, 31);
-        const int32_t ex = lb_exclusive(lb, tile, agg, hdr);
-        pre_s[lane] = ex + inc - v;
-        if (lane == 31) pre_s[kNbrTile] = ex + inc;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kNbrPerWarp; ++q) {
-        const int64_t b = b0 + warp * kNbrPerWarp + q;
-        if (b >= nb) break;
-        const int32_t start = pre_s[warp * kNbrPerWarp + q];
-        if (lane == 0) nbr_start[b] = start;
-        int rank = 0;
-#pragma unroll
-        for (int j = 0; j < 27; ++j) {
-            const int32_t v = __shfl_sync(FULL, c[q], j);
-            rank += (v >= 0 && v < c[q]) ? 1 : 0;
+        for (int q = 0; q < kNbrPerWarp; ++q) {
+            const int64_t b = b0 + warp * kNbrPerWarp + q;
+            c[q] = -1;
+            code[q] = 13;
+            if (b < nb) c[q] = neighbour_cell(b, box_key, nb, level, table, periodic, lane, &code[q]);
+            const int32_t found = __popc(__ballot_sync(FULL, c[q] >= 0));
+            if (lane == 0) cnt_s[warp * kNbrPerWarp + q] = found;
         }
-        if (c[q] >= 0) {
-            nbr_idx[start + rank] = c[q];
-            if (nbr_img) nbr_img[start + rank] = code[q];
+        __syncthreads();
+        if (warp == 0) {
+            const int32_t v = cnt_s[lane];
+            const int32_t inc = warp_incl_scan(v);
+            const int32_t agg = __shfl_sync(FULL, inc, 31);
+            const int32_t ex = lb_exclusive(lb, tile, agg, hdr);
+            pre_s[lane] = ex + inc - v;
+            if (lane == 31) pre_s[kNbrTile] = ex + inc;
         }
-    }
-    if (threadIdx.x == 0 && nb - 1 >= b0 && nb - 1 < b0 + kNbrTile) {
-        nbr_start[nb] = pre_s[kNbrTile];
-        hdr->n_nbr = pre_s[kNbrTile];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kNbrPerWarp; ++q) {
+            const int64_t b = b0 + warp * kNbrPerWarp + q;
+            if (b >= nb) break;
+            const int32_t start = pre_s[warp * kNbrPerWarp + q];
+            if (lane == 0) nbr_start[b] = start;
+            int rank = 0;
+#pragma unroll
+            for (int j = 0; j < 27; ++j) {
+                const int32_t v = __shfl_sync(FULL, c[q], j);
+                rank += (v >= 0 && v < c[q]) ? 1 : 0;
+            }
+            if (c[q] >= 0) {
+                nbr_idx[start + rank] = c[q];
+                if (nbr_img) nbr_img[start + rank] = code[q];
+            }
+        }
+        if (threadIdx.x == 0 && nb - 1 >= b0 && nb - 1 < b0 + kNbrTile) {
+            nbr_start[nb] = pre_s[kNbrTile];
+            hdr->n_nbr = pre_s[kNbrTile];
+        }
+        __syncthreads();   // the shared tile state is reused by the next tile
     }
 }
 
@@ -332,20 +373,21 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     int32_t* hist = at<int32_t>(ws, L.hist);
     int32_t* scratch = at<int32_t>(ws, L.scan_tmp);
 
+    // radix passes over 3*level key bits, equal digit widths <= 8 bits
+    int passes = 0, dbits = 0;
+    sort_digits(p->level, &passes, &dbits);
+    const uint32_t mask = (1u << dbits) - 1u;
+    const int tiles = p->sort_tiles;
+    const int64_t hcount = (int64_t)(mask + 1) * tiles;
+
     const LbRegions lr = lb_regions(n, p->box_cap);
     unsigned long long* lb = at<unsigned long long>(ws, L.lookback);
     int32_t* table = p->use_table ? at<int32_t>(ws, L.table) : nullptr;
     const int64_t table_words = p->use_table ? ((int64_t)1 << (3 * p->level)) : 0;
-    P2P_CUDA_TRY(launch_pdl(k_keys, blocks_for(n, 256), 256, 0, s, pos, n, p->lo[0], p->lo[1], p->lo[2], p->scale,
-                            p->level, ka, hdr, lb, lr.tree_words, table, table_words));
+    P2P_CUDA_TRY(launch_pdl(k_keys, tiles, kSortThreads, 0, s, pos, n, p->lo[0], p->lo[1], p->lo[2], p->scale,
+                            p->level, ka, hdr, lb, lr.tree_words, table, table_words, mask, hist));
     P2P_LAUNCH_CHECK();
 
-    // radix passes over 3*level key bits, equal digit widths <= 8 bits
-    const int bits = 3 * p->level;
-    const int passes = (bits + 7) / 8;
-    const int dbits = (bits + passes - 1) / passes;
-    const uint32_t mask = (1u << dbits) - 1u;
-    const int tiles = p->sort_tiles;
     // ping-pong so that the last pass lands in (skey, perm)
     const uint32_t* kin = ka;
     const int32_t* vin = nullptr;  // first pass: values are the original indices
@@ -355,11 +397,14 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
         int32_t* vout = (remaining % 2 == 0) ? perm : va;
         if (kout == kin) kout = (kout == skey) ? kb : skey;  // never in place
         const int shift = ps * dbits;
-        P2P_CUDA_TRY(launch_pdl(k_radix_hist, tiles, kSortThreads, 0, s, kin, n, shift, mask, hist, tiles));
-        P2P_LAUNCH_CHECK();
-        int st = scan_exclusive(hist, hist, (int64_t)(mask + 1) * tiles, nullptr, nullptr, scratch, s);
+        if (ps > 0) {   // the first pass's digits were counted by the keys kernel
+            P2P_CUDA_TRY(launch_pdl(k_radix_hist, tiles, kSortThreads, 0, s, kin, n, shift, mask, hist));
+            P2P_LAUNCH_CHECK();
+        }
+        int st = scan_exclusive(hist, hist, hcount, nullptr, nullptr, scratch, s);
         if (st) return st;
-        P2P_CUDA_TRY(launch_pdl(k_radix_scatter, tiles, kSortThreads, 0, s, kin, vin, n, shift, mask, hist, tiles, kout, vout));
+        P2P_CUDA_TRY(launch_pdl(k_radix_scatter, tiles, kSortThreads, 0, s, kin, vin, n, shift, mask,
+                                (const int32_t*)hist, tiles, kout, vout));
         P2P_LAUNCH_CHECK();
         kin = kout;
         vin = vout;
@@ -379,7 +424,8 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     // neighbour lists
     const int64_t bc = p->box_cap;
     int32_t* nimg = p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr;
-    P2P_CUDA_TRY(launch_pdl(k_nbr_csr, blocks_for(bc, kNbrTile), 256, 0, s, box_key, hdr, p->level, table,
+    const unsigned nbr_blocks = (unsigned)std::min<int64_t>(blocks_for(bc, kNbrTile), (int64_t)num_sms() * 8);
+    P2P_CUDA_TRY(launch_pdl(k_nbr_csr, nbr_blocks, 256, 0, s, box_key, hdr, p->level, table,
                             at<int32_t>(ws, L.nbr_start), at<int32_t>(ws, L.nbr_idx), nimg, p->periodic,
                             lb + lr.nbr));
     P2P_LAUNCH_CHECK();
