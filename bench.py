@@ -633,13 +633,15 @@ def pipelined_batches(prob, layout: str, dev, steps: int, ctas_per_sm: int = 3):
             "inputs": f"{PIPE_COPIES} rotating input copies ({PIPE_COPIES * (prob.pos.nbytes + prob.strength.nbytes) >> 20} MiB > L2)"}
 
 
-def dbim_forward_adjoint(dev, steps: int, edge_points: int = 128):
+def dbim_forward_adjoint(dev, steps: int, pipes: dict, f_mhz: float, edge_points: int = 128):
     """Differentiable 128^3 configuration: L = ||P(chi u_inc) - d||^2 and dL/dchi through
-    the autograd wrapper (forward P2P + hand-written adjoint P2P), per step."""
+    the autograd wrapper (forward P2P + hand-written adjoint P2P), per step; and the two
+    P2P kernels' own times (forward u = P q, adjoint grad_q = conj(P) gbar) from the
+    plan's events, for their roofline."""
     import torch
     from paper_2511_21535_gb300 import p2p
     prob = wl.diff_helmholtz(edge_points=edge_points)
-    plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, nrhs=1, device=dev)
+    plan = p2p.Plan("helmholtz", prob.n, prob.level, prob.lo, prob.edge, nrhs=1, timing=True, device=dev)
     pos = torch.from_numpy(prob.pos).to(dev)
     uinc = torch.from_numpy(prob.extra["uinc"]).to(dev)
     with torch.no_grad():
@@ -665,10 +667,30 @@ def dbim_forward_adjoint(dev, steps: int, edge_points: int = 128):
     b.synchronize()
     ms = a.elapsed_time(b) / steps
     pairs = plan.counters(check=True)["pairs"]
+    # the two kernels alone: forward on q = chi u_inc, adjoint on gbar = 2 (u - d)
+    q = (chi0 * uinc)[None].contiguous()
+    fwd, adj = [], []
+    for _ in range(steps):
+        plan.restructure(pos, q)
+        u = plan.helmholtz(prob.k)
+        fwd.append(plan.timing()["kernel"])
+        plan.helmholtz_adjoint(prob.k, pos, (2.0 * (u - d)).contiguous(), want_q=True, want_pos=False)
+        adj.append(plan.timing()["kernel"])
+    kf, ka = sum(fwd) / len(fwd), sum(adj) / len(adj)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mufu = min(pipes["mufu_rsqrt"], pipes["mufu_sin"])
+    peak = mufu * sms * f_mhz * 1e6 / 3.0
+    achieved = 2 * pairs / ((kf + ka) * 1e-3)
     return {"workload": f"{edge_points}^3 grid, contrast sphere r = 0.3 of the extent, plane wave; "
                         "L = ||P(chi u_inc) - d||^2, dL/dchi by the adjoint kernel",
             "n": prob.n, "ms_per_step": ms, "pairs_per_step": 2 * pairs,
             "value": 2 * pairs / (ms * 1e-3), "unit": "pairs/s (forward + adjoint)",
+            "kernel_ms": {"forward": kf, "adjoint": ka},
+            "roofline": {"bound": "alu", "pipe": "mufu", "kernel": "k_helmtile (forward and adjoint)",
+                         "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak,
+                         "ops_per_pair": 3.0, "sm_mhz": f_mhz, "sms": sms,
+                         "peak_source": "MUFU lanes per SM per clock measured by p2p_measure_pipes x SMs x "
+                                        "sampled SM clock"},
             "grad_finite": bool(torch.isfinite(g).all())}
 
 
@@ -973,7 +995,7 @@ def main():
             res["pipelined"] = pipelined_batches(prob, args.layout, dev, min(max(args.steps, 20), 400))
         if not args.no_batched:
             res["batched"] = batched_vs_plain(dev, 10, pipes, f_mhz)
-            res["adjoint"] = dbim_forward_adjoint(dev, 10)
+            res["adjoint"] = dbim_forward_adjoint(dev, 10, pipes, f_mhz)
     finally:
         clk.__exit__(None, None, None)
     if rank == 0:

@@ -472,9 +472,11 @@ int p2p_read_counters(const p2p_plan* plan, const void* ws, int64_t* out, void* 
 /* phases timed when the plan has P2P_PLAN_TIMING */
 typedef enum {
     P2P_PHASE_TREE = 0,        /* p2p_tree_build                                 */
-    P2P_PHASE_RESTRUCTURE = 1, /* p2p_restructure                                */
-    P2P_PHASE_KERNEL = 2,      /* the P2P compute kernel alone                   */
-    P2P_PHASE_OPERATOR = 3,    /* p2p_gravity / p2p_helmholtz as a whole         */
+    P2P_PHASE_RESTRUCTURE = 1, /* p2p_restructure (adjoints: their records)      */
+    P2P_PHASE_KERNEL = 2,      /* the P2P compute kernel alone (operator or      */
+                               /* adjoint, whichever ran last)                   */
+    P2P_PHASE_OPERATOR = 3,    /* p2p_gravity / p2p_helmholtz / an adjoint call  */
+                               /* as a whole (work list + kernel + reduction)    */
     P2P_PHASE_COUNT = 4
 } p2p_phase_id;
 
