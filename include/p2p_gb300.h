@@ -505,6 +505,27 @@ int64_t p2p_launch_count(void);
 int p2p_measure_pipes(double* out, void* stream);
 
 /*
+ * Double-precision check reductions on the device (the paper has no
+ * counterpart; the operator computes in FP32 and only these global sums
+ * accumulate in FP64).  One block reads the whole array; the sums are added
+ * in a fixed order (deterministic).  Asynchronous on `stream`.
+ *
+ * p2p_momentum_fp64: the momentum invariant of the gravity near field.
+ *   mass float32 [n], acc float32 [n][3] (device, e.g. the inputs and the
+ *   output of p2p_gravity); out double [6] (device):
+ *   out[c] = sum_i m_i a_i[c], out[3 + c] = sum_i |m_i a_i[c]|, c = x, y, z.
+ *   The first three vanish in exact arithmetic (the neighbour relation is
+ *   symmetric and the softened kernel's gradient is odd, also across
+ *   periodic images).
+ * p2p_dot_fp64: out double [1] (device) = sum_i x_i y_i over `count` float32
+ *   values.  On complex64 arrays viewed as 2 count floats this is
+ *   Re sum_i conj(x_i) y_i, the inner product of the adjoint identity
+ *   Re<P q, y> = Re<q, P^H y> (p2p_helmholtz_adjoint gives P^H y).
+ */
+int p2p_momentum_fp64(const float* mass, const float* acc, int64_t n, double* out, void* stream);
+int p2p_dot_fp64(const float* x, const float* y, int64_t count, double* out, void* stream);
+
+/*
  * Gravity near field for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a library convenience.
  *

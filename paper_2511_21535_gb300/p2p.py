@@ -39,7 +39,8 @@ EXPORTS = ("p2p_status_string", "p2p_abi_version", "p2p_plan_create", "p2p_plan_
            "p2p_batch_set_tuning", "p2p_batch_run", "p2p_batch_autotune", "p2p_batch_capture",
            "p2p_batch_launch", "p2p_batch_counters", "p2p_selftest_bounded_wait",
            "p2p_plan_set_grid", "p2p_build_checked", "p2p_fail_host_allocs", "p2p_gravity_host",
-           "p2p_helmholtz_host", "p2p_batch_timing", "p2p_gravity_noalloc_status")
+           "p2p_helmholtz_host", "p2p_batch_timing", "p2p_gravity_noalloc_status", "p2p_momentum_fp64",
+           "p2p_dot_fp64")
 
 
 class P2PError(RuntimeError):
@@ -106,6 +107,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "p2p_batch_counters": (I, [P, P, ctypes.POINTER(I64), P]),
         "p2p_batch_timing": (I, [P, ctypes.POINTER(F)]),
         "p2p_gravity_noalloc_status": (I, [ctypes.POINTER(U), P]),
+        "p2p_momentum_fp64": (I, [P, P, I64, P, P]),
+        "p2p_dot_fp64": (I, [P, P, I64, P, P]),
         "p2p_selftest_bounded_wait": (I, [ctypes.c_uint64, P, P]),
         "p2p_plan_set_grid": (I, [P, F, I]),
         "p2p_build_checked": (I, []),
@@ -356,6 +359,28 @@ class Plan:
         out = (ctypes.c_float * len(PHASES))()
         _check(load().p2p_plan_timing(self._h, out), "p2p_plan_timing")
         return {k: float(v) for k, v in zip(PHASES, out)}
+
+
+def momentum_fp64(mass, acc, stream=None) -> torch.Tensor:
+    """Device FP64 sums (sum_i m_i a_i [3], sum_i |m_i a_i| [3]) of the gravity outputs: float64 [6]."""
+    _need(mass, torch.float32, None, mass.device)
+    _need(acc, torch.float32, (mass.numel(), 3), mass.device)
+    out = torch.empty(6, dtype=torch.float64, device=mass.device)
+    _check(load().p2p_momentum_fp64(_ptr(mass), _ptr(acc), mass.numel(), _ptr(out), _stream(stream)),
+           "p2p_momentum_fp64")
+    return out
+
+
+def dot_fp64(x, y, stream=None) -> torch.Tensor:
+    """Device FP64 sum of x_i y_i over the float32 (or complex64: Re sum conj(x) y) values: float64 [1]."""
+    xf = torch.view_as_real(x) if x.is_complex() else x
+    yf = torch.view_as_real(y) if y.is_complex() else y
+    if xf.dtype != torch.float32 or yf.dtype != torch.float32 or xf.numel() != yf.numel():
+        raise ValueError("dot_fp64 needs float32 or complex64 tensors of the same size")
+    xf, yf = xf.contiguous(), yf.contiguous()
+    out = torch.empty(1, dtype=torch.float64, device=xf.device)
+    _check(load().p2p_dot_fp64(_ptr(xf), _ptr(yf), xf.numel(), _ptr(out), _stream(stream)), "p2p_dot_fp64")
+    return out
 
 
 def _need(t, dtype, shape, device):
