@@ -1,0 +1,67 @@
+// Record copies of the restructuring (the redundant gather and the pair-task
+// stream): 16-byte words, streamed stores (the data is read later by the bulk
+// copies of the P2P kernels).  A periodic image code other than 13 moves the
+// positions (word 0: x, y, z) by the image offset times the domain edge.
+#pragma once
+
+#include "common.cuh"
+
+namespace p2p {
+
+// One lane copies cnt records of `words` 16-byte words; the other lanes of
+// the warp copy their own ranges.
+__device__ __forceinline__ void lane_copy_records(const float4* __restrict__ src, float4* __restrict__ dst,
+                                                  int32_t cnt, int words, int32_t code, float edge) {
+    const float sx = (float)(code % 3 - 1) * edge, sy = (float)((code / 3) % 3 - 1) * edge,
+                sz = (float)(code / 9 - 1) * edge;
+    const bool shift = code != 13;
+#pragma unroll 4
+    for (int32_t l = 0; l < cnt; ++l) {
+        float4 v = __ldg(src + (int64_t)l * words);
+        if (shift) {
+            v.x += sx;
+            v.y += sy;
+            v.z += sz;
+        }
+        __stcs(dst + (int64_t)l * words, v);
+        for (int w = 1; w < words; ++w) __stcs(dst + (int64_t)l * words + w, __ldg(src + (int64_t)l * words + w));
+    }
+}
+
+// One warp copies cnt records of `words` 16-byte words from src to dst
+// (coalesced, eight loads in flight per lane).
+__device__ __forceinline__ void warp_copy_records(const float4* __restrict__ src, float4* __restrict__ dst,
+                                                  int32_t cnt, int words, int lane, int32_t code, float edge) {
+    if (code != 13) {
+        const float sx = (float)(code % 3 - 1) * edge, sy = (float)((code / 3) % 3 - 1) * edge,
+                    sz = (float)(code / 9 - 1) * edge;
+        for (int32_t l = lane; l < cnt; l += 32) {
+            float4 v = __ldg(src + (int64_t)l * words);
+            v.x += sx;
+            v.y += sy;
+            v.z += sz;
+            __stcs(dst + (int64_t)l * words, v);
+            for (int w = 1; w < words; ++w) __stcs(dst + (int64_t)l * words + w, __ldg(src + (int64_t)l * words + w));
+        }
+        return;
+    }
+    const int64_t nw = (int64_t)cnt * words;
+    int64_t w = lane;
+    for (; w + 224 < nw; w += 256) {  // eight independent 16-byte loads in flight per lane
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(src + w + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) __stcs(dst + w + 32 * u, v[u]);
+    }
+    // the last (up to seven) rounds: their loads issued together, then the stores
+    float4 v[7];
+#pragma unroll
+    for (int u = 0; u < 7; ++u)
+        if (w + 32 * u < nw) v[u] = __ldg(src + w + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 7; ++u)
+        if (w + 32 * u < nw) __stcs(dst + w + 32 * u, v[u]);
+}
+
+}  // namespace p2p

@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "copy.cuh"
 #include "device.cuh"
 
 namespace p2p {

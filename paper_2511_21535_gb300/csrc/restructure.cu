@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "copy.cuh"
 #include "device.cuh"
 #include "lookback.cuh"
 
