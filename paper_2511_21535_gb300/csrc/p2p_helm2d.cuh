@@ -93,7 +93,7 @@ struct HelmTileOp {
         const int lane = threadIdx.x & 31, sg = lane % SP, t0 = (lane / SP) * KT;
         const float2 kk2 = make_float2(kk, kk);
         const float4* rj = sm + (int64_t)sg * W;
-#pragma unroll 2
+#pragma unroll 8
         for (int j = sg; j < cnt; j += SP, rj += SP * W) {
             const float4 ps = rj[0];
             const float2 sx = make_float2(ps.x, ps.x), sy = make_float2(ps.y, ps.y), sz = make_float2(ps.z, ps.z);

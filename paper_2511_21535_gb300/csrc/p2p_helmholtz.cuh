@@ -70,7 +70,7 @@ struct HelmOp {
     __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
         const int stride = W ? W : words;
         const float4* rj = sm;
-#pragma unroll 2
+#pragma unroll 4
         for (int j = 0; j < cnt; ++j, rj += stride) {
             const float4 ps = rj[0];
             float qr[R], qi[R];

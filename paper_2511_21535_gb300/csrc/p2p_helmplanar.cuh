@@ -85,7 +85,7 @@ struct HelmPlanarOp {
     template <bool CHECK>
     __device__ __forceinline__ void body(const float4* __restrict__ sm, int cnt, int rec0) {
         const float4* rj = sm;
-#pragma unroll 2
+#pragma unroll 8
         for (int j = 0; j < cnt; ++j, rj += words) {
             const float4 ps = rj[0];
             float2 qr[RP], qi[RP];
