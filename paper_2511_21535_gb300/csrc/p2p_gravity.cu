@@ -365,7 +365,7 @@ struct GravityPackOp {
     __device__ __forceinline__ void body_split(const float4* __restrict__ sm, int cnt, int rec0) {
         const float2 e2 = make_float2(eps2, eps2);
         const int cpair = cnt & ~1;
-#pragma unroll 2
+#pragma unroll 4
         for (int j = 0; j < cpair; j += 2) split_pair<CHECK>(sm[j], sm[j + 1], false, rec0 + j, e2);
         if (cnt & 1) {
             const float4 a = sm[cpair];
