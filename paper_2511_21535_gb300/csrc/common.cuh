@@ -170,8 +170,8 @@ inline cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, si
 // clears the first two, the record kernels of the restructuring the others.
 constexpr int kCsrTileElems = 2048;
 constexpr int kBoxTile = 32;
-// redundant gather: a stream of at most kGatherLight records is copied by one
-// warp, one lane per neighbour entry; longer streams by kGatherParts warps
+// redundant gather: a stream of at most kGatherLight records is copied flat by
+// one warp (with other light streams); longer ones by kGatherParts warps
 constexpr int kGatherLight = 512;
 constexpr int kGatherParts = 4;
 // Radix sort of 3 * level key bits: equal digit widths of at most 8 bits.

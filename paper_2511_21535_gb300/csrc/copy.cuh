@@ -8,26 +8,6 @@
 
 namespace p2p {
 
-// One lane copies cnt records of `words` 16-byte words; the other lanes of
-// the warp copy their own ranges.
-__device__ __forceinline__ void lane_copy_records(const float4* __restrict__ src, float4* __restrict__ dst,
-                                                  int32_t cnt, int words, int32_t code, float edge) {
-    const float sx = (float)(code % 3 - 1) * edge, sy = (float)((code / 3) % 3 - 1) * edge,
-                sz = (float)(code / 9 - 1) * edge;
-    const bool shift = code != 13;
-#pragma unroll 4
-    for (int32_t l = 0; l < cnt; ++l) {
-        float4 v = __ldg(src + (int64_t)l * words);
-        if (shift) {
-            v.x += sx;
-            v.y += sy;
-            v.z += sz;
-        }
-        __stcs(dst + (int64_t)l * words, v);
-        for (int w = 1; w < words; ++w) __stcs(dst + (int64_t)l * words + w, __ldg(src + (int64_t)l * words + w));
-    }
-}
-
 // One warp copies cnt records of `words` 16-byte words from src to dst
 // (coalesced, eight loads in flight per lane).
 __device__ __forceinline__ void warp_copy_records(const float4* __restrict__ src, float4* __restrict__ dst,

@@ -428,36 +428,119 @@ __global__ void __launch_bounds__(256) k_items_fill(Units U, Header* hdr, int tt
 
 // Redundant gather: each target box's stream is the records of its neighbour
 // boxes, in neighbour order (16-byte words), optionally with the sorted index
-// of every copied record.  A light stream (<= kGatherLight records: sparse
-// boxes, e.g. the background of a clustered distribution) is copied by one
-// warp with one lane per neighbour entry, all entries at once (the offsets are
-// a warp scan of the entries' counts); a heavy stream (listed by the box
-// statistics) by kGatherParts warps, each copying a contiguous chunk of the
-// entries one entry at a time with the whole warp (coalesced, eight loads in
-// flight per lane).  The warps first take every box (a light box whole, a
-// heavy box's first part), then the other parts of the heavy boxes.  With
-// periodic boundaries a wrapped neighbour's records are copied with their
-// positions moved to the image the box meets (word 0 holds x, y, z), so the
-// kernel needs no image logic.
-__device__ __forceinline__ void gather_light(int64_t b, const float4* __restrict__ rec, int words,
+// of every copied record.  The kernel waits on chains of dependent loads
+// (stream bounds, neighbour list, neighbour occupancies, records), so it is
+// organised to keep many chains in flight per warp:
+//  - a light stream (<= kGatherLight records: the sparse boxes of a
+//    clustered distribution, most of its boxes) is copied flat, LB boxes per
+//    warp at once: each level of their loads is issued for all LB boxes
+//    together; lane e reads the box's neighbour entry e, a warp scan of the
+//    entries' counts gives each entry's offset in the stream, and in each
+//    round lane l takes position 32 r + l of every box's stream, finds its
+//    entry by a binary search over the offsets held in the lanes (shuffles)
+//    and issues the loads of all LB boxes before their stores (coalesced);
+//  - a heavy stream (listed by the box statistics) is copied in
+//    kGatherParts parts of its entries, one warp per part copying one entry
+//    at a time with the whole warp (coalesced, eight loads in flight per
+//    lane).
+// With periodic boundaries a wrapped neighbour's records are copied with
+// their positions moved to the image the box meets (word 0 holds x, y, z),
+// so the kernel needs no image logic.
+__device__ __forceinline__ float4 image_shifted(float4 v, int32_t code, float edge) {
+    if (code != 13) {
+        v.x += (float)(code % 3 - 1) * edge;
+        v.y += (float)((code / 3) % 3 - 1) * edge;
+        v.z += (float)(code / 9 - 1) * edge;
+    }
+    return v;
+}
+
+// The light streams of boxes bx[0 .. LB) (bx[u] < 0: none).  W: words per
+// record when known at compile time (1, 2), else 0 (`words`).
+template <int W, int LB>
+__device__ __forceinline__ void gather_light(const int64_t (&bx)[LB], const float4* __restrict__ rec, int words,
                                              const int32_t* __restrict__ box_start,
                                              const int32_t* __restrict__ nbr_start,
                                              const int32_t* __restrict__ nbr_idx,
-                                             const int32_t* __restrict__ nbr_img, float edge, int32_t rs0,
-                                             float4* __restrict__ red, uint32_t* __restrict__ gather,
-                                             const int32_t* __restrict__ task_kind, int lane) {
-    const int32_t e0 = nbr_start[b], ne = nbr_start[b + 1] - e0;
-    int32_t s0 = 0, cnt = 0, code = 13;
-    if (lane < ne && !(task_kind && task_kind[e0 + lane] == kTaskNone)) {
-        const int32_t c = nbr_idx[e0 + lane];
-        s0 = box_start[c];
-        cnt = box_start[c + 1] - s0;
-        if (nbr_img) code = nbr_img[e0 + lane];
+                                             const int32_t* __restrict__ nbr_img, float edge,
+                                             const int32_t* __restrict__ red_start, float4* __restrict__ red,
+                                             uint32_t* __restrict__ gather, const int32_t* __restrict__ task_kind,
+                                             int lane) {
+    const int wd = W > 0 ? W : words;
+    // level 1: the boxes' entry ranges and stream starts
+    int32_t e0[LB], ne[LB], rs[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+        e0[u] = 0;
+        ne[u] = 0;
+        rs[u] = 0;
+        if (bx[u] >= 0) {
+            e0[u] = nbr_start[bx[u]];
+            ne[u] = nbr_start[bx[u] + 1] - e0[u];
+            rs[u] = red_start[bx[u]];
+        }
     }
-    const int64_t out = (int64_t)rs0 + warp_incl_scan(cnt) - cnt;
-    lane_copy_records(rec + (int64_t)s0 * words, red + out * words, cnt, words, code, edge);
-    if (gather)
-        for (int32_t l = 0; l < cnt; ++l) gather[out + l] = (uint32_t)(s0 + l);
+    // level 2: lane e's neighbour entry (symmetric plans: entries of kind none stream nothing)
+    int32_t cb[LB], code[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+        cb[u] = -1;
+        code[u] = 13;
+        if (lane < ne[u] && !(task_kind && task_kind[e0[u] + lane] == kTaskNone)) {
+            cb[u] = nbr_idx[e0[u] + lane];
+            if (nbr_img) code[u] = nbr_img[e0[u] + lane];
+        }
+    }
+    // level 3: the neighbours' source runs, and each entry's offset in the stream
+    int32_t s0[LB], excl[LB], len[LB];
+    int32_t rounds = 0;
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+        s0[u] = 0;
+        int32_t cnt = 0;
+        if (cb[u] >= 0) {
+            s0[u] = box_start[cb[u]];
+            cnt = box_start[cb[u] + 1] - s0[u];
+        }
+        const int32_t inc = warp_incl_scan(cnt);
+        excl[u] = inc - cnt;
+        len[u] = __shfl_sync(FULL, inc, 31);
+        rounds = max(rounds, (len[u] + 31) >> 5);
+    }
+    constexpr int WV = W > 0 ? W : 1;   // words loaded before the stores
+    for (int32_t r = 0; r < rounds; ++r) {
+        const int32_t p = 32 * r + lane;   // position in each stream
+        float4 v[LB][WV];
+        int32_t src[LB], cd[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            int j = 0;   // the last entry that starts at or before p
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int cand = j + st;   // <= 31
+                const int32_t ex = __shfl_sync(FULL, excl[u], cand);
+                if (cand < ne[u] && ex <= p) j = cand;
+            }
+            src[u] = __shfl_sync(FULL, s0[u], j) + (p - __shfl_sync(FULL, excl[u], j));
+            cd[u] = nbr_img ? __shfl_sync(FULL, code[u], j) : 13;
+            if (p < len[u]) {
+#pragma unroll
+                for (int w = 0; w < WV; ++w) v[u][w] = __ldg(rec + (int64_t)src[u] * wd + w);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            if (p >= len[u]) continue;
+            const int64_t d = (int64_t)rs[u] + p;
+            float4* o = red + d * wd;
+            __stcs(o, image_shifted(v[u][0], cd[u], edge));
+#pragma unroll
+            for (int w = 1; w < WV; ++w) __stcs(o + w, v[u][w]);
+            if (W == 0)
+                for (int w = 1; w < wd; ++w) __stcs(o + w, __ldg(rec + (int64_t)src[u] * wd + w));
+            if (gather) gather[d] = (uint32_t)src[u];
+        }
+    }
 }
 
 __device__ __forceinline__ void gather_part(int64_t b, int part, const float4* __restrict__ rec, int words,
@@ -492,7 +575,11 @@ __device__ __forceinline__ void gather_part(int64_t b, int part, const float4* _
     }
 }
 
-__global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ rec, int words,
+// Six blocks of four warps per SM (registers capped to 80, a few bytes spilled):
+// the kernel is latency bound, and 24 resident warps measured faster than 20
+// with no spill (the 4.2 M-particle Plummer sphere and the 128^3 grid).
+template <int W>
+__global__ void __launch_bounds__(128, 6) k_red_gather(const float4* __restrict__ rec, int words,
                                                    const int32_t* __restrict__ box_start,
                                                    const int32_t* __restrict__ nbr_start,
                                                    const int32_t* __restrict__ nbr_idx,
@@ -510,26 +597,27 @@ __global__ void __launch_bounds__(256) k_red_gather(const float4* __restrict__ r
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);
         return;
     }
+    constexpr int LB = W == 1 ? 4 : 2;   // light boxes per warp at once (registers: LB x W loads in flight)
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t nb = hdr->n_boxes;
-    // every box: a light stream whole, a heavy stream's first part
-    for (int64_t b = warp; b < nb; b += nwarps) {
-        const int32_t rs0 = red_start[b];
-        if (red_start[b + 1] - rs0 <= kGatherLight)
-            gather_light(b, rec, words, box_start, nbr_start, nbr_idx, nbr_img, edge, rs0, red, gather, task_kind,
-                         lane);
-        else
-            gather_part(b, 0, rec, words, box_start, nbr_start, nbr_idx, nbr_img, edge, rs0, red, gather, task_kind,
-                        lane);
+    // light streams: boxes warp, warp + nwarps, ..., LB at a time
+    for (int64_t b = warp; b < nb; b += LB * nwarps) {
+        int64_t bx[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int64_t c = b + u * nwarps;
+            bx[u] = (c < nb && red_start[c + 1] - red_start[c] <= kGatherLight) ? c : -1;
+        }
+        gather_light<W, LB>(bx, rec, words, box_start, nbr_start, nbr_idx, nbr_img, edge, red_start, red, gather,
+                            task_kind, lane);
     }
-    // the other parts of the heavy streams
+    // heavy streams, kGatherParts parts each
     const int64_t nh = min((int64_t)hdr->n_heavy, heavy_cap);
-    for (int64_t w = warp; w < nh * (kGatherParts - 1); w += nwarps) {
-        const int32_t b = heavy[w / (kGatherParts - 1)];
-        const int part = 1 + (int)(w % (kGatherParts - 1));
-        gather_part(b, part, rec, words, box_start, nbr_start, nbr_idx, nbr_img, edge, red_start[b], red, gather,
-                    task_kind, lane);
+    for (int64_t w = warp; w < nh * kGatherParts; w += nwarps) {
+        const int32_t b = heavy[w / kGatherParts];
+        gather_part(b, (int)(w % kGatherParts), rec, words, box_start, nbr_start, nbr_idx, nbr_img, edge, red_start[b],
+                    red, gather, task_kind, lane);
     }
 }
 
@@ -557,7 +645,8 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
     P2P_LAUNCH_CHECK();
     if (red) {
         const int sms = num_sms();
-        P2P_CUDA_TRY(launch_pdl(k_red_gather, sms * 8, 256, 0, s, rec, words, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+        auto kern = words == 1 ? k_red_gather<1> : words == 2 ? k_red_gather<2> : k_red_gather<0>;
+        P2P_CUDA_TRY(launch_pdl(kern, sms * 16, 128, 0, s, rec, words, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
                                             at<int32_t>(ws, L.nbr_idx),
                                             p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr, p->edge, red_start,
                                             hdr, p->red_cap,
