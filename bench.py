@@ -316,25 +316,24 @@ def measure_arm(prob, layout: str, args, dev, pipes: dict, clk, steps: int, warm
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     phases = {k: [] for k in p2p.PHASES}
     t_start = time.time()
+    # the timed steps are enqueued back to back (no host wait inside the loop,
+    # so host delays cannot idle the GPU between steps)
     for i in range(steps):
         flush.zero_()
         ev[i][0].record(stream)
         run()
         ev[i][1].record(stream)
-        if graph is None or graph_events:
-            for k, v in plan.timing().items():   # waits for this step's events
-                phases[k].append(v)
     torch.cuda.synchronize()
     t_end = time.time()
-    if graph is not None and not graph_events:
-        # event timing inside a graph replay is not available: phase times
-        # come from the same step launched on the stream, right after
-        for _ in range(min(steps, 50)):
-            flush.zero_()
-            step()
-            for k, v in plan.timing().items():
-                phases[k].append(v)
-        torch.cuda.synchronize()
+    # phase times from further steps, each read when it has ended (the replay's
+    # event nodes, or the same step launched on the stream where a replay
+    # records none)
+    for _ in range(min(steps, 50)):
+        flush.zero_()
+        run() if graph_events else step()
+        for k, v in plan.timing().items():
+            phases[k].append(v)
+    torch.cuda.synchronize()
     launches = p2p.launch_count() - launches0
     if graph is not None:
         launches = launches_per_replay * steps
@@ -521,16 +520,14 @@ def timed_graph_steps(step, steps: int, flush, stream):
         flush.zero_()
         graph.replay()
     torch.cuda.synchronize()
-    tot = 0.0
-    for _ in range(steps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:   # enqueued back to back, read at the end
         flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         graph.replay()
         b.record(stream)
-        b.synchronize()
-        tot += a.elapsed_time(b)
-    return tot / steps
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps
 
 
 def evaluation_variant(prob, layout: str, dev, steps: int, mufu_peak: float):
