@@ -86,8 +86,57 @@ __global__ void __launch_bounds__(256) k_pt_entries(const int32_t* __restrict__ 
     }
 }
 
-// one warp per task copies [records of b | records of c (at its periodic image)]
-// (symmetric self tasks: [records of b]; entries without a task: nothing)
+// The task stream: per task [records of b | records of c (at its periodic
+// image)] (symmetric self tasks: [records of b]; entries without a task:
+// nothing).  The copies wait on dependent loads (the entry, its boxes'
+// bounds, the records), so a warp takes 32 consecutive tasks at once, lane i
+// task i: their blocks are contiguous in the stream, and the blocks of at
+// most kPtFlatMax records are copied flat (in each round lane l takes
+// position 32 r + l of the small blocks, finds its task by a binary search
+// over the blocks' offsets held in the lanes, and the round's loads are
+// issued before its stores, which are coalesced); larger blocks are copied
+// afterwards, one at a time by the whole warp (eight loads in flight per
+// lane), the warps taking the tasks strided.
+// W: words per record when known at compile time (1, 2), else 0.
+constexpr int32_t kPtFlatMax = 64;
+
+__device__ __forceinline__ float4 pt_image_shifted(float4 v, int32_t code, float edge) {
+    if (code != 13) {
+        v.x += (float)(code % 3 - 1) * edge;
+        v.y += (float)((code / 3) % 3 - 1) * edge;
+        v.z += (float)(code / 9 - 1) * edge;
+    }
+    return v;
+}
+
+// task e's block: b's records (sb, nb) then c's (sc, nc, image code), at out
+struct PtBlock {
+    int32_t sb, nb, sc, nc, code, out;
+};
+
+__device__ __forceinline__ PtBlock pt_block(int64_t e, int32_t ne, const int32_t* __restrict__ box_start,
+                                            const int32_t* __restrict__ nbr_idx, const int32_t* __restrict__ ent_box,
+                                            const int32_t* __restrict__ nbr_img, const int32_t* __restrict__ pt_start,
+                                            const int32_t* __restrict__ task_kind) {
+    PtBlock t{0, 0, 0, 0, 13, 0};
+    if (e < ne) {
+        const int32_t kind = task_kind ? task_kind[e] : kTaskOneSided;
+        t.out = pt_start[e];
+        if (kind != kTaskNone) {
+            const int32_t b = ent_box[e], c = nbr_idx[e];
+            t.sb = box_start[b];
+            t.nb = box_start[b + 1] - t.sb;
+            if (kind != kTaskSelf) {
+                t.sc = box_start[c];
+                t.nc = box_start[c + 1] - t.sc;
+            }
+            if (nbr_img) t.code = nbr_img[e];
+        }
+    }
+    return t;
+}
+
+template <int W>
 __global__ void __launch_bounds__(256) k_pt_gather(const float4* __restrict__ rec, int words,
                                                   const int32_t* __restrict__ box_start,
                                                   const int32_t* __restrict__ nbr_idx,
@@ -105,22 +154,78 @@ __global__ void __launch_bounds__(256) k_pt_gather(const float4* __restrict__ re
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&hdr->flags, P2P_FLAG_CAPACITY);
         return;
     }
+    const int wd = W > 0 ? W : words;
+    constexpr int WV = W > 0 ? W : 1;      // words loaded before the stores
+    constexpr int RU = W == 1 ? 4 : 2;     // rounds per step
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t ne = hdr->n_nbr;
-    for (int64_t e = warp; e < ne; e += nwarps) {
-        const int32_t kind = task_kind ? task_kind[e] : kTaskOneSided;
-        if (kind == kTaskNone) continue;
-        const int32_t b = ent_box[e], c = nbr_idx[e];
-        const int32_t sb = box_start[b], nb = box_start[b + 1] - sb;
-        const int32_t sc = box_start[c], nc = kind == kTaskSelf ? 0 : box_start[c + 1] - sc;
-        const int64_t out = pt_start[e];
-        warp_copy_records(rec + (int64_t)sb * words, pt + out * words, nb, words, lane, 13, edge);
-        warp_copy_records(rec + (int64_t)sc * words, pt + (out + nb) * words, nc, words, lane,
-                          nbr_img ? nbr_img[e] : 13, edge);
-        if (gather) {
-            for (int32_t l = lane; l < nb; l += 32) gather[out + l] = (uint32_t)(sb + l);
-            for (int32_t l = lane; l < nc; l += 32) gather[out + nb + l] = (uint32_t)(sc + l);
+    for (int64_t e0 = warp * 32; e0 < ne; e0 += nwarps * 32) {
+        const PtBlock t = pt_block(e0 + lane, ne, box_start, nbr_idx, ent_box, nbr_img, pt_start, task_kind);
+        const int32_t sb = t.sb, nbk = t.nb, sc = t.sc, code = t.code, out = t.out;
+        const int32_t blk = t.nb + t.nc;
+        const bool big = blk > kPtFlatMax;
+        const int32_t fl = big ? 0 : blk;
+        const int32_t inc = warp_incl_scan(fl), excl = inc - fl;
+        const int32_t total = __shfl_sync(FULL, inc, 31);
+        // the small blocks, flat
+        for (int32_t p0 = 0; p0 < total; p0 += 32 * RU) {
+            float4 v[RU][WV];
+            int32_t src[RU], dst[RU], cd[RU];
+#pragma unroll
+            for (int q = 0; q < RU; ++q) {
+                const int32_t p = p0 + 32 * q + lane;
+                int j = 0;   // the last task whose small block starts at or before p
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int cand = j + st;   // <= 31
+                    if (__shfl_sync(FULL, excl, cand) <= p) j = cand;
+                }
+                const int32_t o = p - __shfl_sync(FULL, excl, j), nbj = __shfl_sync(FULL, nbk, j);
+                const int32_t sbj = __shfl_sync(FULL, sb, j), scj = __shfl_sync(FULL, sc, j);
+                const int32_t cdj = __shfl_sync(FULL, code, j);
+                const bool second = o >= nbj;   // c's part of the block
+                src[q] = second ? scj + (o - nbj) : sbj + o;
+                dst[q] = __shfl_sync(FULL, out, j) + o;
+                cd[q] = second ? cdj : 13;
+                if (p < total) {
+#pragma unroll
+                    for (int w = 0; w < WV; ++w) v[q][w] = __ldg(rec + (int64_t)src[q] * wd + w);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RU; ++q) {
+                if (p0 + 32 * q + lane >= total) continue;
+                float4* o = pt + (int64_t)dst[q] * wd;
+                __stcs(o, pt_image_shifted(v[q][0], cd[q], edge));
+#pragma unroll
+                for (int w = 1; w < WV; ++w) __stcs(o + w, v[q][w]);
+                if (W == 0)
+                    for (int w = 1; w < wd; ++w) __stcs(o + w, __ldg(rec + (int64_t)src[q] * wd + w));
+                if (gather) gather[dst[q]] = (uint32_t)src[q];
+            }
+        }
+    }
+    // the large blocks, one at a time with the whole warp: tasks warp + nwarps k,
+    // examined 32 at a time (lane l: k = 32 i + l), so that the large tasks of a
+    // region of big boxes are spread over the warps
+    for (int64_t base = warp; base < ne; base += 32 * nwarps) {
+        const PtBlock t = pt_block(base + (int64_t)lane * nwarps, ne, box_start, nbr_idx, ent_box, nbr_img, pt_start,
+                                   task_kind);
+        unsigned bm = __ballot_sync(FULL, t.nb + t.nc > kPtFlatMax);
+        while (bm) {
+            const int j = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const int32_t sbj = __shfl_sync(FULL, t.sb, j), nbj = __shfl_sync(FULL, t.nb, j);
+            const int32_t scj = __shfl_sync(FULL, t.sc, j), ncj = __shfl_sync(FULL, t.nc, j);
+            const int32_t cdj = __shfl_sync(FULL, t.code, j);
+            const int64_t oj = __shfl_sync(FULL, t.out, j);
+            warp_copy_records(rec + (int64_t)sbj * wd, pt + oj * wd, nbj, wd, lane, 13, edge);
+            warp_copy_records(rec + (int64_t)scj * wd, pt + (oj + nbj) * wd, ncj, wd, lane, cdj, edge);
+            if (gather) {
+                for (int32_t l = lane; l < nbj; l += 32) gather[oj + l] = (uint32_t)(sbj + l);
+                for (int32_t l = lane; l < ncj; l += 32) gather[oj + nbj + l] = (uint32_t)(scj + l);
+            }
         }
     }
 }
@@ -143,7 +248,8 @@ int pairtask_restructure(Plan* p, void* ws, int words, cudaStream_t s) {
     if (st) return st;
     st = scan_exclusive(part_start, part_start, ecap, &hdr->n_nbr, &hdr->part_total, at<int32_t>(ws, L.scan_tmp), s);
     if (st) return st;
-    P2P_CUDA_TRY(launch_pdl(k_pt_gather, num_sms() * 8, 256, 0, s, at<float4>(ws, L.src), words, at<int32_t>(ws, L.box_start),
+    auto gk = words == 1 ? k_pt_gather<1> : words == 2 ? k_pt_gather<2> : k_pt_gather<0>;
+    P2P_CUDA_TRY(launch_pdl(gk, num_sms() * 8, 256, 0, s, at<float4>(ws, L.src), words, at<int32_t>(ws, L.box_start),
                                             at<int32_t>(ws, L.nbr_idx), ent_box,
                                             p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr, p->edge, pt_start,
                                             hdr, p->red_cap, p->part_cap, at<float4>(ws, L.red_src),
