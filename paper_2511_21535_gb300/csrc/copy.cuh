@@ -8,19 +8,24 @@
 
 namespace p2p {
 
+// A record's first word (x, y, z) moved to the periodic image `code`
+// ((ox+1) + 3(oy+1) + 9(oz+1); 13: no move) of a domain of edge `edge`.
+__device__ __forceinline__ float4 image_shifted(float4 v, int32_t code, float edge) {
+    if (code != 13) {
+        v.x += (float)(code % 3 - 1) * edge;
+        v.y += (float)((code / 3) % 3 - 1) * edge;
+        v.z += (float)(code / 9 - 1) * edge;
+    }
+    return v;
+}
+
 // One warp copies cnt records of `words` 16-byte words from src to dst
 // (coalesced, eight loads in flight per lane).
 __device__ __forceinline__ void warp_copy_records(const float4* __restrict__ src, float4* __restrict__ dst,
                                                   int32_t cnt, int words, int lane, int32_t code, float edge) {
     if (code != 13) {
-        const float sx = (float)(code % 3 - 1) * edge, sy = (float)((code / 3) % 3 - 1) * edge,
-                    sz = (float)(code / 9 - 1) * edge;
         for (int32_t l = lane; l < cnt; l += 32) {
-            float4 v = __ldg(src + (int64_t)l * words);
-            v.x += sx;
-            v.y += sy;
-            v.z += sz;
-            __stcs(dst + (int64_t)l * words, v);
+            __stcs(dst + (int64_t)l * words, image_shifted(__ldg(src + (int64_t)l * words), code, edge));
             for (int w = 1; w < words; ++w) __stcs(dst + (int64_t)l * words + w, __ldg(src + (int64_t)l * words + w));
         }
         return;

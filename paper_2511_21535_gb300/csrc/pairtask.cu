@@ -100,15 +100,6 @@ __global__ void __launch_bounds__(256) k_pt_entries(const int32_t* __restrict__ 
 // W: words per record when known at compile time (1, 2), else 0.
 constexpr int32_t kPtFlatMax = 64;
 
-__device__ __forceinline__ float4 pt_image_shifted(float4 v, int32_t code, float edge) {
-    if (code != 13) {
-        v.x += (float)(code % 3 - 1) * edge;
-        v.y += (float)((code / 3) % 3 - 1) * edge;
-        v.z += (float)(code / 9 - 1) * edge;
-    }
-    return v;
-}
-
 // task e's block: b's records (sb, nb) then c's (sc, nc, image code), at out
 struct PtBlock {
     int32_t sb, nb, sc, nc, code, out;
@@ -197,7 +188,7 @@ __global__ void __launch_bounds__(256) k_pt_gather(const float4* __restrict__ re
             for (int q = 0; q < RU; ++q) {
                 if (p0 + 32 * q + lane >= total) continue;
                 float4* o = pt + (int64_t)dst[q] * wd;
-                __stcs(o, pt_image_shifted(v[q][0], cd[q], edge));
+                __stcs(o, image_shifted(v[q][0], cd[q], edge));
 #pragma unroll
                 for (int w = 1; w < WV; ++w) __stcs(o + w, v[q][w]);
                 if (W == 0)

@@ -446,15 +446,6 @@ __global__ void __launch_bounds__(256) k_items_fill(Units U, Header* hdr, int tt
 // With periodic boundaries a wrapped neighbour's records are copied with
 // their positions moved to the image the box meets (word 0 holds x, y, z),
 // so the kernel needs no image logic.
-__device__ __forceinline__ float4 image_shifted(float4 v, int32_t code, float edge) {
-    if (code != 13) {
-        v.x += (float)(code % 3 - 1) * edge;
-        v.y += (float)((code / 3) % 3 - 1) * edge;
-        v.z += (float)(code / 9 - 1) * edge;
-    }
-    return v;
-}
-
 // The light streams of boxes bx[0 .. LB) (bx[u] < 0: none).  W: words per
 // record when known at compile time (1, 2), else 0 (`words`).
 template <int W, int LB>
