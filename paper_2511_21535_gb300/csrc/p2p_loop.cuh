@@ -232,10 +232,6 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
             if (!dcheck(good, a.hdr)) continue;   // the same decision in every warp of the group
         }
         const int sw_lo = self_base + t0, sw_hi = sw_lo + nt;
-        op.begin(tgt, nt, sw_lo, lane);
-        if constexpr (Op::kMutFloats > 0) {
-            if (pairtask) op.set_range(mutual, slot + nbox, rs);
-        }
 
         // this warp's tiles: gw, gw + G, gw + 2G, ... of the item's tile sequence
         TileCursor pc{0, 0, 0, 0};
@@ -256,10 +252,16 @@ __device__ __forceinline__ void warp_item_loop(const LoopArgs& a, Op& op) {
             for (int g = 0; g < G && pc.r < nr; ++g) pc.next(nr, rs, rc, a.tile);
         };
 
+        // the item's first tile is in flight while the op loads its targets (both
+        // stages are free between items: every issued tile has been consumed)
+        if (pc.r < nr) issue();
+        op.begin(tgt, nt, sw_lo, lane);
+        if constexpr (Op::kMutFloats > 0) {
+            if (pairtask) op.set_range(mutual, slot + nbox, rs);
+        }
         bool failed = false;
         int cur_r = -1;   // range whose per-range state (image shift, task kind) the op holds
         const bool per_range = a.nbr_img != nullptr || (Op::kMutFloats > 0 && sym);
-        if (pc.r < nr) issue();
         while (cc.r < nr) {
             if (pc.r < nr) issue();
             if (per_range && cc.r != cur_r) {
