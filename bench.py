@@ -339,9 +339,12 @@ def measure_arm(prob, layout: str, args, dev, pipes: dict, clk, steps: int, warm
         launches = launches_per_replay * steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
+    srt = sorted(step_ms)
+    spread = {"min": srt[0], "median": srt[len(srt) // 2], "max": srt[-1]}
     csum = clk.summary(t_start, t_end)
     phases_ms = {k: (sum(v) / len(v) if v else None) for k, v in phases.items()}
     rec = {"layout": layout, "evaluation": "symmetric" if sym else "one-sided", "ms_per_step": ms,
+           "step_ms_spread": spread,
            "pairs_per_step": pairs, "geometric_pairs": geo_pairs, "phases_ms": phases_ms,
            "kernel_ms": phases_ms["kernel"], "gpu_launches": launches, "graph": graph_note, "clocks": csum,
            "n_boxes": cnt["n_boxes"], "redundant_records": cnt["total_src"] if layout != "indirect" else 0}
@@ -465,6 +468,7 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": e2e,
         "roofline": dict(main["roofline"], pipe_rates_per_sm_clk={k: round(v, 3) for k, v in pipes.items()}),
         "phases_ms": main["phases_ms"],
+        "step_ms_spread": main["step_ms_spread"],
         "pairs_per_step": main["pairs_per_step"],
         "gpu_launches": main["gpu_launches"],
         "graph": main["graph"],
