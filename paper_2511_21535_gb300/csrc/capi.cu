@@ -52,9 +52,8 @@ void compute_layout(Plan* p) {
     L.vals_a = take(n * 4);
     L.perm = take(n * 4);
     L.sorted_key = take(n * 4);
-    L.hist = take(((size_t)256 * p->sort_tiles + 1) * 4);
-    int64_t scan_max = (int64_t)256 * p->sort_tiles;
-    if (n > scan_max) scan_max = n;
+    L.hist = take(sort_scratch_bytes(p->sort_tiles));
+    int64_t scan_max = n;
     const bool pt = is_pairtask(p->layout);
     if (pt && 27 * bc > scan_max) scan_max = 27 * bc;   // scans over neighbour entries
     L.scan_tmp = take(scan_scratch_bytes(scan_max));

@@ -110,6 +110,27 @@ __global__ void __launch_bounds__(256) k_fill32(uint32_t* __restrict__ dst, uint
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) dst[i] = value;
 }
 
+// two ranges in one launch (value 0)
+__global__ void __launch_bounds__(256) k_clear2(uint32_t* __restrict__ a, int64_t na, uint32_t* __restrict__ b,
+                                               int64_t nb) {
+    pdl_wait();
+    pdl_release();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += stride) {
+        if (i < na) a[i] = 0u;
+        else b[i - na] = 0u;
+    }
+}
+
+int clear2(void* a, int64_t na, void* b, int64_t nb, cudaStream_t s) {
+    if (na + nb <= 0) return P2P_OK;
+    const int64_t blocks = std::min<int64_t>((na + nb + 255) / 256, (int64_t)num_sms() * 8);
+    P2P_CUDA_TRY(launch_pdl(k_clear2, (unsigned)blocks, 256, 0, s, static_cast<uint32_t*>(a), na,
+                            static_cast<uint32_t*>(b), nb));
+    P2P_LAUNCH_CHECK();
+    return P2P_OK;
+}
+
 int fill32(void* dst, uint32_t value, int64_t count, cudaStream_t s) {
     if (count <= 0) return P2P_OK;
     const int64_t blocks = std::min<int64_t>((count + 255) / 256, (int64_t)num_sms() * 8);

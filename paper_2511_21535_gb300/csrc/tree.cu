@@ -21,38 +21,32 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
 // ---------------------------------------------------------------------------
-// 1. keys (with the first radix pass's digit counts)
+// 1. keys (with every radix pass's digit counts)
 // ---------------------------------------------------------------------------
-// Digit histograms: hist[d * tiles + t] = the count of digit d in sort tile t
-// (kSortTile keys); the scan kernels then turn it into the scatter's offsets
-// (digit-major exclusive scan).  (Scanning a small histogram in the last
-// block of the counting kernel instead, to save the scan launch, measured
-// slower on the 64^3 grid: 0.060 vs 0.048 ms for the tree build.)
-__device__ __forceinline__ void hist_publish(const int32_t* cnt, int radix, int tiles, int32_t* hist) {
-    __syncthreads();
-    for (int d = threadIdx.x; d < radix; d += kSortThreads) hist[(int64_t)d * tiles + blockIdx.x] = cnt[d];
-}
-
-// One sort tile per block: the box key of each particle and the tile's counts
-// of the first pass's digits.  Also clears the chained-scan scratch of the box
-// and neighbour CSR kernels that follow (lb_words words) and the dense
-// key -> box table (-1).
+// One sort tile per block: the box key of each particle, and the counts of
+// each pass's digits over the tile, added to the global counts (gcount[pass *
+// 256 + digit], zeroed before the launch).  Also clears the chained-scan
+// scratch of the radix passes (sort_words words) and of the box and neighbour
+// CSR kernels (lb_words words) that follow, and the dense key -> box table (-1).
 __global__ void __launch_bounds__(kSortThreads) k_keys(const float* __restrict__ pos, int64_t n, float lo0,
                                                       float lo1, float lo2, float scale, int level,
                                                       uint32_t* __restrict__ keys, Header* hdr,
                                                       unsigned long long* __restrict__ lb, int64_t lb_words,
+                                                      uint32_t* __restrict__ sort_st, int64_t sort_words,
                                                       int32_t* __restrict__ table, int64_t table_words,
-                                                      uint32_t mask, int32_t* __restrict__ hist) {
+                                                      int passes, int dbits, uint32_t* __restrict__ gcount) {
     pdl_wait();
     pdl_release();
-    __shared__ int32_t cnt[256];
+    __shared__ int32_t cnt[kSortMaxPasses][256];
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = gid; t < lb_words; t += gstride) lb[t] = 0ull;
+    for (int64_t t = gid; t < sort_words; t += gstride) sort_st[t] = 0u;
     // the dense key -> box table starts empty (-1); the box CSR kernel fills it
     for (int64_t t = gid; t < table_words; t += gstride) table[t] = -1;
+    const uint32_t mask = (1u << dbits) - 1u;
     const int radix = (int)mask + 1;
-    if (threadIdx.x < radix) cnt[threadIdx.x] = 0;
+    for (int t = threadIdx.x; t < kSortMaxPasses * 256; t += kSortThreads) (&cnt[0][0])[t] = 0;
     __syncthreads();
     const float side = (float)(1 << level);
     const int32_t cmax = (1 << level) - 1;
@@ -84,70 +78,137 @@ __global__ void __launch_bounds__(kSortThreads) k_keys(const float* __restrict__
             }
             const uint32_t key = morton3(c[0], c[1], c[2]);
             keys[i] = key;
-            atomicAdd(&cnt[key & mask], 1);
+            for (int ps = 0; ps < passes; ++ps) atomicAdd(&cnt[ps][(key >> (ps * dbits)) & mask], 1);
         }
     }
     if (bad) atomicOr(&hdr->flags, P2P_FLAG_DOMAIN);
-    hist_publish(cnt, radix, gridDim.x, hist);
-}
-
-// ---------------------------------------------------------------------------
-// 2. stable radix sort
-// ---------------------------------------------------------------------------
-// Digit counts of a later pass, one sort tile per block.
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n,
-                                                            int shift, uint32_t mask, int32_t* hist) {
-    pdl_wait();
-    pdl_release();
-    __shared__ int32_t cnt[256];
-    const int radix = (int)mask + 1;
-    if (threadIdx.x < radix) cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        int64_t i = base + r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & mask], 1);
+    for (int t = threadIdx.x; t < passes * radix; t += kSortThreads) {
+        const int ps = t / radix, d = t - ps * radix;
+        const int32_t c = cnt[ps][d];
+        if (c) atomicAdd(&gcount[ps * 256 + d], (uint32_t)c);
     }
-    hist_publish(cnt, radix, gridDim.x, hist);
 }
 
-// Stable scatter.  Within a tile, keys are taken in index order: round-major,
-// then warp, then lane.  A key's rank among equal digits is its rank inside
-// its warp (match + popcount) plus the counts of earlier warps of the same
-// round plus the counts of earlier rounds.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
-                                                               const int32_t* __restrict__ vin, int64_t n,
-                                                               int shift, uint32_t mask,
-                                                               const int32_t* __restrict__ hist, int tiles,
-                                                               uint32_t* __restrict__ kout,
-                                                               int32_t* __restrict__ vout) {
+// ---------------------------------------------------------------------------
+// 2. stable radix sort, one launch per pass
+// ---------------------------------------------------------------------------
+// Each pass is a single-pass scatter with a decoupled look-back per digit
+// (the scheme of Merrill & Garland's chained scan, lookback.cuh, run for all
+// digits at once, as in Adinets & Merrill, "Onesweep", 2022): a block takes a
+// ticket as its sort tile, counts the tile's digits, publishes the counts,
+// and thread d walks back over the earlier tiles' status words of digit d,
+// kLookWindow tiles per step, until it meets an inclusive prefix.  The destination of the tile's first
+// key of digit d is then
+//   (keys of smaller digits, all tiles) + (keys of digit d in earlier tiles).
+// Status word of (tile, digit): (state << 30) | count; state 1 = the tile's
+// own count, 2 = the inclusive prefix over tiles 0..tile (counts < 2^30).
+// Word 0 of the pass's status region is the ticket counter.  Every wait is
+// bounded: past kLookbackLimitNs the digit records P2P_FLAG_TIMEOUT and goes
+// on with what it has (the order is then wrong but flagged).
+constexpr uint32_t kStOwn = 1u << 30;
+constexpr uint32_t kStPrefix = 2u << 30;
+constexpr uint32_t kStValue = (1u << 30) - 1u;
+constexpr int kLookWindow = 8;
+
+__device__ __forceinline__ void st_store(uint32_t* p, uint32_t v) { *reinterpret_cast<volatile uint32_t*>(p) = v; }
+__device__ __forceinline__ uint32_t st_load(const uint32_t* p) { return *reinterpret_cast<const volatile uint32_t*>(p); }
+
+// Within a tile, keys are taken in index order: round-major, then warp, then
+// lane.  A key's rank among equal digits is its rank inside its warp (match +
+// popcount) plus the counts of earlier warps of the same round plus the
+// counts of earlier rounds.
+__global__ void __launch_bounds__(kSortThreads) k_radix_pass(const uint32_t* __restrict__ kin,
+                                                            const int32_t* __restrict__ vin, int64_t n,
+                                                            int shift, uint32_t mask,
+                                                            const uint32_t* __restrict__ gcount,
+                                                            uint32_t* st, uint32_t* __restrict__ kout,
+                                                            int32_t* __restrict__ vout, Header* hdr) {
     pdl_wait();
     pdl_release();
     constexpr int W = kSortThreads / 32;
     __shared__ int32_t base[256];
     __shared__ int32_t wcnt[W][256];
     __shared__ int32_t woff[W][256];
+    __shared__ int tile_s;
     const int radix = (int)mask + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) tile_s = (int)atomicAdd(st, 1u);
     for (int d = threadIdx.x; d < radix; d += kSortThreads) {
-        base[d] = hist[(int64_t)d * tiles + blockIdx.x];
+        base[d] = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) wcnt[w][d] = 0;
     }
     __syncthreads();
-    const uint32_t lt = (1u << lane) - 1u;
-    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int tile = tile_s;
+    const int64_t tbase = (int64_t)tile * kSortTile;
+    uint32_t key[kSortItems];
+    int32_t val[kSortItems];
+#pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t i = tbase + r * kSortThreads + threadIdx.x;
-        const bool valid = i < n;
-        uint32_t key = 0;
-        int32_t val = 0;
-        if (valid) {
-            key = kin[i];
-            val = vin ? vin[i] : (int32_t)i;
+        key[r] = 0;
+        val[r] = 0;
+        if (i < n) {
+            key[r] = kin[i];
+            val[r] = vin ? vin[i] : (int32_t)i;
         }
-        const uint32_t d = valid ? ((key >> shift) & mask) : (uint32_t)radix;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r)
+        if (tbase + r * kSortThreads + threadIdx.x < n) atomicAdd(&base[(key[r] >> shift) & mask], 1);
+    __syncthreads();
+
+    // look-back: thread d finds the keys of digit d in the earlier tiles
+    int32_t excl = 0;
+    if (threadIdx.x < radix) {
+        uint32_t* sd = st + 1 + threadIdx.x;          // status of (t, d) at sd[t * radix]
+        const int32_t own = base[threadIdx.x];
+        if (tile == 0) {
+            st_store(sd, kStPrefix | (uint32_t)own);
+        } else {
+            st_store(sd + (int64_t)tile * radix, kStOwn | (uint32_t)own);
+            const uint64_t t0 = global_ns();
+            int t = tile - 1;   // nearest tile not yet added
+            for (;;) {
+                // kLookWindow predecessors per round trip (independent loads)
+                uint32_t v[kLookWindow];
+#pragma unroll
+                for (int j = 0; j < kLookWindow; ++j)
+                    v[j] = t - j >= 0 ? st_load(sd + (int64_t)(t - j) * radix) : kStPrefix;   // before tile 0: 0
+                bool done = false;
+                int j = 0;
+                for (; j < kLookWindow; ++j) {
+                    const uint32_t state = v[j] >> 30;
+                    if (state == 0u) break;           // not published yet: read again from here
+                    excl += (int32_t)(v[j] & kStValue);
+                    if (state == 2u) {
+                        done = true;
+                        break;
+                    }
+                }
+                if (done) break;
+                t -= j;
+                if (j < kLookWindow && global_ns() - t0 > kLookbackLimitNs) {
+                    atomicOr(&hdr->flags, P2P_FLAG_TIMEOUT);
+                    break;
+                }
+            }
+            st_store(sd + (int64_t)tile * radix, kStPrefix | (uint32_t)(excl + own));
+        }
+    }
+    // keys of smaller digits over all tiles (exclusive scan of the global counts)
+    const int32_t g = threadIdx.x < radix ? (int32_t)gcount[threadIdx.x] : 0;
+    int32_t gtotal;
+    const int32_t gex = block_excl_scan<kSortThreads>(g, &gtotal);
+    if (threadIdx.x < radix) base[threadIdx.x] = gex + excl;
+    __syncthreads();
+
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const bool valid = tbase + r * kSortThreads + threadIdx.x < n;
+        const uint32_t d = valid ? ((key[r] >> shift) & mask) : (uint32_t)radix;
         const uint32_t m = __match_any_sync(FULL, d);
         const int rank = __popc(m & lt);
         if (valid && rank == 0) wcnt[warp][d] = __popc(m);
@@ -166,8 +227,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         __syncthreads();
         if (valid) {
             const int32_t p = woff[warp][d] + rank;
-            kout[p] = key;
-            vout[p] = val;
+            kout[p] = key[r];
+            vout[p] = val[r];
         }
     }
 }
@@ -361,31 +422,32 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
     const Layout& L = p->L;
     Header* hdr = at<Header>(ws, L.header);
     const int64_t n = p->n;
-    // clear the tree and restructuring sections of the header (counts and flags)
-    int st0 = fill32(hdr, 0u, kOpSectionOffset / 4, s);
-    if (st0) return st0;
-
     uint32_t* ka = at<uint32_t>(ws, L.keys_a);
     uint32_t* kb = at<uint32_t>(ws, L.keys_b);
     int32_t* va = at<int32_t>(ws, L.vals_a);
     int32_t* perm = at<int32_t>(ws, L.perm);
     uint32_t* skey = at<uint32_t>(ws, L.sorted_key);
-    int32_t* hist = at<int32_t>(ws, L.hist);
-    int32_t* scratch = at<int32_t>(ws, L.scan_tmp);
 
     // radix passes over 3*level key bits, equal digit widths <= 8 bits
     int passes = 0, dbits = 0;
     sort_digits(p->level, &passes, &dbits);
     const uint32_t mask = (1u << dbits) - 1u;
     const int tiles = p->sort_tiles;
-    const int64_t hcount = (int64_t)(mask + 1) * tiles;
+    uint32_t* gcount = at<uint32_t>(ws, L.hist);
+    uint32_t* sort_st = gcount + kSortCountWords;
+    const int64_t pass_words = sort_pass_words((int)mask + 1, tiles);
+
+    // clear the tree and restructuring sections of the header (counts and flags) and the digit counts
+    int st0 = clear2(hdr, kOpSectionOffset / 4, gcount, kSortCountWords, s);
+    if (st0) return st0;
 
     const LbRegions lr = lb_regions(n, p->box_cap);
     unsigned long long* lb = at<unsigned long long>(ws, L.lookback);
     int32_t* table = p->use_table ? at<int32_t>(ws, L.table) : nullptr;
     const int64_t table_words = p->use_table ? ((int64_t)1 << (3 * p->level)) : 0;
     P2P_CUDA_TRY(launch_pdl(k_keys, tiles, kSortThreads, 0, s, pos, n, p->lo[0], p->lo[1], p->lo[2], p->scale,
-                            p->level, ka, hdr, lb, lr.tree_words, table, table_words, mask, hist));
+                            p->level, ka, hdr, lb, lr.tree_words, sort_st, passes * pass_words, table, table_words,
+                            passes, dbits, gcount));
     P2P_LAUNCH_CHECK();
 
     // ping-pong so that the last pass lands in (skey, perm)
@@ -396,15 +458,8 @@ int tree_build(Plan* p, const float* pos, void* ws, cudaStream_t s) {
         uint32_t* kout = (remaining % 2 == 0) ? skey : kb;
         int32_t* vout = (remaining % 2 == 0) ? perm : va;
         if (kout == kin) kout = (kout == skey) ? kb : skey;  // never in place
-        const int shift = ps * dbits;
-        if (ps > 0) {   // the first pass's digits were counted by the keys kernel
-            P2P_CUDA_TRY(launch_pdl(k_radix_hist, tiles, kSortThreads, 0, s, kin, n, shift, mask, hist));
-            P2P_LAUNCH_CHECK();
-        }
-        int st = scan_exclusive(hist, hist, hcount, nullptr, nullptr, scratch, s);
-        if (st) return st;
-        P2P_CUDA_TRY(launch_pdl(k_radix_scatter, tiles, kSortThreads, 0, s, kin, vin, n, shift, mask,
-                                (const int32_t*)hist, tiles, kout, vout));
+        P2P_CUDA_TRY(launch_pdl(k_radix_pass, tiles, kSortThreads, 0, s, kin, vin, n, ps * dbits, mask,
+                                (const uint32_t*)(gcount + ps * 256), sort_st + ps * pass_words, kout, vout, hdr));
         P2P_LAUNCH_CHECK();
         kin = kout;
         vin = vout;
