@@ -7,6 +7,7 @@
 #include "common.cuh"
 #include "nvtx_range.cuh"
 #include "p2p_loop.cuh"
+#include "sort_scratch.cuh"
 
 struct p2p_plan {
     p2p::Plan p;

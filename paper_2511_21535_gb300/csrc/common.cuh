@@ -181,17 +181,6 @@ inline void sort_digits(int level, int* passes, int* dbits) {
     *dbits = (bits + *passes - 1) / *passes;
 }
 
-// Radix-sort scratch (the workspace's `hist` section): the digit counts of
-// every pass over all particles (kSortMaxPasses x 256 words, cleared by the
-// tree build's first fill), then per pass a ticket word and one look-back
-// status word per (sort tile, digit), cleared by the keys kernel.
-constexpr int kSortMaxPasses = 4;
-constexpr int64_t kSortCountWords = (int64_t)kSortMaxPasses * 256;
-inline int64_t sort_pass_words(int radix, int tiles) { return 1 + (int64_t)radix * tiles; }
-inline size_t sort_scratch_bytes(int tiles) {
-    return (size_t)(kSortCountWords + kSortMaxPasses * sort_pass_words(256, tiles)) * 4;
-}
-
 struct LbRegions {
     int64_t csr, nbr, stats, stats2, tree_words, words;   // offsets and sizes in 8-byte words
 };
@@ -211,8 +200,6 @@ inline LbRegions lb_regions(int64_t n, int64_t box_cap) {
 // 32-bit fill of a device range as a kernel (a memset node would break the
 // chain of programmatic launches)
 int fill32(void* dst, uint32_t value, int64_t count, cudaStream_t s);
-// zero two 32-bit ranges in one launch
-int clear2(void* a, int64_t na, void* b, int64_t nb, cudaStream_t s);
 
 inline int num_sms() {
     static int sms = 0;

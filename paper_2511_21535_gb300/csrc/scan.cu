@@ -8,6 +8,7 @@
 
 #include "common.cuh"
 #include "device.cuh"
+#include "sort_scratch.cuh"
 
 namespace p2p {
 

@@ -13,6 +13,7 @@
 #include "common.cuh"
 #include "device.cuh"
 #include "lookback.cuh"
+#include "sort_scratch.cuh"
 
 namespace p2p {
 
