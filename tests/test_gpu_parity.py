@@ -91,6 +91,12 @@ STRUCT_CASES = {
     "plummer_60000_L6": lambda: wl.plummer_gravity(n=60000, level=6, eps=1e-3),
     "grid_24": lambda: wl.grid_helmholtz(edge_points=24),
     "grid_16": lambda: wl.grid_helmholtz(edge_points=16),
+    # sort-tile edges (2,048 keys a tile) and every digit width: level 8 = three
+    # passes of 8 bits (256 digits), level 5 = two of 8, level 4 = two of 6
+    "uniform_2048_L8": lambda: wl.uniform_gravity(n=2048, level=8, seed=5),
+    "uniform_2049_L5": lambda: wl.uniform_gravity(n=2049, level=5, seed=6),
+    "plummer_4097_L4": lambda: wl.plummer_gravity(n=4097, level=4, eps=1e-3, seed=7),
+    "plummer_6143_L8": lambda: wl.plummer_gravity(n=6143, level=8, eps=1e-3, seed=8),
 }
 
 
