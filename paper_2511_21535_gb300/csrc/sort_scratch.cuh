@@ -10,6 +10,8 @@
 namespace p2p {
 
 constexpr int kSortMaxPasses = 4;   // 3 * P2P_MAX_LEVEL key bits in digits of <= 8 bits
+static_assert(3 * P2P_MAX_LEVEL <= 8 * kSortMaxPasses, "key bits beyond the reserved radix passes");
+static_assert(P2P_MAX_N < (1LL << 30), "look-back counts hold 30 bits");
 constexpr int64_t kSortCountWords = (int64_t)kSortMaxPasses * 256;
 inline int64_t sort_pass_words(int radix, int tiles) { return 1 + (int64_t)radix * tiles; }
 inline size_t sort_scratch_bytes(int tiles) {
