@@ -568,7 +568,11 @@ __device__ __forceinline__ void gather_part(int64_t b, int part, const float4* _
 
 // Six blocks of four warps per SM (registers capped to 80, a few bytes spilled):
 // the kernel is latency bound, and 24 resident warps measured faster than 20
-// with no spill (the 4.2 M-particle Plummer sphere and the 128^3 grid).
+// with no spill (the 4.2 M-particle Plummer sphere and the 128^3 grid).  The
+// grid is 32 blocks per SM (about five waves): the boxes and heavy parts are
+// dealt to warps by a fixed stride, and smaller shares per warp even out the
+// waves (measured faster than 16 and than one resident wave on the clustered
+// sphere, equal on grids).
 template <int W>
 __global__ void __launch_bounds__(128, 6) k_red_gather(const float4* __restrict__ rec, int words,
                                                    const int32_t* __restrict__ box_start,
@@ -637,7 +641,7 @@ static int restructure_tail(Plan* p, void* ws, int words, cudaStream_t s) {
     if (red) {
         const int sms = num_sms();
         auto kern = words == 1 ? k_red_gather<1> : words == 2 ? k_red_gather<2> : k_red_gather<0>;
-        P2P_CUDA_TRY(launch_pdl(kern, sms * 16, 128, 0, s, rec, words, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
+        P2P_CUDA_TRY(launch_pdl(kern, sms * 32, 128, 0, s, rec, words, at<int32_t>(ws, L.box_start), at<int32_t>(ws, L.nbr_start),
                                             at<int32_t>(ws, L.nbr_idx),
                                             p->periodic ? at<int32_t>(ws, L.nbr_img) : nullptr, p->edge, red_start,
                                             hdr, p->red_cap,
