@@ -67,25 +67,36 @@ def kernel_name(kind: str, symmetric: bool, pattern: bool = False, tile2d: bool 
     return "k_gravity_pk" if (tile2d and not symmetric) else "k_gravity"
 
 
+def traffic_records(entry):
+    """The capture records of one kernel: a single record or a list of them
+    (one per workload, layout or evaluation)."""
+    if isinstance(entry, dict):
+        return [entry]
+    return list(entry) if entry else []
+
+
 def kernel_traffic(kernel: str, workload: str, layout: str, n: int, symmetric: bool):
-    """DRAM bytes per launch from the committed ncu capture, if the kernel's
-    sources are unchanged since that capture (else None)."""
+    """DRAM bytes per launch from the committed ncu capture of this kernel on
+    this workload, layout and evaluation, if the kernel's sources are
+    unchanged since that capture (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "kernel_traffic.json")
     try:
-        rec = json.load(open(path)).get(kernel)
+        entry = json.load(open(path)).get(kernel)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("workload") != workload or rec.get("layout") != layout:
-        return None
-    if bool(rec.get("symmetric", False)) != symmetric:
-        return None
-    if rec.get("n") is not None and rec["n"] != n:
-        return None
-    h = hashlib.sha256()
-    for f in rec["source_files"]:
-        h.update(open(os.path.join(ROOT, "paper_2511_21535_gb300", "csrc", f), "rb").read())
-    return rec["dram_bytes_per_launch"] if h.hexdigest()[:16] == rec["source_hash"] else None
+    for rec in traffic_records(entry):
+        if rec.get("workload") != workload or rec.get("layout") != layout:
+            continue
+        if bool(rec.get("symmetric", False)) != symmetric:
+            continue
+        if rec.get("n") is not None and rec["n"] != n:
+            continue
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, "paper_2511_21535_gb300", "csrc", f), "rb").read())
+        return rec["dram_bytes_per_launch"] if h.hexdigest()[:16] == rec["source_hash"] else None
+    return None
 L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
 MUFU_PER_SM_CLK = 16           # nominal XU (MUFU) throughput per SM per clock
 FP32_PER_SM_CLK = 128

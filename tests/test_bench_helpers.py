@@ -35,15 +35,28 @@ def test_traffic_lookup_matches_workload_and_sources(tmp_path, monkeypatch):
     assert bench.kernel_traffic("k_y", "w", "redundant", 10, False) is None     # no record
     (csrc / "a.cuh").write_text("two")                                           # kernel changed since capture
     assert bench.kernel_traffic("k_x", "w", "redundant", 10, False) is None
+    # one record per layout of the same kernel
+    (csrc / "a.cuh").write_text("one")
+    rec["k_x"] = [rec["k_x"], dict(rec["k_x"], layout="indirect", dram_bytes_per_launch=45)]
+    (tmp_path / "profiles" / "kernel_traffic.json").write_text(json.dumps(rec))
+    assert bench.kernel_traffic("k_x", "w", "redundant", 10, False) == 123
+    assert bench.kernel_traffic("k_x", "w", "indirect", 10, False) == 45
+    assert bench.kernel_traffic("k_x", "w", "pairtask", 10, False) is None
 
 
 def test_committed_traffic_records_are_well_formed():
     d = json.load(open(os.path.join(bench.ROOT, "profiles", "kernel_traffic.json")))
-    for name, rec in d.items():
-        assert name.startswith("k_") and rec["dram_bytes_per_launch"] > 0
-        assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
-        for f in rec["source_files"]:
-            assert os.path.exists(os.path.join(bench.ROOT, "paper_2511_21535_gb300", "csrc", f))
+    for name, entry in d.items():
+        assert name.startswith("k_")
+        keys = set()
+        for rec in bench.traffic_records(entry):
+            assert rec["dram_bytes_per_launch"] > 0
+            assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
+            for f in rec["source_files"]:
+                assert os.path.exists(os.path.join(bench.ROOT, "paper_2511_21535_gb300", "csrc", f))
+            key = (rec["workload"], rec["layout"], bool(rec.get("symmetric", False)), rec.get("n"))
+            assert key not in keys   # one record per workload, layout and evaluation
+            keys.add(key)
 
 
 def test_clock_summary():
